@@ -1,0 +1,360 @@
+"""Throughput of the reacting-flow RHS / SSP-RK3 step on the 3-D jet-in-a-box
+workload (256^3 cells, 9 species, 19 reversible reactions, Gaussian laser).
+
+Metric: RHS cell-updates per second = cells x RHS evaluations / time (an RK3
+step is three RHS evaluations plus the stage updates).  The headline `value` is
+the mixed-precision path; the FP64 path is measured beside it (`fp64`).
+
+One JSON line on rank 0.  Multi-GPU runs are independent replicas (the path
+does not shard): each rank advances its own copy, value = all ranks' cell
+updates / max-over-ranks time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--n 256] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RHS cell-updates/s at 256^3 9 species, mixed vs FP64; % HBM roofline"
+UNIT = "cell-updates/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- algorithmic bytes
+
+def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
+    """Algorithmic HBM bytes per cell of one sweep launch (each input read once,
+    each output written once): Q fields (8 + 3 Ns), the state copy the fluxes use
+    (FP32 copy in the mixed path, FP64 U otherwise), the RHS accumulator; the
+    final sweep also reads U^n and U^(k) and writes U^(k+1) in FP64."""
+    nv = ns + 4
+    nq = 8 + 3 * ns
+    b = nq * rsize + nv * rsize
+    if mode == "accum":
+        return b + 2 * nv * rsize
+    return b + nv * rsize + 3 * nv * 8
+
+
+def cell_state_bytes(ns: int, rsize: int) -> int:
+    """Reads U (FP64) and T, writes T, the Q fields, the RHS source and (mixed) the FP32 copy of U."""
+    nv = ns + 4
+    b = nv * 8 + 8 + 8 + (8 + 3 * ns) * rsize + nv * rsize
+    if rsize == 4:
+        b += nv * 4
+    return b
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+    from paper_2202_02319_b300 import native as nv, synth
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    n = args.n
+    t_gen = time.time()
+    case = synth.case_jet(0, n, device=dev)
+    gen_s = time.time() - t_gen
+    ns = case.mech.n_species
+    ncell = case.grid.ncells
+    prim = case.prim.reshape(5 + ns, ncell).contiguous()
+    mech = nv.init_mechanism(case.mech)
+    las = case.laser.as_tuple()
+
+    def make(precision):
+        ctx = nv.create_ctx(mech, case.grid, precision, 0)
+        U = torch.empty((ns + 4, ncell), dtype=torch.float64, device=dev)
+        T = torch.empty(ncell, dtype=torch.float64, device=dev)
+        nv.init_state(ctx, prim, U, T)
+        nv.check(ctx)
+        return ctx, U, T
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed_steps(ctx, U, T, steps, warmup):
+        t = torch.zeros(1, dtype=torch.float64, device=dev)
+        dt = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(warmup):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, dt)
+        nv.check(ctx)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(steps):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, dt)
+        e1.record(s)
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        nv.check(ctx)
+        return ms, float(t), float(dt)
+
+    # --- mixed path (headline)
+    ctx, U, T = make(nv.RF_MIXED)
+    with ClockSampler(local) as clk:
+        ms_mixed, t_end, dt_last = timed_steps(ctx, U, T, args.steps, args.warmup)
+    clocks = clk.summary()
+    if world > 1:
+        import torch.distributed as dist
+        tm = torch.tensor([ms_mixed], device=dev)
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ms_mixed = float(tm)
+    per_step_ms = ms_mixed / args.steps
+    value = world * ncell * 3 * args.steps / (ms_mixed * 1e-3)
+    launches_per_step = 0
+
+    # per-kernel live timings (CUDA events on the launching stream) for one step
+    nv.set_option(ctx, "profile", 1)
+    tprof = torch.zeros(1, dtype=torch.float64, device=dev)
+    tprof.fill_(t_end)
+    nsteps_prof = 2
+    for _ in range(nsteps_prof):
+        nv.rk_step(ctx, U, T, tprof, 0.0, case.cfl, las, None)
+    prof = nv.profile_read(ctx)
+    nv.set_option(ctx, "profile", 0)
+    launches_per_step = sum(v[1] for v in prof.values()) // nsteps_prof + 3     # + dt, prologue, epilogue kernels
+
+    # --- e2e through the public API with host buffers: H2D U,T, one step, D2H U
+    Uh = torch.empty_like(U, device="cpu").pin_memory()
+    Th = torch.empty_like(T, device="cpu").pin_memory()
+    Uh.copy_(U)
+    Th.copy_(T)
+    s = torch.cuda.current_stream()
+    te = torch.zeros(1, dtype=torch.float64, device=dev)
+    e2e_steps = max(1, min(3, args.steps))
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    f0.record(s)
+    for _ in range(e2e_steps):
+        U.copy_(Uh, non_blocking=True)
+        T.copy_(Th, non_blocking=True)
+        nv.rk_step(ctx, U, T, te, 0.0, case.cfl, las, None)
+        Uh.copy_(U, non_blocking=True)
+    f1.record(s)
+    torch.cuda.synchronize()
+    nv.check(ctx)
+    e2e_ms = f0.elapsed_time(f1)
+    e2e_value = world * ncell * 3 * e2e_steps / (e2e_ms * 1e-3)
+    h2d = (U.numel() + T.numel()) * 8
+    d2h = U.numel() * 8
+    del ctx, U, T, Uh, Th
+    torch.cuda.empty_cache()
+
+    # --- FP64 path
+    ctx64, U64, T64 = make(nv.RF_FP64)
+    ms64, _, _ = timed_steps(ctx64, U64, T64, args.fp64_steps, 1)
+    nv.set_option(ctx64, "profile", 1)
+    t64 = torch.zeros(1, dtype=torch.float64, device=dev)
+    nv.rk_step(ctx64, U64, T64, t64, 0.0, case.cfl, las, None)
+    prof64 = nv.profile_read(ctx64)
+    nv.set_option(ctx64, "profile", 0)
+    value64 = world * ncell * 3 * args.fp64_steps / (ms64 * 1e-3)
+    del ctx64, U64, T64
+
+    # --- roofline of the dominant kernel of the mixed step
+    peaks = _peaks()
+    tot = {k: v[0] for k, v in prof.items()}
+    dom = max(("cell_state", "sweep_x", "sweep_y", "sweep_z"), key=lambda k: tot[k])
+    kernels = {}
+    for k in ("cell_state", "sweep_x", "sweep_y", "sweep_z"):
+        ms_k, nl = prof[k]
+        if nl == 0:
+            continue
+        avg = ms_k / nl
+        if k == "cell_state":
+            b = cell_state_bytes(ns, 4)
+        else:
+            # per step: two accumulate launches per axis other than z, final z launches
+            b = sweep_bytes(ns, 4, "stage" if k == "sweep_z" else "accum")
+        gbs = b * ncell / (avg * 1e-3) / 1e9
+        kernels[k] = {"ms_per_launch": round(avg, 4), "launches": nl, "share": round(ms_k / sum(tot.values()), 4),
+                      "alg_bytes_per_cell": b, "achieved_gbs": round(gbs, 1),
+                      "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+    k64 = {}
+    for k in ("cell_state", "sweep_x", "sweep_y", "sweep_z"):
+        ms_k, nl = prof64[k]
+        if nl:
+            k64[k] = {"ms_per_launch": round(ms_k / nl, 4), "share": round(ms_k / sum(v[0] for v in prof64.values()), 4)}
+    d = kernels[dom]
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,
+                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic (seeded jet-in-a-box, device-generated)",
+        "config": {"workload": f"jet_in_box_{n}^3_9sp_19r_laser", "cells": ncell, "species": ns,
+                   "reactions": case.mech.n_reactions, "precision": "mixed", "cfl": case.cfl,
+                   "l2_flush": "not needed: state and workspace (>10 GB) exceed the 126 MB L2",
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps,
+                 "kernels": k64},
+        "kernels": kernels,
+        "roofline": roofline,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "sim": {"t_end_s": t_end, "dt_last_s": dt_last, "generation_s": round(gen_s, 2)},
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, case_n=args.cpu_n)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- oracle arm
+
+def _oracle_sample(n):
+    """A bounded sample of the workload: the same generator and mechanism on an
+    n^3 periodic box (jet radius scaled), on the host."""
+    from paper_2202_02319_b300 import synth
+    return synth.case_jet(0, n)
+
+
+def cpu_baseline(args, case_n=32, budget_s=20.0):
+    import torch
+    import oracle
+    from oracle.mech import from_synth, grid_from_synth
+    case = _oracle_sample(case_n)
+    mt = from_synth(case.mech)
+    g = grid_from_synth(case.grid)
+    U, T = oracle.rhs.init_state(mt, torch.as_tensor(case.prim, dtype=torch.float64))
+    las = case.laser.as_tuple()
+    oracle.rhs.rhs(mt, g, U, T, 0.0, las)            # warm-up
+    t0 = time.time()
+    k = 0
+    while True:
+        oracle.rhs.rhs(mt, g, U, T, 0.0, las)
+        k += 1
+        if time.time() - t0 > budget_s or k >= 50:
+            break
+    el = time.time() - t0
+    return {"value": case.grid.ncells * k / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"{k} oracle RHS evaluations of the same generator and mechanism on a {case_n}^3 box "
+                      f"({el:.1f} s)"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import torch
+    cb = cpu_baseline(args, case_n=args.cpu_n, budget_s=max(5.0, args.steps * 4.0))
+    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet-in-a-box)",
+           "config": {"workload": f"jet_in_box_{args.n}^3_9sp_19r_laser",
+                      "sample": f"{args.cpu_n}^3 box of the same generator and mechanism"},
+           "cpu_baseline": cb,
+           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--n", type=int, default=256)
+    ap.add_argument("--cpu-n", type=int, default=32)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

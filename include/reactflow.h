@@ -1,0 +1,193 @@
+/*
+ * reactflow.h -- C ABI of the B300 reacting-flow right-hand-side library.
+ *
+ * The library evaluates the explicit right-hand side of the multicomponent
+ * reacting Navier-Stokes equations on a uniform Cartesian grid and advances it
+ * with SSP-RK3 (paper: Methods, Governing equations; Methods, Numerical method).
+ * Each RHS evaluation recovers primitives (temperature by a Newton solve on the
+ * NASA polynomial fits), evaluates Wilke / mixture-averaged transport,
+ * reversible Arrhenius chemistry and a Gaussian laser source, and adds the
+ * divergence of WENO3-Z local-Lax-Friedrichs inviscid fluxes and second-order
+ * central viscous, heat and species-diffusion fluxes.
+ *
+ * Conventions
+ *  - Every entry point returns int: RF_OK (0) or a negative RF_E* code; no C++
+ *    exception, trap or device assert crosses the ABI.  rf_last_error() gives a
+ *    thread-local message for the last failing call on this thread.
+ *  - Arrays marked "device" are CUDA device pointers owned by the caller (for
+ *    example torch tensors); the library never frees them.  Arrays marked "host"
+ *    are read during the call only.
+ *  - Field layout: structure of arrays, variable-major, x fastest:
+ *    a[v][k][j][i] at offset v*N + (k*ny + j)*nx + i, N = nx*ny*nz.
+ *    Conserved variables U (nv = Ns + 4 fields, FP64):
+ *    rho*Y_1 .. rho*Y_Ns [kg/m^3], rho*u, rho*v, rho*w [kg/m^2/s], E [J/m^3]
+ *    (total energy including formation enthalpy).  T: one FP64 field [K].
+ *  - Device work is enqueued on the caller's stream and is asynchronous.
+ *    Run-time failures detected on the device (Newton non-convergence,
+ *    non-finite values, temperature out of range, a bounded wait that ran out)
+ *    are recorded in a per-context status word; rf_status() synchronises the
+ *    stream, returns the matching RF_E* code and clears the word.
+ *  - SI units throughout.
+ */
+#ifndef REACTFLOW_H
+#define REACTFLOW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rf_stream;       /* = cudaStream_t */
+
+enum rf_code {
+    RF_OK = 0,
+    RF_EINVAL = -1,       /* bad argument: null pointer, size, unsupported species count ... */
+    RF_ENEWTON = -2,      /* temperature Newton solve did not converge in some cell */
+    RF_ENONFINITE = -3,   /* NaN or Inf met in the state or its derived quantities */
+    RF_ERANGE = -4,       /* temperature or density outside the admissible range */
+    RF_ECUDA = -5,        /* a CUDA runtime call failed (message names it) */
+    RF_ETIMEOUT = -6,     /* a bounded device-side wait gave up */
+    RF_ENOMEM = -7        /* device allocation failed */
+};
+
+enum rf_precision {
+    RF_FP64 = 0,          /* every operation in FP64 */
+    RF_MIXED = 1          /* FP32 bulk arithmetic; FP64 for the temperature Newton solve,
+                             Gibbs-energy equilibrium constants and reverse rates, and
+                             the conserved-variable stage accumulation */
+};
+
+enum rf_bc {
+    RF_BC_PERIODIC = 0,
+    RF_BC_EXTRAPOLATE = 1 /* zero-gradient ghost cells (copies of the edge cell) */
+};
+
+enum rf_flags {           /* switches for tests; 0 = full method */
+    RF_NO_INVISCID = 1,
+    RF_NO_VISCOUS = 2,
+    RF_NO_CHEMISTRY = 4,
+    RF_NO_LASER = 8
+};
+
+/* Mechanism description (host arrays, copied by rf_init_mechanism).
+ * Paper: Methods, Governing equations (EOS, NASA fits, Wilke's rule,
+ * mixture-averaged diffusion) and Methods, Combustion chemistry (finite-rate
+ * Arrhenius reactions).  Ns in {1, 2, 4, 9}; Nr <= 64; every species uses the
+ * same T_mid; at most 3 reactant and 3 product molecules per reaction. */
+typedef struct {
+    int n_species;            /* Ns */
+    int n_reactions;          /* Nr */
+    const double *W;          /* [Ns] molar mass, kg/mol */
+    const double *nasa_low;   /* [Ns][7] NASA-7 a1..a7 for T <  T_mid */
+    const double *nasa_high;  /* [Ns][7] NASA-7 a1..a7 for T >= T_mid */
+    const double *T_mid;      /* [Ns] K */
+    const double *mu_ref;     /* [Ns] species viscosity at 300 K, Pa s */
+    const double *mu_exp;     /* [Ns] exponent n_s of mu_s = mu_ref (T/300)^n_s */
+    const double *D_ref;      /* [Ns][Ns] binary diffusivity at 300 K and 1 atm, m^2/s (symmetric) */
+    const double *A;          /* [Nr] pre-exponential factor, (m^3/mol)^(order-1)/s */
+    const double *b;          /* [Nr] temperature exponent */
+    const double *Theta;      /* [Nr] activation temperature Ea/R, K */
+    const int *nu_f;          /* [Nr][Ns] reactant stoichiometric coefficients */
+    const int *nu_r;          /* [Nr][Ns] product stoichiometric coefficients */
+    const int *reversible;    /* [Nr] 1 = reversible (k_r = k_f / K_c), 0 = irreversible */
+} rf_mech_desc;
+
+typedef struct {
+    int nx, ny, nz;           /* cells per axis, each >= 1; nx <= 1024 */
+    double dx, dy, dz;        /* spacing, m */
+    int bc[3];                /* per axis x, y, z: rf_bc */
+} rf_grid_desc;
+
+/* Gaussian laser deposition (paper: Methods, Diffusion flame, Eq. laser-qs):
+ * q_L = E / ((2 pi)^2 sigma_r^3 sigma_t) exp(-r^2 / 2 sigma_r^2) exp(-(t - t0)^2 / 2 sigma_t^2)
+ * on 3-D grids; nz = 1 uses the paper's per-unit-depth 2-D form. */
+typedef struct {
+    double E, x0, y0, z0, sigma_r, t0, sigma_t;
+} rf_laser;
+
+/* Grid totals after one evaluation (see rf_diagnostics). */
+typedef struct {
+    double total[32];         /* sum over cells of each conserved variable times the cell volume */
+    double heat_release;      /* sum over cells of HRR = -sum_s h_s omega_s times the cell volume, W */
+    double max_T;             /* K */
+    int nv;
+} rf_diag;
+
+typedef struct rf_mech rf_mech;
+typedef struct rf_ctx rf_ctx;
+
+/* Thread-local text of the last error on this thread ("" if none). */
+const char *rf_last_error(void);
+
+/* Copies the mechanism to the device.  *out owns device memory until
+ * rf_free_mechanism.  Errors: RF_EINVAL (sizes, unsupported Ns, T_mid not
+ * shared, more than 3 molecules on a side), RF_ECUDA / RF_ENOMEM. */
+int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out);
+void rf_free_mechanism(rf_mech *m);
+
+/* Creates a solver context for one grid: allocates its device workspace
+ * (primitive/coefficient fields, RHS accumulator, two RK stage states,
+ * reduction scalars, status word).  `m` must outlive the context. */
+int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precision, uint32_t flags, rf_ctx **out);
+void rf_free_ctx(rf_ctx *c);
+
+/* Device bytes held by the context's workspace. */
+size_t rf_ctx_workspace_bytes(const rf_ctx *c);
+
+/* Conserved state from primitive fields.
+ * prim (device, FP64, [5+Ns][N]): p [Pa], T [K], u, v, w [m/s], Y_1..Y_Ns.
+ * U (device, FP64, [Ns+4][N]) and T (device, FP64, [N]) are written.
+ * Paper: Methods, Governing equations (EOS p = rho R T sum Y_s / W_s). */
+int rf_init_state(rf_ctx *c, const double *prim, double *U, double *T, rf_stream s);
+
+/* dU/dt at time t (paper: Methods, Governing equations and Numerical method).
+ * U (device, FP64, [Ns+4][N]) is read; T (device, [N]) carries the Newton
+ * warm start in and the temperature of U out; laser may be NULL (no source);
+ * dUdt (device, FP64, [Ns+4][N]) is written.  Asynchronous; check rf_status. */
+int rf_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *laser, double *dUdt, rf_stream s);
+
+/* One SSP-RK3 step (Shu-Osher form, stage times t, t+dt, t+dt/2; paper:
+ * Methods, Numerical method).  U (device, [Ns+4][N]) is advanced in place;
+ * T (device, [N]) holds the Newton warm start (on exit: the temperature of the
+ * last stage's input); t_dev (device, 1 double) is advanced by dt;
+ * dt_fixed > 0 uses that step, otherwise dt = min(CFL / max sum_d (|u_d|+c)/h_d,
+ * 0.25 h_min^2 / max(nu, lambda/(rho cp), D_s), 0.2 / max |d omega_s/d rho_s|,
+ * laser clamp); dt_dev (device, 1 double) receives the step used.
+ * Asynchronous; check rf_status. */
+int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, double cfl,
+               const rf_laser *laser, double *dt_dev, rf_stream s);
+
+/* Tuning and test options of a context (host-side, take effect on the next call):
+ *   "newton_maxit" Newton iteration cap (default 30; 0 forces RF_ENEWTON, for tests)
+ *   "x_block"      threads per block of the x sweep (multiple of 32, <= 256; default 256)
+ *   "walk_block"   threads per block of the y / z sweeps (multiple of 32, <= 128; default 128)
+ *   "walk_seg"     cells walked per thread in the y / z sweeps (default 16)
+ *   "profile"      1: record a CUDA event pair on the launching stream around every
+ *                  kernel launch of this context (read with rf_profile_read); 0: off
+ * Errors: RF_EINVAL for an unknown key or a value out of range. */
+int rf_set_option(rf_ctx *c, const char *key, double value);
+
+/* Kernel classes of rf_profile_read: cell state, x sweep, y sweep, z sweep, other. */
+enum { RF_PROF_CELL = 0, RF_PROF_SWEEP_X = 1, RF_PROF_SWEEP_Y = 2, RF_PROF_SWEEP_Z = 3, RF_PROF_OTHER = 4, RF_PROF_N = 5 };
+
+/* Sums the recorded event intervals per kernel class since profiling was
+ * enabled (or last read): ms[k] total milliseconds, launches[k] launch count,
+ * for k < RF_PROF_N (nclass >= RF_PROF_N).  Waits for the recorded events;
+ * clears the record.  Errors: RF_EINVAL, RF_ECUDA. */
+int rf_profile_read(rf_ctx *c, double *ms, int *launches, int nclass);
+
+/* Synchronises s, returns the device-side status of the context as an RF_E*
+ * code (RF_OK if clean) and clears it.  *cell_out (may be NULL) receives a
+ * flat cell index that raised the first recorded failure, or -1. */
+int rf_status(rf_ctx *c, rf_stream s, long long *cell_out);
+
+/* Totals of every conserved variable, total heat release rate and max T of the
+ * state U (with T as Newton warm start).  Synchronous (result on the host). */
+int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* REACTFLOW_H */

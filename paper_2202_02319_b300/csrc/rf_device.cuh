@@ -1,0 +1,263 @@
+// Device-side data structures and per-cell physics of the reacting-flow RHS.
+//
+// Every function here is templated on R, the type of the bulk arithmetic
+// (double for the FP64 path, float for the mixed path), and on NS, the species
+// count, so that species loops unroll into registers.  The parts the mixed
+// path keeps in FP64 are written with double explicitly: the temperature
+// Newton solve, the Gibbs energies, equilibrium constants and reverse rates.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rf {
+
+constexpr int NSMAX = 9;
+constexpr int NRMAX = 64;
+constexpr double RU = 8.314462618;    // J/mol/K
+constexpr double PATM = 101325.0;     // Pa
+constexpr double EPS_WENO = 1.0e-30;
+constexpr double EPS_D = 1.0e-12;
+constexpr double T_MAX_ADMISSIBLE = 1.0e5;
+
+enum StatusBits : int { ST_NEWTON = 1, ST_NONFINITE = 2, ST_RANGE = 4, ST_TIMEOUT = 8 };
+
+// Mechanism constants, passed to every kernel by value (__grid_constant__),
+// so that reads come from the constant bank.
+struct MechDev {
+    int ns, nr, two_ranges, pad_;
+    double Tmid;
+    double W[NSMAX], invW[NSMAX], RW[NSMAX];   // R/W_s
+    double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
+    double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
+    double sc[2][NSMAX][6];                    // a1 (x lnT), a2, a3/2, a4/3, a5/4, a7
+    double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
+    double invDref[NSMAX][NSMAX];
+    double wc[NSMAX][NSMAX];                   // (W_j / W_i)^(1/4)
+    double wd[NSMAX][NSMAX];                   // 1 / sqrt(8 (1 + W_i / W_j))
+    float Wf[NSMAX], invWf[NSMAX], RWf[NSMAX];
+    float cpcf[2][NSMAX][5];
+    float mu_reff[NSMAX], mu_expf[NSMAX], euckenf[NSMAX];
+    float invDreff[NSMAX][NSMAX];
+    float wcf[NSMAX][NSMAX], wdf[NSMAX][NSMAX];
+    // reactions: compact stoichiometry (species indices repeated by coefficient)
+    double lnA[NRMAX], A[NRMAX], b[NRMAX], Theta[NRMAX];
+    float lnAf[NRMAX], bf[NRMAX], Thetaf[NRMAX];
+    int8_t n_reac[NRMAX], n_prod[NRMAX], reac[NRMAX][3], prod[NRMAX][3];
+    int8_t n_net[NRMAX], net_sp[NRMAX][6], net_nu[NRMAX][6];
+    int8_t dnu_sum[NRMAX], rev[NRMAX];
+};
+
+// One grid and the buffers of one evaluation or RK stage.
+struct Member {
+    int nx, ny, nz;
+    int bc[3];
+    double h[3], invh[3];
+    long long n;                 // cells
+    const double *U;             // stage input state (FP64, [nv][n])
+    const double *Un;            // state at the start of the step (stage update)
+    double *Uout;                // stage output state (FP64)
+    double *dUdt;                // rf_rhs output (FP64)
+    double *T;                   // temperature warm start in/out
+    void *Q;                     // primitive/coefficient fields, type R
+    void *rhs;                   // RHS accumulator, type R
+    float *U32;                  // FP32 copy of U (mixed path)
+    double *clock;               // [0] = t, [1] = dt, [2] = CFL, [3] = dt_fixed (<= 0: rule)
+    unsigned long long *rates;   // [0] acoustic, [1] diffusive, [2] chemical maxima (double bits)
+    int *status;
+    long long *bad_cell;
+    double stage_a, stage_b, stage_c;   // U_out = a Un + b (U + dt L), time t + c dt
+    double las[7];               // E, x0, y0, z0, sigma_r, t0, sigma_t
+    int laser_on;
+    int flags;
+    int want_rates;
+    int t_from_host;             // 1: stage time is t_host (rf_rhs), 0: clock[0] + stage_c clock[1]
+    double t_host;
+};
+
+// Q field order (each field n values of type R).
+enum QField { Q_U = 0, Q_V = 1, Q_W = 2, Q_P = 3, Q_C = 4, Q_T = 5, Q_MU = 6, Q_LAM = 7, Q_X0 = 8 };
+template <int NS> struct QL {
+    static constexpr int X = Q_X0, DC = Q_X0 + NS, H = Q_X0 + 2 * NS, NQ = Q_X0 + 3 * NS;
+};
+
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double log_(double x) { return log(x); }
+__device__ __forceinline__ float log_(float x) { return logf(x); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+
+template <typename R> __device__ __forceinline__ R mech_mu_ref(const MechDev &M, int s);
+template <> __device__ __forceinline__ double mech_mu_ref<double>(const MechDev &M, int s) { return M.mu_ref[s]; }
+template <> __device__ __forceinline__ float mech_mu_ref<float>(const MechDev &M, int s) { return M.mu_reff[s]; }
+template <typename R> __device__ __forceinline__ R mech_mu_exp(const MechDev &M, int s);
+template <> __device__ __forceinline__ double mech_mu_exp<double>(const MechDev &M, int s) { return M.mu_exp[s]; }
+template <> __device__ __forceinline__ float mech_mu_exp<float>(const MechDev &M, int s) { return M.mu_expf[s]; }
+template <typename R> __device__ __forceinline__ R mech_eucken(const MechDev &M, int s);
+template <> __device__ __forceinline__ double mech_eucken<double>(const MechDev &M, int s) { return M.eucken[s]; }
+template <> __device__ __forceinline__ float mech_eucken<float>(const MechDev &M, int s) { return M.euckenf[s]; }
+template <typename R> __device__ __forceinline__ R mech_invD(const MechDev &M, int s, int j);
+template <> __device__ __forceinline__ double mech_invD<double>(const MechDev &M, int s, int j) { return M.invDref[s][j]; }
+template <> __device__ __forceinline__ float mech_invD<float>(const MechDev &M, int s, int j) { return M.invDreff[s][j]; }
+template <typename R> __device__ __forceinline__ R mech_wc(const MechDev &M, int i, int j);
+template <> __device__ __forceinline__ double mech_wc<double>(const MechDev &M, int i, int j) { return M.wc[i][j]; }
+template <> __device__ __forceinline__ float mech_wc<float>(const MechDev &M, int i, int j) { return M.wcf[i][j]; }
+template <typename R> __device__ __forceinline__ R mech_wd(const MechDev &M, int i, int j);
+template <> __device__ __forceinline__ double mech_wd<double>(const MechDev &M, int i, int j) { return M.wd[i][j]; }
+template <> __device__ __forceinline__ float mech_wd<float>(const MechDev &M, int i, int j) { return M.wdf[i][j]; }
+template <typename R> __device__ __forceinline__ R mech_W(const MechDev &M, int s);
+template <> __device__ __forceinline__ double mech_W<double>(const MechDev &M, int s) { return M.W[s]; }
+template <> __device__ __forceinline__ float mech_W<float>(const MechDev &M, int s) { return M.Wf[s]; }
+template <typename R> __device__ __forceinline__ R mech_RW(const MechDev &M, int s);
+template <> __device__ __forceinline__ double mech_RW<double>(const MechDev &M, int s) { return M.RW[s]; }
+template <> __device__ __forceinline__ float mech_RW<float>(const MechDev &M, int s) { return M.RWf[s]; }
+template <typename R> __device__ __forceinline__ R mech_cpc(const MechDev &M, int r, int s, int k);
+template <> __device__ __forceinline__ double mech_cpc<double>(const MechDev &M, int r, int s, int k) { return M.cpc[r][s][k]; }
+template <> __device__ __forceinline__ float mech_cpc<float>(const MechDev &M, int r, int s, int k) { return M.cpcf[r][s][k]; }
+
+// ----------------------------------------------------------------------------- thermo
+
+// Mixture polynomial of the specific internal energy for one NASA range:
+// e(T) = e5 + T (e0 + T (e1 + T (e2 + T (e3 + T e4)))), cv(T) = de/dT.
+struct MixPoly {
+    double e[6];
+    double cv[5];
+};
+
+template <int NS>
+__device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double Rm, MixPoly &P) {
+    double c[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const double yr = Y[s] * M.RW[s];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c[k] = fma(yr, M.ec[r][s][k], c[k]);
+    }
+    // sum_s Y_s (R/W_s) [a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6] - Rm T
+    P.e[0] = c[0] - Rm;
+    P.e[1] = c[1];
+    P.e[2] = c[2];
+    P.e[3] = c[3];
+    P.e[4] = c[4];
+    P.e[5] = c[5];
+    // cv = (c0 - Rm) + 2 c1 T + 3 c2 T^2 + 4 c3 T^3 + 5 c4 T^4
+    P.cv[0] = c[0] - Rm;
+    P.cv[1] = 2.0 * c[1];
+    P.cv[2] = 3.0 * c[2];
+    P.cv[3] = 4.0 * c[3];
+    P.cv[4] = 5.0 * c[4];
+}
+
+// Newton solve of e(T) = e_target, warm-started from T; returns false if the
+// update did not fall below 1e-13 T within maxit iterations.
+template <int NS>
+__device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
+                                         double &T, int maxit) {
+    MixPoly P;
+    int r = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
+    mix_poly<NS>(M, r, Y, Rm, P);
+    for (int it = 0; it < maxit; ++it) {
+        const int rn = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
+        if (rn != r) {
+            r = rn;
+            mix_poly<NS>(M, r, Y, Rm, P);
+        }
+        const double e = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), P.e[5]);
+        const double cv = fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
+        const double dT = (e - e_target) / cv;
+        T = T - dT;
+        if (fabs(dT) <= 1.0e-13 * fabs(T)) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ int nasa_range(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
+
+// h_s/RT of species s.
+__device__ __forceinline__ double h_RT(const MechDev &M, int r, int s, double T, double invT) {
+    const double *c = M.ec[r][s];
+    return fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[0]) + c[5] * invT;
+}
+
+// s_s/R of species s.
+__device__ __forceinline__ double s_R(const MechDev &M, int r, int s, double T, double lnT) {
+    const double *c = M.sc[r][s];
+    return fma(c[0], lnT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[5]));
+}
+
+template <typename R>
+__device__ __forceinline__ R cp_R(const MechDev &M, int r, int s, R T) {
+    return fma(T, fma(T, fma(T, fma(T, mech_cpc<R>(M, r, s, 4), mech_cpc<R>(M, r, s, 3)), mech_cpc<R>(M, r, s, 2)),
+                      mech_cpc<R>(M, r, s, 1)),
+               mech_cpc<R>(M, r, s, 0));
+}
+
+// ----------------------------------------------------------------------------- transport
+
+// Wilke mixture viscosity and conductivity, mixture-averaged diffusion
+// coefficients Dc_s = rho D_s W_s / Wbar.  Ts = T / 300.
+template <typename R, int NS>
+__device__ __forceinline__ void transport(const MechDev &M, int rng, R T, R p, R rho, R Wbar, const R (&X)[NS],
+                                          R &mu, R &lam, R (&Dc)[NS], R &Dmax) {
+    const R lnTs = log_(T * R(1.0 / 300.0));
+    R mus[NS], sq[NS], isq[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        mus[s] = mech_mu_ref<R>(M, s) * exp_(mech_mu_exp<R>(M, s) * lnTs);
+        sq[s] = sqrt_(mus[s]);
+        isq[s] = rcp(sq[s]);
+    }
+    R num_mu = 0, num_lam = 0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        R den = 0;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const R a = fma(sq[i] * isq[j], mech_wc<R>(M, i, j), R(1));
+            den = fma(X[j], a * a * mech_wd<R>(M, i, j), den);
+        }
+        const R xr = X[i] * rcp(den);
+        const R cps = cp_R<R>(M, rng, i, T) * mech_RW<R>(M, i);          // cp_s, J/kg/K
+        num_mu = fma(xr, mus[i], num_mu);
+        num_lam = fma(xr, mus[i] * (cps + mech_eucken<R>(M, i)), num_lam);
+    }
+    mu = num_mu;
+    lam = num_lam;
+    if (NS == 1) {
+        Dc[0] = 0;
+        Dmax = 0;
+        return;
+    }
+    // D_ij = D_ref,ij (T/300)^1.75 (p_atm / p)
+    const R fT = exp_(R(1.75) * lnTs) * R(PATM) * rcp(p);
+    R Xe[NS];
+    R Wbe = 0;
+#pragma unroll
+    for (int j = 0; j < NS; ++j) {
+        Xe[j] = X[j] + R(EPS_D);
+        Wbe = fma(Xe[j], mech_W<R>(M, j), Wbe);
+    }
+    const R rWbe = rcp(Wbe);
+    const R rhoW = rho * rcp(Wbar);
+    Dmax = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        R num = 0, den = 0;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            if (j == s) continue;
+            num = fma(Xe[j], mech_W<R>(M, j), num);
+            den = fma(Xe[j], mech_invD<R>(M, s, j), den);
+        }
+        const R D = num * fT * rWbe * rcp(den);
+        Dmax = D > Dmax ? D : Dmax;
+        Dc[s] = rhoW * D * mech_W<R>(M, s);
+    }
+}
+
+}  // namespace rf

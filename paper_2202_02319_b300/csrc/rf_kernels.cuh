@@ -1,0 +1,699 @@
+// Kernels of one RHS evaluation / SSP-RK3 stage:
+//   cell_state   per cell: primitives (FP64 Newton for T), transport,
+//                chemistry, laser; writes the Q fields and the source-initialised RHS
+//   sweep_x      x faces: LLF-split WENO3-Z inviscid + central diffusive flux,
+//                divergence into the RHS (rows in chunks, carried left face)
+//   sweep_walk   y or z faces, one thread per line segment walking along the axis
+//   the last active sweep either accumulates, writes dU/dt, or performs the
+//   Shu-Osher stage update U_out = a Un + b (U + dt L) in FP64.
+#pragma once
+
+#include "rf_device.cuh"
+
+namespace rf {
+
+enum SweepMode { MODE_ACCUM = 0, MODE_RHS = 1, MODE_STAGE = 2 };
+enum Flags { F_NO_INVISCID = 1, F_NO_VISCOUS = 2, F_NO_CHEM = 4, F_NO_LASER = 8 };
+
+__device__ __forceinline__ int map_idx(int i, int n, int bc) {
+    if (i < 0) return bc == 0 ? i + n * ((n - 1 - i) / n) : 0;
+    if (i >= n) return bc == 0 ? i % n : n - 1;
+    return i;
+}
+
+__device__ __forceinline__ void flag_error(const Member &m, int bits, long long cell) {
+    atomicOr(m.status, bits);
+    atomicCAS((unsigned long long *)m.bad_cell, (unsigned long long)(-1LL), (unsigned long long)cell);
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) {
+    // non-negative doubles order like their bit patterns
+    if (v > 0.0) atomicMax(a, (unsigned long long)__double_as_longlong(v));
+}
+
+// ----------------------------------------------------------------------------- chemistry
+
+// Reversible mass-action rates.  C (FP64 concentrations) and G (FP64 g_s/RT)
+// live in per-thread shared-memory columns (stride = block size) so that the
+// compact stoichiometry can index species at run time; omega is accumulated in
+// the same way.  If want_rate, returns max_s |d omega_s / d rho_s|.
+template <typename R, int NS>
+__device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT, const double *__restrict__ sC,
+                                       const double *__restrict__ sG, R *__restrict__ sW, R *__restrict__ sD,
+                                       int stride, bool want_rate) {
+    const double lnRTp = lnT + log(RU / PATM);    // ln(R T / p_atm)
+    for (int j = 0; j < M.nr; ++j) {
+        double kf;
+        if (sizeof(R) == 8) {
+            kf = exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
+        } else {
+            const float lnTf = (float)lnT, invTf = (float)invT;
+            kf = (double)expf(M.lnAf[j] + M.bf[j] * lnTf - M.Thetaf[j] * invTf);
+        }
+        const int nrc = M.n_reac[j], npd = M.n_prod[j];
+        double cf = 1.0;
+        for (int k = 0; k < nrc; ++k) cf *= sC[M.reac[j][k] * stride];
+        const double fwd = kf * cf;
+        double kr = 0.0, cr = 1.0;
+        if (M.rev[j]) {
+            double dg = 0.0;
+            for (int k = 0; k < M.n_net[j]; ++k) dg = fma((double)M.net_nu[j][k], sG[M.net_sp[j][k] * stride], dg);
+            kr = kf * exp(dg + (double)M.dnu_sum[j] * lnRTp);    // k_f / K_c
+            for (int k = 0; k < npd; ++k) cr *= sC[M.prod[j][k] * stride];
+        }
+        const double q = fwd - kr * cr;
+        for (int k = 0; k < M.n_net[j]; ++k) {
+            const int s = M.net_sp[j][k];
+            sW[s * stride] = (R)fma((double)M.net_nu[j][k], q, (double)sW[s * stride]);
+        }
+        if (want_rate) {
+            // d q / d C_s by removing one factor at each position of the reactant / product lists
+            for (int k = 0; k < nrc; ++k) {
+                double part = kf;
+                for (int k2 = 0; k2 < nrc; ++k2)
+                    if (k2 != k) part *= sC[M.reac[j][k2] * stride];
+                const int s = M.reac[j][k];
+                double dn = 0.0;
+                for (int k3 = 0; k3 < M.n_net[j]; ++k3)
+                    if (M.net_sp[j][k3] == s) dn = M.net_nu[j][k3];
+                sD[s * stride] = (R)((double)sD[s * stride] + dn * part);
+            }
+            if (M.rev[j]) {
+                for (int k = 0; k < npd; ++k) {
+                    double part = kr;
+                    for (int k2 = 0; k2 < npd; ++k2)
+                        if (k2 != k) part *= sC[M.prod[j][k2] * stride];
+                    const int s = M.prod[j][k];
+                    double dn = 0.0;
+                    for (int k3 = 0; k3 < M.n_net[j]; ++k3)
+                        if (M.net_sp[j][k3] == s) dn = M.net_nu[j][k3];
+                    sD[s * stride] = (R)((double)sD[s * stride] - dn * part);
+                }
+            }
+        }
+    }
+    R best = 0;
+    if (want_rate) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const R d = fabs(sD[s * stride]);
+            best = d > best ? d : best;
+        }
+    }
+    return best;
+}
+
+// ----------------------------------------------------------------------------- cell state
+
+template <typename R, int NS>
+__global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                         int newton_maxit) {
+    constexpr int NV = NS + 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int B = blockDim.x;
+    double *sC = (double *)smem_raw;
+    double *sG = sC + NS * B;
+    R *sW = (R *)(sG + NS * B);
+    R *sD = sW + NS * B;
+    __shared__ double s_laser[2];
+    __shared__ double s_red[3][32];
+
+    const int tid = threadIdx.x;
+    const long long n = m.n;
+    const long long cell = (long long)blockIdx.x * B + tid;
+    const bool chem_on = !(m.flags & F_NO_CHEM) && M.nr > 0;
+    const bool laser_on = m.laser_on && !(m.flags & F_NO_LASER);
+    if (tid == 0 && laser_on) {
+        const double t = m.t_from_host ? m.t_host : m.clock[0] + m.stage_c * m.clock[1];
+        const double tt = (t - m.las[5]) / m.las[6];
+        const double two_pi = 6.283185307179586;
+        double norm;
+        if (m.nz == 1) norm = m.las[0] / (two_pi * sqrt(two_pi) * m.las[4] * m.las[4] * m.las[6]);
+        else norm = m.las[0] / (two_pi * two_pi * m.las[4] * m.las[4] * m.las[4] * m.las[6]);
+        s_laser[0] = norm * exp(-0.5 * tt * tt);
+        s_laser[1] = -0.5 / (m.las[4] * m.las[4]);
+    }
+    __syncthreads();
+
+    R r_ac = 0, r_df = 0, r_ch = 0;
+    if (cell < n) {
+        const double *U = m.U;
+        double rs[NS], Y[NS];
+        double rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rs[s] = U[s * n + cell];
+            rho += rs[s];
+        }
+        const double mx = U[(NS + 0) * n + cell], my = U[(NS + 1) * n + cell], mz = U[(NS + 2) * n + cell];
+        const double E = U[(NS + 3) * n + cell];
+        const double irho = 1.0 / rho;
+        const double u = mx * irho, v = my * irho, w = mz * irho;
+        double Rm = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            Y[s] = rs[s] * irho;
+            Rm = fma(Y[s], M.RW[s], Rm);
+        }
+        const double e = E * irho - 0.5 * (u * u + v * v + w * w);
+        double T = m.T[cell];
+        const bool ok = newton_T<NS>(M, Y, Rm, e, T, newton_maxit);
+        if (!ok) flag_error(m, ST_NEWTON, cell);
+        if (!(rho > 0.0) || !(T > 0.0) || !(T < T_MAX_ADMISSIBLE)) {
+            if (isfinite(rho) && isfinite(T)) flag_error(m, ST_RANGE, cell);
+            else flag_error(m, ST_NONFINITE, cell);
+        }
+        if (!isfinite(E) || !isfinite(u) || !isfinite(v) || !isfinite(w)) flag_error(m, ST_NONFINITE, cell);
+        m.T[cell] = T;
+
+        const int rng = nasa_range(M, T);
+        const double invT = 1.0 / T;
+        const double lnT = log(T);
+        double cp = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) cp = fma(Y[s] * M.RW[s], cp_R<double>(M, rng, s, T), cp);
+        const double cv = cp - Rm;
+        const double p = rho * Rm * T;
+        const double c = sqrt(cp / cv * Rm * T);
+        const double Wbar = RU / Rm;
+        R *Q = (R *)m.Q;
+        Q[Q_U * n + cell] = (R)u;
+        Q[Q_V * n + cell] = (R)v;
+        Q[Q_W * n + cell] = (R)w;
+        Q[Q_P * n + cell] = (R)p;
+        Q[Q_C * n + cell] = (R)c;
+        Q[Q_T * n + cell] = (R)T;
+        R X[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            X[s] = (R)(Y[s] * M.RW[s] / Rm);
+            Q[(QL<NS>::X + s) * n + cell] = X[s];
+            const double hrt = h_RT(M, rng, s, T, invT);
+            Q[(QL<NS>::H + s) * n + cell] = (R)(hrt * M.RW[s] * T);
+            if (chem_on) {
+                sC[s * B + tid] = rs[s] * M.invW[s];
+                sG[s * B + tid] = hrt - s_R(M, rng, s, T, lnT);
+                sW[s * B + tid] = (R)0;
+                sD[s * B + tid] = (R)0;
+            }
+        }
+        R mu, lam, Dc[NS], Dmax;
+        transport<R, NS>(M, rng, (R)T, (R)p, (R)rho, (R)Wbar, X, mu, lam, Dc, Dmax);
+        Q[Q_MU * n + cell] = mu;
+        Q[Q_LAM * n + cell] = lam;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) Q[(QL<NS>::DC + s) * n + cell] = Dc[s];
+
+        R *rhs = (R *)m.rhs;
+        if (chem_on) {
+            r_ch = chemistry<R, NS>(M, lnT, invT, sC + tid, sG + tid, sW + tid, sD + tid, B, m.want_rates != 0);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rhs[s * n + cell] = (R)((double)sW[s * B + tid] * M.W[s]);
+        } else {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rhs[s * n + cell] = (R)0;
+        }
+        rhs[(NS + 0) * n + cell] = (R)0;
+        rhs[(NS + 1) * n + cell] = (R)0;
+        rhs[(NS + 2) * n + cell] = (R)0;
+        double qL = 0.0;
+        if (laser_on) {
+            const long long nxy = (long long)m.nx * m.ny;
+            const int k = (int)(cell / nxy);
+            const long long rem = cell - (long long)k * nxy;
+            const int j = (int)(rem / m.nx), i = (int)(rem - (long long)j * m.nx);
+            const double dx = (i + 0.5) * m.h[0] - m.las[1];
+            const double dy = (j + 0.5) * m.h[1] - m.las[2];
+            double r2 = dx * dx + dy * dy;
+            if (m.nz > 1) {
+                const double dz = (k + 0.5) * m.h[2] - m.las[3];
+                r2 += dz * dz;
+            }
+            if (sizeof(R) == 8) qL = s_laser[0] * exp(s_laser[1] * r2);
+            else qL = s_laser[0] * (double)expf((float)(s_laser[1] * r2));
+        }
+        rhs[(NS + 3) * n + cell] = (R)qL;
+        if (sizeof(R) == 4) {
+#pragma unroll
+            for (int v2 = 0; v2 < NV; ++v2) m.U32[v2 * n + cell] = (float)U[v2 * n + cell];
+        }
+        if (m.want_rates) {
+            double ac = 0.0;
+            if (m.nx > 1) ac += (fabs(u) + c) * m.invh[0];
+            if (m.ny > 1) ac += (fabs(v) + c) * m.invh[1];
+            if (m.nz > 1) ac += (fabs(w) + c) * m.invh[2];
+            r_ac = (R)ac;
+            if (!(m.flags & F_NO_VISCOUS)) {
+                const R nu = mu / (R)rho;
+                const R al = lam / ((R)rho * (R)cp);
+                R d = nu > al ? nu : al;
+                r_df = Dmax > d ? Dmax : d;
+            }
+        }
+    }
+    if (m.want_rates) {
+        // block max (deterministic: max is exact), then one atomic per block
+        double a = r_ac, d = r_df, ch = r_ch;
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+            d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
+            ch = fmax(ch, __shfl_xor_sync(0xffffffffu, ch, o));
+        }
+        const int wid = tid >> 5, lane = tid & 31;
+        if (lane == 0) {
+            s_red[0][wid] = a;
+            s_red[1][wid] = d;
+            s_red[2][wid] = ch;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 1; q < (B + 31) / 32; ++q) {
+                a = fmax(a, s_red[0][q]);
+                d = fmax(d, s_red[1][q]);
+                ch = fmax(ch, s_red[2][q]);
+            }
+            atomic_max_pos(&m.rates[0], a);
+            atomic_max_pos(&m.rates[1], d);
+            atomic_max_pos(&m.rates[2], ch);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- face flux
+
+template <typename R>
+__device__ __forceinline__ R weno3z(R a, R b, R c) {
+    const R q0 = fma(R(-0.5), a, R(1.5) * b);
+    const R q1 = R(0.5) * b + R(0.5) * c;
+    const R d0 = b - a, d1 = c - b;
+    const R beta0 = d0 * d0, beta1 = d1 * d1;
+    const R tau = fabs(beta1 - beta0);
+    const R al0 = R(1.0 / 3.0) * fma(tau, rcp(beta0 + R(EPS_WENO)), R(1));
+    const R al1 = R(2.0 / 3.0) * fma(tau, rcp(beta1 + R(EPS_WENO)), R(1));
+    return fma(al0, q0, al1 * q1) * rcp(al0 + al1);
+}
+
+// Flux G = -Fhat^a + F^d at the face between cells (coord-1) and coord along DIR.
+// `cc` holds the cell's coordinates (i, j, k) with cc[DIR] = coord.
+template <typename R, typename UT, int NS, int DIR>
+__device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict__ U, const R *__restrict__ Q, const int (&cc)[3],
+                                          R (&G)[NS + 4]) {
+    constexpr int NV = NS + 4;
+    const long long n = m.n;
+    const long long sx = 1, sy = m.nx, sz = (long long)m.nx * m.ny;
+    const long long st[3] = {sx, sy, sz};
+    const int nd = DIR == 0 ? m.nx : (DIR == 1 ? m.ny : m.nz);
+    const long long base = (long long)cc[0] * sx + (long long)cc[1] * sy + (long long)cc[2] * sz - (long long)cc[DIR] * st[DIR];
+    long long id[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) id[o] = base + (long long)map_idx(cc[DIR] + o - 2, nd, m.bc[DIR]) * st[DIR];
+    // id[1] = L (coord-1), id[2] = R (coord)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    R rhoL = 0, rhoR = 0;
+    if (!(m.flags & F_NO_INVISCID)) {
+        R un[4], pp[4];
+        R alpha = 0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            un[o] = Q[(Q_U + DIR) * n + id[o]];
+            pp[o] = Q[Q_P * n + id[o]];
+            const R lam = fabs(un[o]) + Q[Q_C * n + id[o]];
+            alpha = lam > alpha ? lam : alpha;
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R fp[4], fm[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const R Uv = (R)U[v * n + id[o]];
+                if (v < NS) {
+                    if (o == 1) rhoL += Uv;
+                    if (o == 2) rhoR += Uv;
+                }
+                R F = un[o] * Uv;
+                if (v == NS + DIR) F += pp[o];
+                if (v == NS + 3) F = fma(pp[o], un[o], F);
+                fp[o] = R(0.5) * fma(alpha, Uv, F);
+                fm[o] = R(0.5) * fma(-alpha, Uv, F);
+            }
+            G[v] = -(weno3z<R>(fp[0], fp[1], fp[2]) + weno3z<R>(fm[3], fm[2], fm[1]));
+        }
+    }
+    if (!(m.flags & F_NO_VISCOUS)) {
+        if (m.flags & F_NO_INVISCID) {
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                rhoL += (R)U[s * n + id[1]];
+                rhoR += (R)U[s * n + id[2]];
+            }
+        }
+        const long long iL = id[1], iR = id[2];
+        const R ih = (R)m.invh[DIR];
+        R velL[3], velR[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            velL[q] = Q[(Q_U + q) * n + iL];
+            velR[q] = Q[(Q_U + q) * n + iR];
+        }
+        const R mu = R(0.5) * (Q[Q_MU * n + iL] + Q[Q_MU * n + iR]);
+        const R lam = R(0.5) * (Q[Q_LAM * n + iL] + Q[Q_LAM * n + iR]);
+        R dn[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) dn[q] = (velR[q] - velL[q]) * ih;
+        // tangential derivatives of u_DIR and u_t along t at L and R
+        R dtd[3] = {0, 0, 0}, dtt[3] = {0, 0, 0};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == DIR) continue;
+            const int nt = t == 0 ? m.nx : (t == 1 ? m.ny : m.nz);
+            const long long op = (long long)(map_idx(cc[t] + 1, nt, m.bc[t]) - cc[t]) * st[t];
+            const long long om = (long long)(map_idx(cc[t] - 1, nt, m.bc[t]) - cc[t]) * st[t];
+            const R q4 = R(0.25) * (R)m.invh[t];
+            const R *vd = Q + (Q_U + DIR) * n;
+            const R *vt = Q + (Q_U + t) * n;
+            dtd[t] = ((vd[iL + op] - vd[iL + om]) + (vd[iR + op] - vd[iR + om])) * q4;
+            dtt[t] = ((vt[iL + op] - vt[iL + om]) + (vt[iR + op] - vt[iR + om])) * q4;
+        }
+        R div = dn[DIR];
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t != DIR) div += dtt[t];
+        R tau[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (q == DIR) tau[q] = mu * (R(2) * dn[DIR]) - R(2.0 / 3.0) * mu * div;
+            else tau[q] = mu * (dtd[q] + dn[q]);
+        }
+        // species diffusion with correction velocity, enthalpy flux
+        R corr = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const R dX = (Q[(QL<NS>::X + s) * n + iR] - Q[(QL<NS>::X + s) * n + iL]) * ih;
+            const R Dcf = R(0.5) * (Q[(QL<NS>::DC + s) * n + iL] + Q[(QL<NS>::DC + s) * n + iR]);
+            corr = fma(Dcf, dX, corr);
+        }
+        const R irL = rcp(rhoL), irR = rcp(rhoR);
+        R qh = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const R dX = (Q[(QL<NS>::X + s) * n + iR] - Q[(QL<NS>::X + s) * n + iL]) * ih;
+            const R Dcf = R(0.5) * (Q[(QL<NS>::DC + s) * n + iL] + Q[(QL<NS>::DC + s) * n + iR]);
+            const R Yf = R(0.5) * ((R)U[s * n + iL] * irL + (R)U[s * n + iR] * irR);
+            const R J = fma(Yf, corr, -Dcf * dX);
+            const R hf = R(0.5) * (Q[(QL<NS>::H + s) * n + iL] + Q[(QL<NS>::H + s) * n + iR]);
+            qh = fma(J, hf, qh);
+            G[s] -= J;
+        }
+        const R q = fma(-lam, (Q[Q_T * n + iR] - Q[Q_T * n + iL]) * ih, qh);
+        R work = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G[NS + k] += tau[k];
+            work = fma(tau[k], R(0.5) * (velL[k] + velR[k]), work);
+        }
+        G[NS + 3] += work - q;
+    }
+}
+
+template <typename R, int NS, int MODE>
+__device__ __forceinline__ void cell_update(const Member &m, long long cell, const R (&dG)[NS + 4], R ih) {
+    constexpr int NV = NS + 4;
+    const long long n = m.n;
+    R *rhs = (R *)m.rhs;
+    if (MODE == MODE_ACCUM) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) rhs[v * n + cell] = fma(dG[v], ih, rhs[v * n + cell]);
+    } else if (MODE == MODE_RHS) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) m.dUdt[v * n + cell] = (double)fma(dG[v], ih, rhs[v * n + cell]);
+    } else {
+        const double dt = m.clock[1];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const double L = (double)fma(dG[v], ih, rhs[v * n + cell]);
+            const double uk = m.U[v * n + cell];
+            const double un = m.Un[v * n + cell];
+            m.Uout[v * n + cell] = fma(m.stage_a, un, m.stage_b * fma(dt, L, uk));
+        }
+    }
+}
+
+// x sweep: each block row group processes its rows in chunks of W faces; face
+// f = c W + lx goes to slot lx+1, slot 0 carries the previous chunk's last face.
+template <typename R, typename UT, int NS, int MODE>
+__global__ void __launch_bounds__(256) sweep_x_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                      int W, int rpb) {
+    constexpr int NV = NS + 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sG = (R *)smem_raw;                       // [NV][rpb][W + 1]
+    R *s0 = sG + (size_t)NV * rpb * (W + 1);     // [NV][rpb]: face 0 of each row (periodic wrap)
+    const int tid = threadIdx.x;
+    const int r = tid / W, lx = tid - r * W;
+    const int nrows = m.ny * m.nz;
+    const int row = blockIdx.x * rpb + r;
+    const bool active = r < rpb && row < nrows;
+    const int j = active ? row % m.ny : 0, k = active ? row / m.ny : 0;
+    const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
+    const R *Q = (const R *)m.Q;
+    const int nx = m.nx;
+    const bool periodic = m.bc[0] == 0;
+    const R ih = (R)m.invh[0];
+    const int nchunks = (nx + 1 + W - 1) / W;
+    auto slot = [&](int v, int s) -> R & { return sG[((size_t)v * rpb + r) * (W + 1) + s]; };
+    for (int c = 0; c < nchunks; ++c) {
+        const int f = c * W + lx;
+        if (active && (f < nx || (f == nx && !periodic))) {
+            R G[NV];
+            const int cc[3] = {f, j, k};
+            face_flux<R, UT, NS, 0>(m, U, Q, cc, G);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) slot(v, lx + 1) = G[v];
+            if (f == 0) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) s0[v * rpb + r] = G[v];
+            }
+        }
+        __syncthreads();
+        if (active && f >= 1 && f <= nx) {
+            R dG[NV];
+            const bool wrap = (f == nx && periodic);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dG[v] = (wrap ? s0[v * rpb + r] : slot(v, lx + 1)) - slot(v, lx);
+            const long long cell = ((long long)k * m.ny + j) * nx + (f - 1);
+            cell_update<R, NS, MODE>(m, cell, dG, ih);
+        }
+        __syncthreads();
+        if (active) {
+            for (int v = lx; v < NV; v += W) slot(v, 0) = slot(v, W);
+        }
+        __syncthreads();
+    }
+}
+
+// y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
+template <typename R, typename UT, int NS, int DIR, int MODE>
+__global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                         int seg) {
+    constexpr int NV = NS + 4;
+    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nd = DIR == 1 ? m.ny : m.nz;
+    const int no = DIR == 1 ? m.nz : m.ny;
+    if (line >= (long long)m.nx * no) return;
+    const int x = (int)(line % m.nx), o = (int)(line / m.nx);
+    const int c0 = blockIdx.y * seg;
+    if (c0 >= nd) return;
+    const int c1 = min(c0 + seg, nd);
+    const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
+    const R *Q = (const R *)m.Q;
+    const R ih = (R)m.invh[DIR];
+    int cc[3];
+    cc[0] = x;
+    if (DIR == 1) cc[2] = o;
+    else cc[1] = o;
+    R Gp[NV], Gn[NV];
+    cc[DIR] = c0;
+    face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gp);
+    const long long sd = DIR == 1 ? (long long)m.nx : (long long)m.nx * m.ny;
+    const long long cbase = DIR == 1 ? ((long long)o * m.ny) * m.nx + x : (long long)o * m.nx + x;
+    for (int c = c0; c < c1; ++c) {
+        cc[DIR] = c + 1;
+        face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
+        R dG[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            dG[v] = Gn[v] - Gp[v];
+            Gp[v] = Gn[v];
+        }
+        cell_update<R, NS, MODE>(m, cbase + (long long)c * sd, dG, ih);
+    }
+}
+
+// Grids with no axis longer than one cell: the RHS is the source alone.
+template <typename R, int NS, int MODE>
+__global__ void pointwise_final_kernel(const __grid_constant__ Member m) {
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= m.n) return;
+    R z[NS + 4];
+#pragma unroll
+    for (int v = 0; v < NS + 4; ++v) z[v] = 0;
+    cell_update<R, NS, MODE>(m, cell, z, R(0));
+}
+
+// ----------------------------------------------------------------------------- time step
+
+// Step prologue: clock[2] = CFL, clock[3] = fixed dt (<= 0: rule), rate maxima cleared.
+__global__ void step_params_kernel(double *clock, double cfl, double dt_fixed, unsigned long long *rates) {
+    clock[2] = cfl;
+    clock[3] = dt_fixed;
+    rates[0] = 0ull;
+    rates[1] = 0ull;
+    rates[2] = 0ull;
+}
+
+// dt = min(CFL / acoustic, 0.25 h^2 / diffusive, 0.2 / chemical, laser clamp),
+// or clock[3] if it is positive.
+__global__ void dt_kernel(double *clock, const unsigned long long *rates, double hmin, int viscous, int chem,
+                          int laser, double t0, double sigma_t, double *dt_out) {
+    double dt = clock[3];
+    if (!(dt > 0.0)) {
+        const double ac = __longlong_as_double((long long)rates[0]);
+        const double df = __longlong_as_double((long long)rates[1]);
+        const double ch = __longlong_as_double((long long)rates[2]);
+        dt = ac > 0.0 ? clock[2] / ac : 1.0e300;
+        if (viscous && df > 0.0) dt = fmin(dt, 0.25 * hmin * hmin / df);
+        if (chem && ch > 0.0) dt = fmin(dt, 0.2 / ch);
+        if (laser) {
+            const double t = clock[0];
+            const double lo = t0 - 6.0 * sigma_t, hi = t0 + 6.0 * sigma_t;
+            if (t + dt > lo && t < hi) dt = fmin(dt, fmax(0.25 * sigma_t, lo - t));
+        }
+    }
+    clock[1] = dt;
+    if (dt_out) *dt_out = dt;
+}
+
+__global__ void step_end_kernel(double *clock, double *t_out) {
+    clock[0] += clock[1];
+    if (t_out) *t_out = clock[0];
+}
+
+// ----------------------------------------------------------------------------- init state
+
+template <int NS>
+__global__ void init_state_kernel(const __grid_constant__ MechDev M, const double *__restrict__ prim, double *__restrict__ U,
+                                  double *__restrict__ Tout, long long n) {
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= n) return;
+    const double p = prim[cell], T = prim[n + cell];
+    const double u = prim[2 * n + cell], v = prim[3 * n + cell], w = prim[4 * n + cell];
+    double Y[NS], Rm = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        Y[s] = prim[(5 + s) * n + cell];
+        Rm = fma(Y[s], M.RW[s], Rm);
+    }
+    const double rho = p / (Rm * T);
+    const int rng = nasa_range(M, T);
+    const double invT = 1.0 / T;
+    double e = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        U[s * n + cell] = rho * Y[s];
+        e = fma(Y[s] * M.RW[s] * T, h_RT(M, rng, s, T, invT) - 1.0, e);
+    }
+    U[(NS + 0) * n + cell] = rho * u;
+    U[(NS + 1) * n + cell] = rho * v;
+    U[(NS + 2) * n + cell] = rho * w;
+    U[(NS + 3) * n + cell] = rho * (e + 0.5 * (u * u + v * v + w * w));
+    Tout[cell] = T;
+}
+
+// ----------------------------------------------------------------------------- diagnostics
+
+// Per-block partial sums of U_v dV, HRR dV and the block max of T; a second
+// kernel folds the partials in block order (deterministic).
+template <int NS>
+__global__ void __launch_bounds__(64) diag_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                   double *partial, int newton_maxit) {
+    constexpr int NV = NS + 4;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int B = blockDim.x, tid = threadIdx.x;
+    double *sC = (double *)smem_raw;
+    double *sG = sC + NS * B;
+    double *sW = sG + NS * B;
+    double *sD = sW + NS * B;
+    __shared__ double red[NV + 2][64];
+    const long long n = m.n, cell = (long long)blockIdx.x * B + tid;
+    const double dV = m.h[0] * m.h[1] * m.h[2];
+    double vals[NV + 2];
+#pragma unroll
+    for (int v = 0; v < NV + 2; ++v) vals[v] = 0.0;
+    if (cell < n) {
+        double rs[NS], Y[NS], rho = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rs[s] = m.U[s * n + cell];
+            rho += rs[s];
+        }
+        const double irho = 1.0 / rho;
+        const double u = m.U[NS * n + cell] * irho, v = m.U[(NS + 1) * n + cell] * irho, w = m.U[(NS + 2) * n + cell] * irho;
+        double Rm = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            Y[s] = rs[s] * irho;
+            Rm = fma(Y[s], M.RW[s], Rm);
+        }
+        const double e = m.U[(NS + 3) * n + cell] * irho - 0.5 * (u * u + v * v + w * w);
+        double T = m.T[cell];
+        if (!newton_T<NS>(M, Y, Rm, e, T, newton_maxit)) flag_error(m, ST_NEWTON, cell);
+        m.T[cell] = T;
+        const int rng = nasa_range(M, T);
+        const double invT = 1.0 / T, lnT = log(T);
+        double hs[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double hrt = h_RT(M, rng, s, T, invT);
+            hs[s] = hrt * M.RW[s] * T;
+            sC[s * B + tid] = rs[s] * M.invW[s];
+            sG[s * B + tid] = hrt - s_R(M, rng, s, T, lnT);
+            sW[s * B + tid] = 0.0;
+            sD[s * B + tid] = 0.0;
+        }
+        double hrr = 0.0;
+        if (M.nr > 0) {
+            chemistry<double, NS>(M, lnT, invT, sC + tid, sG + tid, sW + tid, sD + tid, B, false);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) hrr -= hs[s] * sW[s * B + tid] * M.W[s];
+        }
+#pragma unroll
+        for (int v2 = 0; v2 < NV; ++v2) vals[v2] = m.U[v2 * n + cell] * dV;
+        vals[NV] = hrr * dV;
+        vals[NV + 1] = T;
+    }
+#pragma unroll
+    for (int v = 0; v < NV + 2; ++v) red[v][tid] = vals[v];
+    __syncthreads();
+    if (tid < NV + 2) {
+        double acc = 0.0;
+        if (tid == NV + 1) {
+            for (int q = 0; q < B; ++q) acc = fmax(acc, red[tid][q]);
+        } else {
+            for (int q = 0; q < B; ++q) acc += red[tid][q];
+        }
+        partial[(size_t)blockIdx.x * (NV + 2) + tid] = acc;
+    }
+}
+
+__global__ void diag_fold_kernel(const double *partial, int nblocks, int nvals, double *out) {
+    const int v = threadIdx.x;
+    if (v >= nvals) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+        const double x = partial[(size_t)b * nvals + v];
+        acc = (v == nvals - 1) ? fmax(acc, x) : acc + x;
+    }
+    out[v] = acc;
+}
+
+}  // namespace rf

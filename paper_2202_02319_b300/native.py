@@ -1,0 +1,223 @@
+"""Thin Python binding of the C ABI in include/reactflow.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Functions keep the C names without the `rf_` prefix.  Device arrays are torch
+CUDA tensors (float64, contiguous) passed as raw pointers on the current torch
+stream.  If the shared library is missing, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libreactflow.so")
+
+RF_OK, RF_EINVAL, RF_ENEWTON, RF_ENONFINITE, RF_ERANGE, RF_ECUDA, RF_ETIMEOUT, RF_ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
+RF_FP64, RF_MIXED = 0, 1
+RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER = 1, 2, 4, 8
+CODE_NAMES = {0: "RF_OK", -1: "RF_EINVAL", -2: "RF_ENEWTON", -3: "RF_ENONFINITE", -4: "RF_ERANGE",
+              -5: "RF_ECUDA", -6: "RF_ETIMEOUT", -7: "RF_ENOMEM"}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"CUDA library not built: {LIB_PATH} is missing (run paper_2202_02319_b300/build.py)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class MechDesc(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int), ("n_reactions", ctypes.c_int), ("W", _dp), ("nasa_low", _dp),
+                ("nasa_high", _dp), ("T_mid", _dp), ("mu_ref", _dp), ("mu_exp", _dp), ("D_ref", _dp),
+                ("A", _dp), ("b", _dp), ("Theta", _dp), ("nu_f", _ip), ("nu_r", _ip), ("reversible", _ip)]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("dx", ctypes.c_double),
+                ("dy", ctypes.c_double), ("dz", ctypes.c_double), ("bc", ctypes.c_int * 3)]
+
+
+class Laser(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("E", "x0", "y0", "z0", "sigma_r", "t0", "sigma_t")]
+
+
+class Diag(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_double * 32), ("heat_release", ctypes.c_double), ("max_T", ctypes.c_double),
+                ("nv", ctypes.c_int)]
+
+
+_vp = ctypes.c_void_p
+_sigs = {
+    "rf_last_error": (ctypes.c_char_p, []),
+    "rf_init_mechanism": (ctypes.c_int, [ctypes.POINTER(MechDesc), ctypes.POINTER(_vp)]),
+    "rf_free_mechanism": (None, [_vp]),
+    "rf_create_ctx": (ctypes.c_int, [_vp, ctypes.POINTER(GridDesc), ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(_vp)]),
+    "rf_free_ctx": (None, [_vp]),
+    "rf_ctx_workspace_bytes": (ctypes.c_size_t, [_vp]),
+    "rf_init_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "rf_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Laser), _vp, _vp]),
+    "rf_rk_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _vp, _vp]),
+    "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
+    "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
+    "rf_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "rf_diagnostics": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Diag), _vp]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class ReactFlowError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.rf_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {CODE_NAMES.get(code, code)}: {msg}")
+
+
+def _check(code: int, where: str):
+    if code != RF_OK:
+        raise ReactFlowError(code, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    import torch
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def last_error() -> str:
+    return _lib.rf_last_error().decode(errors="replace")
+
+
+class Mechanism:
+    """Device copy of a mechanism (rf_init_mechanism / rf_free_mechanism)."""
+
+    def __init__(self, m):
+        ns, nr = m.n_species, m.n_reactions
+        keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data_as(_dp)
+
+        def i(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            keep.append(a)
+            return a.ctypes.data_as(_ip)
+        desc = MechDesc(ns, nr, d(m.W), d(m.nasa_low), d(m.nasa_high), d(m.T_mid), d(m.mu_ref), d(m.mu_exp),
+                        d(m.D_ref), d(m.A if nr else np.zeros(1)), d(m.b if nr else np.zeros(1)),
+                        d(m.Theta if nr else np.zeros(1)), i(m.nu_f if nr else np.zeros(1)),
+                        i(m.nu_r if nr else np.zeros(1)), i(m.reversible if nr else np.zeros(1)))
+        h = _vp()
+        _check(_lib.rf_init_mechanism(ctypes.byref(desc), ctypes.byref(h)), "rf_init_mechanism")
+        self.handle = h
+        self.n_species = ns
+        self.n_reactions = nr
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.rf_free_mechanism(self.handle)
+            self.handle = None
+
+
+def init_mechanism(m) -> Mechanism:
+    return Mechanism(m)
+
+
+class Context:
+    """Solver context for one grid (rf_create_ctx / rf_free_ctx)."""
+
+    def __init__(self, mech: Mechanism, grid, precision: int = RF_FP64, flags: int = 0):
+        g = GridDesc(grid.nx, grid.ny, grid.nz, grid.dx, grid.dy, grid.dz, (ctypes.c_int * 3)(*grid.bc))
+        h = _vp()
+        _check(_lib.rf_create_ctx(mech.handle, ctypes.byref(g), precision, flags, ctypes.byref(h)), "rf_create_ctx")
+        self.handle = h
+        self.mech = mech
+        self.grid = grid
+        self.precision = precision
+        self.flags = flags
+        self.n = grid.nx * grid.ny * grid.nz
+        self.nv = mech.n_species + 4
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.rf_free_ctx(self.handle)
+            self.handle = None
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(_lib.rf_ctx_workspace_bytes(self.handle))
+
+
+def create_ctx(mech: Mechanism, grid, precision: int = RF_FP64, flags: int = 0) -> Context:
+    return Context(mech, grid, precision, flags)
+
+
+def _laser(las) -> Optional[Laser]:
+    if las is None:
+        return None
+    t = las.as_tuple() if hasattr(las, "as_tuple") else tuple(las)
+    return Laser(*[float(v) for v in t])
+
+
+def init_state(ctx: Context, prim, U, T, stream=None):
+    _check(_lib.rf_init_state(ctx.handle, _ptr(prim), _ptr(U), _ptr(T), _stream(stream)), "rf_init_state")
+
+
+def rhs(ctx: Context, U, T, t: float, laser, dUdt, stream=None):
+    L = _laser(laser)
+    _check(_lib.rf_rhs(ctx.handle, _ptr(U), _ptr(T), float(t), ctypes.byref(L) if L else None, _ptr(dUdt),
+                       _stream(stream)), "rf_rhs")
+
+
+def rk_step(ctx: Context, U, T, t_dev, dt_fixed: float = 0.0, cfl: float = 0.5, laser=None, dt_dev=None, stream=None):
+    L = _laser(laser)
+    _check(_lib.rf_rk_step(ctx.handle, _ptr(U), _ptr(T), _ptr(t_dev), float(dt_fixed), float(cfl),
+                           ctypes.byref(L) if L else None, _ptr(dt_dev), _stream(stream)), "rf_rk_step")
+
+
+def set_option(ctx: Context, key: str, value: float):
+    _check(_lib.rf_set_option(ctx.handle, key.encode(), float(value)), "rf_set_option")
+
+
+PROF_CLASSES = ("cell_state", "sweep_x", "sweep_y", "sweep_z", "other")
+
+
+def profile_read(ctx: Context) -> dict:
+    """{class: (total_ms, launches)} since profiling was enabled or last read."""
+    ms = (ctypes.c_double * 5)()
+    ln = (ctypes.c_int * 5)()
+    _check(_lib.rf_profile_read(ctx.handle, ms, ln, 5), "rf_profile_read")
+    return {k: (ms[i], ln[i]) for i, k in enumerate(PROF_CLASSES)}
+
+
+def status(ctx: Context, stream=None):
+    """(code, cell) of the device-side status; clears it."""
+    cell = ctypes.c_longlong(-1)
+    code = _lib.rf_status(ctx.handle, _stream(stream), ctypes.byref(cell))
+    return code, cell.value
+
+
+def check(ctx: Context, stream=None):
+    code, _ = status(ctx, stream)
+    _check(code, "rf_status")
+
+
+def diagnostics(ctx: Context, U, T, stream=None) -> dict:
+    d = Diag()
+    _check(_lib.rf_diagnostics(ctx.handle, _ptr(U), _ptr(T), ctypes.byref(d), _stream(stream)), "rf_diagnostics")
+    return {"total": np.array(d.total[:d.nv]), "heat_release": d.heat_release, "max_T": d.max_T}

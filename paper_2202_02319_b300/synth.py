@@ -295,7 +295,8 @@ class Laser:
 @dataclass
 class Case:
     """A workload: mechanism, grid, primitive fields prim[5+Ns, nz, ny, nx] in the
-    order (p, T, u, v, w, Y_1..Y_Ns), laser and run length."""
+    order (p, T, u, v, w, Y_1..Y_Ns) (a numpy array, or a torch tensor for the
+    jet-in-a-box cases), laser and run length."""
     name: str
     mech: Mechanism
     grid: Grid
@@ -387,7 +388,7 @@ def case_mixing_layer(seed: int = 0, n: int = 512) -> Case:
     grid = Grid(n, n, 1, dx, dx, dx, (BC_PERIODIC, BC_EXTRAPOLATE, BC_PERIODIC))
     y = _centres(n, dx)
     phi = 0.5 * (1.0 + np.tanh((y - n * dx / 2) / (4.0 * dx)))            # 0 fuel -> 1 oxidiser
-    phi = np.broadcast_to(phi[None, :, None], (1, n, n))
+    phi = np.ascontiguousarray(np.broadcast_to(phi[None, :, None], (1, n, n)))
     g = stream(seed, "mix2d/noise")
     u = 50.0 * (1.0 - 2.0 * phi) + 0.5 * g.standard_normal((1, n, n))
     v = 0.5 * g.standard_normal((1, n, n))
@@ -398,36 +399,68 @@ def case_mixing_layer(seed: int = 0, n: int = 512) -> Case:
     return Case(f"mixing_layer_{n}x{n}", mech, grid, prim, Laser(), steps=200)
 
 
-def _jet_box(mech: Mechanism, seed: int, tag: str, shape, dx: float, r_jet: float,
-             turb: bool = True) -> np.ndarray:
-    nz, ny, nx = shape
-    yc, zc = ny * dx / 2, nz * dx / 2
-    Z, Yg = np.meshgrid(_centres(nz, dx), _centres(ny, dx), indexing="ij")
-    r = np.sqrt((Yg - yc) ** 2 + (Z - zc) ** 2)
-    phi = 0.5 * (1.0 - np.tanh((r - r_jet) / (2.0 * dx)))                 # 1 in the jet
-    phi = np.broadcast_to(phi[:, :, None], shape)
-    Yf = phi[None] * _fuel(mech)[:, None, None, None] + (1.0 - phi)[None] * _air(mech)[:, None, None, None]
-    u = 100.0 * phi
-    vel = [u.copy(), np.zeros(shape), np.zeros(shape)]
-    if turb:
-        ke = 1.0 / (r_jet / dx)                      # in grid wavenumber units of 2 pi / (n dx)
-        kscale = 2.0 * np.pi / np.array(shape).min()
+def _torch_gen(seed: int, name: str, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(zlib.crc32(f"{int(seed)}/{name}".encode()))
+    return g
 
-        def vk(k):
-            kk = k * kscale
-            return kk ** 4 / (1.0 + (kk / ke) ** 2) ** (17.0 / 6.0)
-        t = _solenoidal(stream(seed, tag + "/turb"), shape, lambda k: k > 0, vk)
-        rms = np.sqrt(np.mean(t[0] ** 2 + t[1] ** 2 + t[2] ** 2) / 3.0)
+
+def _jet_box(mech: Mechanism, seed: int, tag: str, shape, dx: float, r_jet: float,
+             turb: bool = True, device=None):
+    """Jet-in-a-box primitive fields as a float64 torch tensor [5+Ns, nz, ny, nx] on
+    `device` (default CPU): fuel jet along x of radius r_jet (tanh edge, 2 cells),
+    air-like oxidiser, p = 1 atm, T = 300 K, plus a von Karman turbulence field
+    E(k) ~ k^4 / (1 + (k/k_e)^2)^(17/6), k_e = 1/r_jet, solenoidal, rms 5 m/s per
+    component.  Random numbers come from torch's generator on `device`, seeded by
+    (seed, tag), so a case is reproducible on the device that generated it."""
+    import torch
+    dev = torch.device(device if device is not None else "cpu")
+    f64 = torch.float64
+    nz, ny, nx = shape
+    zc = (torch.arange(nz, device=dev, dtype=f64) + 0.5) * dx - nz * dx / 2
+    yc = (torch.arange(ny, device=dev, dtype=f64) + 0.5) * dx - ny * dx / 2
+    r = torch.sqrt(yc[None, :] ** 2 + zc[:, None] ** 2)
+    phi2 = 0.5 * (1.0 - torch.tanh((r - r_jet) / (2.0 * dx)))            # [nz, ny], 1 in the jet
+    prim = torch.empty((5 + mech.n_species,) + tuple(shape), dtype=f64, device=dev)
+    phi = phi2[:, :, None].expand(shape)
+    prim[0].fill_(P_ATM)
+    prim[1].fill_(300.0)
+    prim[2].copy_(100.0 * phi)
+    prim[3].zero_()
+    prim[4].zero_()
+    fu, ox = _fuel(mech), _air(mech)
+    for s_ in range(mech.n_species):
+        prim[5 + s_].copy_(phi * float(fu[s_]) + (1.0 - phi) * float(ox[s_]))
+    if turb:
+        g = _torch_gen(seed, tag + "/turb", dev)
+        kz = torch.fft.fftfreq(nz, device=dev, dtype=f64) * nz
+        ky = torch.fft.fftfreq(ny, device=dev, dtype=f64) * ny
+        kx = torch.fft.rfftfreq(nx, device=dev, dtype=f64) * nx
+        KZ, KY, KX = kz[:, None, None], ky[None, :, None], kx[None, None, :]
+        k2 = KX ** 2 + KY ** 2 + KZ ** 2
+        k = torch.sqrt(k2)
+        ke = 1.0 / (r_jet / dx)
+        kk = k * (2.0 * np.pi / min(shape))
+        spec = kk ** 4 / (1.0 + (kk / ke) ** 2) ** (17.0 / 6.0)
+        amp = torch.where(k > 0, torch.sqrt(spec / (4 * np.pi * torch.clamp(k2, min=1e-30))), torch.zeros_like(k))
+        cshape = k.shape
+        a = [torch.complex(torch.randn(cshape, generator=g, device=dev, dtype=f64),
+                           torch.randn(cshape, generator=g, device=dev, dtype=f64)) * amp for _ in range(3)]
+        kd = (KX * a[0] + KY * a[1] + KZ * a[2]) / torch.where(k2 > 0, k2, torch.ones_like(k2))
+        a = [a[0] - KX * kd, a[1] - KY * kd, a[2] - KZ * kd]
+        t = [torch.fft.irfftn(c, s=tuple(shape), dim=(0, 1, 2)) for c in a]
+        del a, kd
+        rms = torch.sqrt((t[0] ** 2 + t[1] ** 2 + t[2] ** 2).mean() / 3.0)
         for i in range(3):
-            vel[i] = vel[i] + t[i] * (5.0 / rms)
-    return np.concatenate([np.full((1,) + shape, P_ATM), np.full((1,) + shape, 300.0),
-                           *(v[None] for v in vel), Yf])
+            prim[2 + i].add_(t[i] * (5.0 / rms))
+    return prim
 
 
 JET_DX = 3.0e-4     # m; places the configs' 5-40 mJ, 3-cell laser kernels at 1000-4500 K
 
 
-def case_jet(seed: int = 0, n: int = 256) -> Case:
+def case_jet(seed: int = 0, n: int = 256, device=None) -> Case:
     """3-D jet in a periodic box n^3: fuel jet (X2) of radius 16 n/256 cells (at
     least 2) along x at 100 m/s into quiescent air-like oxidiser at 1 atm and
     300 K, von Karman turbulence at 5 % of 100 m/s, and a 20 mJ Gaussian laser
@@ -436,7 +469,7 @@ def case_jet(seed: int = 0, n: int = 256) -> Case:
     dx = JET_DX
     r_jet = max(2, (16 * n) // 256) * dx
     grid = Grid(n, n, n, dx, dx, dx)
-    prim = _jet_box(mech, seed, f"jet{n}", (n, n, n), dx, r_jet)
+    prim = _jet_box(mech, seed, f"jet{n}", (n, n, n), dx, r_jet, device=device)
     g = stream(seed, f"jet{n}/laser")
     th = g.uniform(0.0, 2.0 * np.pi)
     las = Laser(E=20e-3, x0=g.uniform(0.25, 0.75) * n * dx,
@@ -446,7 +479,7 @@ def case_jet(seed: int = 0, n: int = 256) -> Case:
 
 
 def ensemble_members(seed: int = 0, n_members: int = 64, lo: int = 48, hi: int = 96,
-                     t0_max: float = 50e-6) -> List[Case]:
+                     t0_max: float = 50e-6, device=None) -> List[Case]:
     """Batched-ensemble workload: each member a jet-in-a-box with every axis drawn
     from U{lo..hi}, jet radius min(ny, nz)/8 cells, laser energy U[5, 40] mJ at a
     point on the shear layer, deposition time U[0, t0_max]."""
@@ -457,7 +490,7 @@ def ensemble_members(seed: int = 0, n_members: int = 64, lo: int = 48, hi: int =
     for m in range(n_members):
         nx, ny, nz = (int(v) for v in g.integers(lo, hi + 1, size=3))
         r_jet = max(2, min(ny, nz) // 8) * dx
-        prim = _jet_box(mech, seed, f"ensemble/{m}", (nz, ny, nx), dx, r_jet)
+        prim = _jet_box(mech, seed, f"ensemble/{m}", (nz, ny, nx), dx, r_jet, device=device)
         th = g.uniform(0.0, 2.0 * np.pi)
         las = Laser(E=g.uniform(5e-3, 40e-3), x0=g.uniform(0.25, 0.75) * nx * dx,
                     y0=ny * dx / 2 + r_jet * np.cos(th), z0=nz * dx / 2 + r_jet * np.sin(th),

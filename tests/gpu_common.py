@@ -1,0 +1,63 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path and the oracle on
+the same seeded inputs and compare."""
+import numpy as np
+import torch
+
+import oracle
+from oracle.mech import from_synth, grid_from_synth
+
+F64 = torch.float64
+
+
+def prim_tensor(case):
+    return torch.as_tensor(case.prim, dtype=F64).cpu().contiguous()
+
+
+def gpu_setup(case, precision=0, flags=0, options=None):
+    from paper_2202_02319_b300 import native as nv
+    mech = nv.init_mechanism(case.mech)
+    ctx = nv.create_ctx(mech, case.grid, precision, flags)
+    for k, v in (options or {}).items():
+        nv.set_option(ctx, k, v)
+    ns = case.mech.n_species
+    n = case.grid.ncells
+    prim = prim_tensor(case).reshape(5 + ns, n).cuda()
+    U = torch.empty((ns + 4, n), dtype=F64, device="cuda")
+    T = torch.empty(n, dtype=F64, device="cuda")
+    nv.init_state(ctx, prim, U, T)
+    nv.check(ctx)
+    return mech, ctx, U, T
+
+
+def oracle_setup(case):
+    mt = from_synth(case.mech)
+    g = grid_from_synth(case.grid)
+    U, T = oracle.rhs.init_state(mt, prim_tensor(case))
+    return mt, g, U, T
+
+
+def oracle_flags(flags):
+    from paper_2202_02319_b300 import native as nv
+    return {"inviscid": not (flags & nv.RF_NO_INVISCID), "viscous": not (flags & nv.RF_NO_VISCOUS),
+            "chemistry": not (flags & nv.RF_NO_CHEMISTRY), "laser": not (flags & nv.RF_NO_LASER)}
+
+
+def rel_inf(a, b):
+    """Per-variable ||a_v - b_v||_inf / ||b_v||_inf (0/0 -> 0), as a numpy vector."""
+    a = a.reshape(a.shape[0], -1).double().cpu()
+    b = b.reshape(b.shape[0], -1).double().cpu()
+    num = (a - b).abs().amax(1)
+    den = b.abs().amax(1)
+    return torch.where(den > 0, num / torch.where(den > 0, den, torch.ones_like(den)), num).numpy()
+
+
+def rel_l2(a, b):
+    a = a.reshape(a.shape[0], -1).double().cpu()
+    b = b.reshape(b.shape[0], -1).double().cpu()
+    num = (a - b).norm(dim=1)
+    den = b.norm(dim=1)
+    return torch.where(den > 0, num / torch.where(den > 0, den, torch.ones_like(den)), num).numpy()
+
+
+def laser_tuple(case):
+    return case.laser.as_tuple() if case.laser.E > 0 else None

@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports every entry point its header declares, and
+its host-side argument checks reject bad input before any device work.  No
+compute call is made here (this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2202_02319_b300 import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(rf_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2202_02319_b300 import native
+    lib = ctypes.CDLL(native.LIB_PATH)
+    names = _declared()
+    assert len(names) >= 10
+    missing = [n for n in sorted(names) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_argument_checks():
+    from paper_2202_02319_b300 import native as nv
+    m = synth.mechanism_4sp(0)
+    mech = nv.init_mechanism(m)                    # host-only packing, no device call
+    assert mech.n_species == 4
+    bad = synth.mechanism_4sp(0)
+    bad.W = bad.W.copy()
+    bad.W[1] = -1.0
+    with pytest.raises(nv.ReactFlowError) as e:
+        nv.init_mechanism(bad)
+    assert e.value.code == nv.RF_EINVAL
+    # five species: not a supported species count
+    five = synth.Mechanism(["A"] * 5, np.full(5, 0.02), np.ones((5, 1)), np.zeros((5, 7)), np.zeros((5, 7)),
+                           np.full(5, 1000.0), np.full(5, 2e-5), np.full(5, 0.7), np.full((5, 5), 2e-5),
+                           np.zeros(0), np.zeros(0), np.zeros(0), np.zeros((0, 5), dtype=np.int64),
+                           np.zeros((0, 5), dtype=np.int64), np.zeros(0, dtype=np.int32))
+    with pytest.raises(nv.ReactFlowError):
+        nv.init_mechanism(five)
+    # grid checks happen before any allocation
+    for g in (synth.Grid(0, 4, 4, 1e-4, 1e-4, 1e-4), synth.Grid(2048, 1, 1, 1e-4, 1e-4, 1e-4),
+              synth.Grid(4, 4, 4, -1.0, 1e-4, 1e-4), synth.Grid(4, 4, 4, 1e-4, 1e-4, 1e-4, (0, 7, 0))):
+        with pytest.raises(nv.ReactFlowError) as e:
+            nv.create_ctx(mech, g)
+        assert e.value.code == nv.RF_EINVAL
+    # more than three molecules on one side of a reaction
+    m2 = synth.mechanism_4sp(0)
+    m2.nu_f = m2.nu_f.copy()
+    m2.nu_f[0, 0] = 4
+    with pytest.raises(nv.ReactFlowError):
+        nv.init_mechanism(m2)
