@@ -50,9 +50,10 @@ def rate_limits(mech, grid, U, T0, flags=None):
 
 def time_step(mech, grid, U, T0, t: float, las, cfl: float, flags=None) -> float:
     ac, dmax, ch = rate_limits(mech, grid, U, T0, flags)
-    dt = cfl / ac
-    if _flag(flags, "viscous"):
-        hmin = min(grid.h[d] for d in range(3) if grid.n[d] > 1)
+    dt = cfl / ac if ac > 0.0 else 1.0e300
+    active = [grid.h[d] for d in range(3) if grid.n[d] > 1]
+    if _flag(flags, "viscous") and active and dmax > 0.0:
+        hmin = min(active)
         dt = min(dt, 0.25 * hmin * hmin / dmax)
     if _flag(flags, "chemistry") and ch > 0.0:
         dt = min(dt, 0.2 / ch)

@@ -281,16 +281,24 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
 
 // ----------------------------------------------------------------------------- face flux
 
+// WENO3-Z value at i+1/2 from (f_{i-1}, f_i, f_{i+1}) with d = (1/3, 2/3), p = 1.
+// The Z weights alpha_k = d_k (1 + tau / (beta_k + eps)) are formed after
+// multiplying both by (beta_0 + eps)(beta_1 + eps) / S^2, S = beta_0 + beta_1 + 2 eps:
+// omega_0 = d0 b1 (b0 + t) / (d0 b1 (b0 + t) + d1 b0 (b1 + t)) with b_k = (beta_k + eps) / S,
+// t = tau / S.  Every scaled quantity lies in [0, 2], so the weights cannot overflow
+// even in FP32, where tau / (beta + 1e-30) would for any |f_{i+1} - f_i| above ~2e4.
 template <typename R>
 __device__ __forceinline__ R weno3z(R a, R b, R c) {
     const R q0 = fma(R(-0.5), a, R(1.5) * b);
     const R q1 = R(0.5) * b + R(0.5) * c;
     const R d0 = b - a, d1 = c - b;
     const R beta0 = d0 * d0, beta1 = d1 * d1;
-    const R tau = fabs(beta1 - beta0);
-    const R al0 = R(1.0 / 3.0) * fma(tau, rcp(beta0 + R(EPS_WENO)), R(1));
-    const R al1 = R(2.0 / 3.0) * fma(tau, rcp(beta1 + R(EPS_WENO)), R(1));
-    return fma(al0, q0, al1 * q1) * rcp(al0 + al1);
+    const R iS = rcp(beta0 + beta1 + R(2.0 * EPS_WENO));
+    const R b0 = (beta0 + R(EPS_WENO)) * iS, b1 = (beta1 + R(EPS_WENO)) * iS;
+    const R t = fabs(beta1 - beta0) * iS;
+    const R a0 = R(1.0 / 3.0) * b1 * (b0 + t);
+    const R a1 = R(2.0 / 3.0) * b0 * (b1 + t);
+    return fma(a0, q0, a1 * q1) * rcp(a0 + a1);
 }
 
 // Flux G = -Fhat^a + F^d at the face between cells (coord-1) and coord along DIR.
@@ -512,20 +520,21 @@ __global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__
     if (DIR == 1) cc[2] = o;
     else cc[1] = o;
     R Gp[NV], Gn[NV];
-    cc[DIR] = c0;
-    face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gp);
     const long long sd = DIR == 1 ? (long long)m.nx : (long long)m.nx * m.ny;
     const long long cbase = DIR == 1 ? ((long long)o * m.ny) * m.nx + x : (long long)o * m.nx + x;
-    for (int c = c0; c < c1; ++c) {
+    // one call site of face_flux, so every face is computed by the same code
+    // whichever segment computes it (bitwise independence of the segmentation)
+    for (int c = c0 - 1; c < c1; ++c) {
         cc[DIR] = c + 1;
         face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
-        R dG[NV];
+        if (c >= c0) {
+            R dG[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            dG[v] = Gn[v] - Gp[v];
-            Gp[v] = Gn[v];
+            for (int v = 0; v < NV; ++v) dG[v] = Gn[v] - Gp[v];
+            cell_update<R, NS, MODE>(m, cbase + (long long)c * sd, dG, ih);
         }
-        cell_update<R, NS, MODE>(m, cbase + (long long)c * sd, dG, ih);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
     }
 }
 

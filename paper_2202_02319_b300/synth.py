@@ -348,8 +348,10 @@ def _sound_speed(mech: Mechanism, Y: np.ndarray, T: np.ndarray) -> np.ndarray:
 
 def case_box32(seed: int = 0) -> Case:
     """32^3 periodic box, 4 species, constant cp: T = 300 K plus a Gaussian hot kernel
-    peaking at 1500 K (sigma 4 cells), Y ~ Dirichlet(1,1,1,1) per cell, random
-    solenoidal Fourier modes |k| <= 4 scaled to max |u|/c = 0.3, p = 1 atm."""
+    peaking at 1500 K (sigma 4 cells), mass fractions from one Dirichlet(1,1,1,1) draw
+    modulated by +-50 % smooth random modes |k| <= 4 (a per-cell draw would be
+    grid-scale white noise), random solenoidal Fourier modes |k| <= 4 scaled to
+    max |u|/c = 0.3, p = 1 atm."""
     mech = mechanism_4sp(seed)
     n, dx = 32, 1.0e-4
     grid = Grid(n, n, n, dx, dx, dx)
@@ -358,7 +360,13 @@ def case_box32(seed: int = 0) -> Case:
     c = n * dx / 2
     r2 = (X - c) ** 2 + (Y_ - c) ** 2 + (Z - c) ** 2
     T = 300.0 + 1200.0 * np.exp(-r2 / (2 * (4 * dx) ** 2))
-    Yf = stream(seed, "box32/Y").dirichlet(np.ones(4), size=(n, n, n)).transpose(3, 0, 1, 2)
+    gY = stream(seed, "box32/Y")
+    base = gY.dirichlet(np.ones(4))
+    w = np.empty((4, n, n, n))
+    for s_ in range(4):
+        phi = _solenoidal(gY, (n, n, n), lambda k: (k > 0) & (k <= 4.0))[0]
+        w[s_] = base[s_] * (1.0 + 0.5 * phi / np.abs(phi).max())
+    Yf = w / w.sum(0)
     u = _solenoidal(stream(seed, "box32/u"), (n, n, n), lambda k: (k > 0) & (k <= 4.0))
     umag = np.sqrt(u[0] ** 2 + u[1] ** 2 + u[2] ** 2)
     scale = 0.3 / np.max(umag / _sound_speed(mech, Yf, T))

@@ -61,3 +61,16 @@ def rel_l2(a, b):
 
 def laser_tuple(case):
     return case.laser.as_tuple() if case.laser.E > 0 else None
+
+
+def state_rel_l2(a, b, ns):
+    """Relative L2 error of a conserved state, per variable, each scaled by the norm
+    of its group: species densities by ||rho||, momentum components by ||rho |u|||,
+    energy by ||E||.  (A per-species norm would divide by the near-zero densities
+    of species a run has not produced yet.)"""
+    a = a.reshape(a.shape[0], -1).double().cpu()
+    b = b.reshape(b.shape[0], -1).double().cpu()
+    rho = b[:ns].sum(0).norm()
+    mom = b[ns:ns + 3].norm(dim=0).norm()
+    scale = torch.cat([rho.repeat(ns), mom.repeat(3), b[ns + 3].norm().reshape(1)])
+    return ((a - b).norm(dim=1) / scale).numpy()

