@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <type_traits>
@@ -606,5 +607,91 @@ extern "C" int rf_status(rf_ctx *c, rf_stream s, long long *cell_out) {
     if (st & ST_NEWTON) return fail(RF_ENEWTON, "temperature Newton solve did not converge at cell %lld", cell);
     if (st & ST_RANGE) return fail(RF_ERANGE, "temperature or density out of range at cell %lld", cell);
     if (st & ST_TIMEOUT) return fail(RF_ETIMEOUT, "a bounded device wait gave up");
+    return RF_OK;
+}
+
+// ----------------------------------------------------------------------------- allocation-free RHS
+
+// Scratch of rf_rhs_noalloc: a file-scope device array, so the entry point never
+// allocates.  Each GPU that loads this library holds these bytes until the
+// process exits.  In host code `g_noalloc_scratch` names a host-side stand-in,
+// not the device array: its device address is looked up once per device with
+// cudaGetSymbolAddress and passed to the kernels.
+static constexpr size_t RF_NOALLOC_BYTES = (size_t)16 << 20;
+static constexpr size_t RF_NOALLOC_HEADER = 256;   // status, bad cell, clock, rate maxima
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RF_NOALLOC_BYTES];
+static constexpr int RF_NOALLOC_MAX_DEVICES = 64;
+static unsigned char *g_noalloc_dev[RF_NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mutex;
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static int noalloc_rhs_dispatch(rf_ctx *c, const double *U, double *T, double t, const rf_laser *L, double *dUdt,
+                                cudaStream_t s) {
+    DISPATCH(c, rhs(c, U, T, t, L, dUdt, s));
+}
+
+extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int precision, uint32_t flags, const double *U,
+                              double *T, double t, const rf_laser *L, double *dUdt, rf_stream s) {
+    if (!m || !g || !U || !T || !dUdt) return fail(RF_EINVAL, "rf_rhs_noalloc: null argument");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(RF_EINVAL, "rf_rhs_noalloc: grid %dx%dx%d has an empty axis", g->nx, g->ny, g->nz);
+    if (g->nx > 1024) return fail(RF_EINVAL, "rf_rhs_noalloc: nx = %d exceeds 1024", g->nx);
+    if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return fail(RF_EINVAL, "rf_rhs_noalloc: grid spacing must be > 0");
+    for (int a = 0; a < 3; ++a)
+        if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_rhs_noalloc: bc[%d] = %d unknown", a, g->bc[a]);
+    if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_rhs_noalloc: precision %d unknown", precision);
+    const long long n = (long long)g->nx * g->ny * g->nz;
+    const int ns = m->ns, nv = ns + 4, nq = Q_X0 + 3 * ns;
+    const size_t rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);
+    const size_t bq = align256((size_t)n * nq * rsize), br = align256((size_t)n * nv * rsize);
+    const size_t b32 = precision == RF_MIXED ? align256((size_t)n * nv * sizeof(float)) : 0;
+    const size_t need = RF_NOALLOC_HEADER + bq + br + b32;
+    if (need > RF_NOALLOC_BYTES)
+        return fail(RF_EINVAL, "rf_rhs_noalloc: grid of %lld cells needs %zu scratch bytes, more than the %zu-byte maximum",
+                    n, need, RF_NOALLOC_BYTES);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= RF_NOALLOC_MAX_DEVICES) return fail(RF_EINVAL, "rf_rhs_noalloc: device %d out of range", dev);
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_dev[dev]) {
+            void *p = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_dev[dev] = (unsigned char *)p;
+        }
+        base = g_noalloc_dev[dev];
+    }
+    cudaStream_t st = (cudaStream_t)s;
+    // the header persists between calls: clear the status word, reset the bad-cell index
+    CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(int) * 2, st));
+    CUDA_TRY(cudaMemsetAsync(base + 8, 0xff, sizeof(long long), st));
+    rf_ctx c;                                  // descriptor only: every buffer points into the scratch
+    c.mech = m;
+    c.g = *g;
+    c.precision = precision;
+    c.flags = flags;
+    c.n = n;
+    c.ns = ns;
+    c.nv = nv;
+    c.nq = nq;
+    c.rsize = rsize;
+    c.status = (int *)base;
+    c.bad_cell = (long long *)(base + 8);
+    c.clock = (double *)(base + 64);
+    c.rates = (unsigned long long *)(base + 128);
+    c.Q = base + RF_NOALLOC_HEADER;
+    c.rhs = base + RF_NOALLOC_HEADER + bq;
+    c.U32 = precision == RF_MIXED ? (float *)(base + RF_NOALLOC_HEADER + bq + br) : nullptr;
+    int rc = noalloc_rhs_dispatch(&c, U, T, t, L, dUdt, st);
+    if (rc) return rc;
+    int status = 0;
+    long long cell = -1;
+    CUDA_TRY(cudaMemcpyAsync(&status, base, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaMemcpyAsync(&cell, base + 8, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (status & ST_NONFINITE) return fail(RF_ENONFINITE, "non-finite state at cell %lld", cell);
+    if (status & ST_NEWTON) return fail(RF_ENEWTON, "temperature Newton solve did not converge at cell %lld", cell);
+    if (status & ST_RANGE) return fail(RF_ERANGE, "temperature or density out of range at cell %lld", cell);
     return RF_OK;
 }
