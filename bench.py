@@ -110,6 +110,16 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
     return b + nv * rsize + 3 * nv * 8
 
 
+# Counts of the mixed-precision cell-state kernel (9 species, 19 reactions) from one
+# ncu capture of the 96^3 case (profiles/cell_state_mixed_jet96.md):
+# FP64 FLOP = 2 DFMA + DMUL + DADD thread instructions, DRAM = dram__bytes_read.sum +
+# dram__bytes_write.sum, both per cell (traffic grows with the cell count, so a
+# full 256^3 launch is the per-cell figure times 256^3).  None until captured for
+# the current kernel.
+CELL_STATE_MIXED_FP64_FLOP_PER_CELL = None
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = None
+
+
 def cell_state_bytes(ns: int, rsize: int) -> int:
     """Reads U (FP64) and T, writes T, the Q fields, the RHS source and (mixed) the FP32 copy of U."""
     nv = ns + 4
@@ -237,6 +247,8 @@ def run_ours(args):
 
     # --- roofline of the dominant kernel of the mixed step
     peaks = _peaks()
+    fp64_peak = nv.probe_peak(0)
+    fp32_peak = nv.probe_peak(1)
     tot = {k: v[0] for k, v in prof.items()}
     dom = max(("cell_state", "sweep_x", "sweep_y", "sweep_z"), key=lambda k: tot[k])
     kernels = {}
@@ -260,9 +272,18 @@ def run_ours(args):
         if nl:
             k64[k] = {"ms_per_launch": round(ms_k / nl, 4), "share": round(ms_k / sum(v[0] for v in prof64.values()), 4)}
     d = kernels[dom]
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,
-                "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
+    if dom == "cell_state" and CELL_STATE_MIXED_FP64_FLOP_PER_CELL:
+        ms_k = prof["cell_state"][0] / prof["cell_state"][1]
+        ach = CELL_STATE_MIXED_FP64_FLOP_PER_CELL * ncell / (ms_k * 1e-3) / 1e12
+        traffic = (CELL_STATE_MIXED_DRAM_BYTES_PER_CELL * ncell) if CELL_STATE_MIXED_DRAM_BYTES_PER_CELL else None
+        roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4), "traffic": traffic,
+                    "peak_source": "FP64 FMA rate measured in this run (rf_probe_peak)",
+                    "flop_per_cell": CELL_STATE_MIXED_FP64_FLOP_PER_CELL}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
+                    "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,
+                    "peak_source": peaks["source"] + " (MEASURED_PEAKS.json hbm_gbs)"}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -276,6 +297,8 @@ def run_ours(args):
                  "kernels": k64},
         "kernels": kernels,
         "roofline": roofline,
+        "peaks_measured": {"fp64_tflops": round(fp64_peak, 4), "fp32_tflops": round(fp32_peak, 3),
+                           "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps},
         "gpu_launches": launches_per_step * args.steps,

@@ -187,6 +187,11 @@ int rf_status(rf_ctx *c, rf_stream s, long long *cell_out);
  * state U (with T as Newton warm start).  Synchronous (result on the host). */
 int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s);
 
+/* Measures the FMA throughput of the current device (kind 0: FP64, 1: FP32)
+ * with independent FMA chains on every SM; *tflops receives 2 x FMAs / s / 1e12.
+ * Synchronous.  The FP64 figure is the ALU roofline of the cell-state kernel. */
+int rf_probe_peak(int kind, double *tflops, rf_stream s);
+
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Computes the same dU/dt as rf_rhs for a
  * mechanism and grid without a context, for callers that cannot allocate device

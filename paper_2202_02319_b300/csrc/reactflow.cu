@@ -161,7 +161,15 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             M.sc[r][s][3] = a[3] / 3.0;
             M.sc[r][s][4] = a[4] / 4.0;
             M.sc[r][s][5] = a[6];
+            M.gc[r][s][0] = a[0] - a[6];
+            M.gc[r][s][1] = -a[1] / 2.0;
+            M.gc[r][s][2] = -a[2] / 6.0;
+            M.gc[r][s][3] = -a[3] / 12.0;
+            M.gc[r][s][4] = -a[4] / 20.0;
+            M.gc[r][s][5] = a[5];
+            M.gc[r][s][6] = -a[0];
             for (int k = 0; k < 5; ++k) M.cpcf[r][s][k] = (float)a[k];
+            for (int k = 0; k < 6; ++k) M.ecf[r][s][k] = (float)M.ec[r][s][k];
         }
         M.mu_ref[s] = d->mu_ref[s];
         M.mu_exp[s] = d->mu_exp[s];
@@ -365,7 +373,7 @@ struct Path {
     static int cell_state(rf_ctx *c, const Member &m, cudaStream_t s) {
         const int B = 128;
         const long long nb = (c->n + B - 1) / B;
-        const size_t smem = (size_t)B * NS * (2 * sizeof(double) + 2 * sizeof(R));
+        const size_t smem = (size_t)B * NS * (3 * sizeof(double) + 2 * sizeof(R) + (sizeof(R) == 4 ? sizeof(R) : 0));
         ProfScope ps(c, PROF_CELL, s);
         cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mech->d, m, c->newton_maxit);
         LAUNCH_CHECK();
@@ -491,7 +499,7 @@ struct Path {
         m.U = U;
         m.T = T;
         const int B = 64;
-        const size_t smem = (size_t)B * NS * 4 * sizeof(double);
+        const size_t smem = (size_t)B * NS * 5 * sizeof(double);
         diag_kernel<NS><<<c->diag_blocks, B, smem, s>>>(c->mech->d, m, c->diag, c->newton_maxit);
         LAUNCH_CHECK();
         const int nvals = NS + 6;
@@ -607,6 +615,51 @@ extern "C" int rf_status(rf_ctx *c, rf_stream s, long long *cell_out) {
     if (st & ST_NEWTON) return fail(RF_ENEWTON, "temperature Newton solve did not converge at cell %lld", cell);
     if (st & ST_RANGE) return fail(RF_ERANGE, "temperature or density out of range at cell %lld", cell);
     if (st & ST_TIMEOUT) return fail(RF_ETIMEOUT, "a bounded device wait gave up");
+    return RF_OK;
+}
+
+// ----------------------------------------------------------------------------- peak probe
+
+// Eight independent FMA chains per thread on every SM: the issue-limited FMA rate
+// of the type, the ALU roofline of the FP64-bound cell-state kernel.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_probe_kernel(T *out, int iters, T b, T c) {
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += a[k];
+    if (sum == (T)-1.25) out[0] = sum;        // keeps the chains live; never true
+}
+
+extern "C" int rf_probe_peak(int kind, double *tflops, rf_stream s) {
+    if (!tflops || (kind != 0 && kind != 1)) return fail(RF_EINVAL, "rf_probe_peak: bad argument");
+    int dev = 0, sms = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8, threads = 256;
+    const int iters = kind == 0 ? 2048 : 65536;
+    cudaStream_t st = (cudaStream_t)s;
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {        // first launch warms up
+        CUDA_TRY(cudaEventRecord(e0, st));
+        if (kind == 0) fma_probe_kernel<double><<<blocks, threads, 0, st>>>(nullptr, iters, 0.9999999, 1e-9);
+        else fma_probe_kernel<float><<<blocks, threads, 0, st>>>(nullptr, iters, 0.9999999f, 1e-9f);
+        CUDA_TRY(cudaEventRecord(e1, st));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
     return RF_OK;
 }
 

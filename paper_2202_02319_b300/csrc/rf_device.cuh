@@ -31,6 +31,8 @@ struct MechDev {
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
     double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
     double sc[2][NSMAX][6];                    // a1 (x lnT), a2, a3/2, a4/3, a5/4, a7
+    double gc[2][NSMAX][7];                    // g/RT = gc0 + T(gc1 + T(gc2 + T(gc3 + T gc4))) + gc5/T + gc6 lnT
+    float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
     double invDref[NSMAX][NSMAX];
     double wc[NSMAX][NSMAX];                   // (W_j / W_i)^(1/4)
@@ -169,7 +171,9 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
         }
         const double e = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), P.e[5]);
         const double cv = fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
-        const double dT = (e - e_target) / cv;
+        // The root is fixed by e(T) = e_target alone; an FP32 reciprocal of cv only
+        // perturbs the convergence rate (by ~1e-7 per step), not the converged T.
+        const double dT = (e - e_target) * (double)__frcp_rn((float)cv);
         T = T - dT;
         if (fabs(dT) <= 1.0e-13 * fabs(T)) return true;
     }
@@ -188,6 +192,21 @@ __device__ __forceinline__ double h_RT(const MechDev &M, int r, int s, double T,
 __device__ __forceinline__ double s_R(const MechDev &M, int r, int s, double T, double lnT) {
     const double *c = M.sc[r][s];
     return fma(c[0], lnT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[5]));
+}
+
+// g_s/RT = h_s/RT - s_s/R of species s in one Horner pass.
+__device__ __forceinline__ double g_RT(const MechDev &M, int r, int s, double T, double invT, double lnT) {
+    const double *c = M.gc[r][s];
+    return fma(c[6], lnT, fma(c[5], invT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[0])));
+}
+
+// h_s/RT in the bulk type.
+__device__ __forceinline__ float h_RT_bulk(const MechDev &M, int r, int s, float T, float invT) {
+    const float *c = M.ecf[r][s];
+    return fmaf(T, fmaf(T, fmaf(T, fmaf(T, c[4], c[3]), c[2]), c[1]), c[0]) + c[5] * invT;
+}
+__device__ __forceinline__ double h_RT_bulk(const MechDev &M, int r, int s, double T, double invT) {
+    return h_RT(M, r, s, T, invT);
 }
 
 template <typename R>

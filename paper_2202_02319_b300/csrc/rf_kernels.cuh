@@ -33,61 +33,64 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) 
 
 // ----------------------------------------------------------------------------- chemistry
 
-// Reversible mass-action rates.  C (FP64 concentrations) and G (FP64 g_s/RT)
-// live in per-thread shared-memory columns (stride = block size) so that the
-// compact stoichiometry can index species at run time; omega is accumulated in
-// the same way.  If want_rate, returns max_s |d omega_s / d rho_s|.
+// Reversible mass-action rates.  Per-species inputs sit in per-thread
+// shared-memory columns (stride = block size) so the compact stoichiometry can
+// index species at run time:
+//   sC  = C_s (FP64), sCb = C_s in the bulk type,
+//   sP  = C_s G_s and sRr = 1 / G_s (FP64), G_s = exp(g_s/RT) R T / p_atm,
+// so that k_f / K_c,j * prod_s C_s^nu''_sj = k_f prod_prod (C G)_s prod_reac (1/G)_s,
+// i.e. the equilibrium constant costs one FP64 exponential per species rather than
+// per reaction, and the reverse rate stays in FP64.  sW accumulates
+// sum_j nu_sj q_j in the bulk type.  If want_rate, sD accumulates the diagonal of
+// d omega / d C and the function returns max_s |d omega_s / d rho_s|.
 template <typename R, int NS>
 __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT, const double *__restrict__ sC,
-                                       const double *__restrict__ sG, R *__restrict__ sW, R *__restrict__ sD,
+                                       const R *__restrict__ sCb, const double *__restrict__ sP,
+                                       const double *__restrict__ sRr, R *__restrict__ sW, R *__restrict__ sD,
                                        int stride, bool want_rate) {
-    const double lnRTp = lnT + log(RU / PATM);    // ln(R T / p_atm)
+    const R lnTb = (R)lnT, invTb = (R)invT;
     for (int j = 0; j < M.nr; ++j) {
-        double kf;
-        if (sizeof(R) == 8) {
-            kf = exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
-        } else {
-            const float lnTf = (float)lnT, invTf = (float)invT;
-            kf = (double)expf(M.lnAf[j] + M.bf[j] * lnTf - M.Thetaf[j] * invTf);
-        }
+        R kf;
+        if (sizeof(R) == 8) kf = (R)exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
+        else kf = (R)expf(M.lnAf[j] + M.bf[j] * (float)lnTb - M.Thetaf[j] * (float)invTb);
         const int nrc = M.n_reac[j], npd = M.n_prod[j];
-        double cf = 1.0;
-        for (int k = 0; k < nrc; ++k) cf *= sC[M.reac[j][k] * stride];
-        const double fwd = kf * cf;
-        double kr = 0.0, cr = 1.0;
+        R cf = kf;
+        for (int k = 0; k < nrc; ++k) cf *= sCb[M.reac[j][k] * stride];
+        double rv = 0.0;
         if (M.rev[j]) {
-            double dg = 0.0;
-            for (int k = 0; k < M.n_net[j]; ++k) dg = fma((double)M.net_nu[j][k], sG[M.net_sp[j][k] * stride], dg);
-            kr = kf * exp(dg + (double)M.dnu_sum[j] * lnRTp);    // k_f / K_c
-            for (int k = 0; k < npd; ++k) cr *= sC[M.prod[j][k] * stride];
+            double pr = (double)kf;
+            for (int k = 0; k < npd; ++k) pr *= sP[M.prod[j][k] * stride];
+            for (int k = 0; k < nrc; ++k) pr *= sRr[M.reac[j][k] * stride];
+            rv = pr;
         }
-        const double q = fwd - kr * cr;
+        const R q = (R)((double)cf - rv);
         for (int k = 0; k < M.n_net[j]; ++k) {
             const int s = M.net_sp[j][k];
-            sW[s * stride] = (R)fma((double)M.net_nu[j][k], q, (double)sW[s * stride]);
+            sW[s * stride] = fma((R)M.net_nu[j][k], q, sW[s * stride]);
         }
         if (want_rate) {
-            // d q / d C_s by removing one factor at each position of the reactant / product lists
+            // d q / d C_s: remove one factor at each position of the reactant / product lists
             for (int k = 0; k < nrc; ++k) {
-                double part = kf;
+                R part = kf;
                 for (int k2 = 0; k2 < nrc; ++k2)
-                    if (k2 != k) part *= sC[M.reac[j][k2] * stride];
+                    if (k2 != k) part *= sCb[M.reac[j][k2] * stride];
                 const int s = M.reac[j][k];
-                double dn = 0.0;
+                R dn = 0;
                 for (int k3 = 0; k3 < M.n_net[j]; ++k3)
-                    if (M.net_sp[j][k3] == s) dn = M.net_nu[j][k3];
-                sD[s * stride] = (R)((double)sD[s * stride] + dn * part);
+                    if (M.net_sp[j][k3] == s) dn = (R)M.net_nu[j][k3];
+                sD[s * stride] = fma(dn, part, sD[s * stride]);
             }
             if (M.rev[j]) {
                 for (int k = 0; k < npd; ++k) {
-                    double part = kr;
-                    for (int k2 = 0; k2 < npd; ++k2)
-                        if (k2 != k) part *= sC[M.prod[j][k2] * stride];
                     const int s = M.prod[j][k];
-                    double dn = 0.0;
+                    double part = (double)kf / sRr[s * stride];
+                    for (int k2 = 0; k2 < npd; ++k2)
+                        if (k2 != k) part *= sP[M.prod[j][k2] * stride];
+                    for (int k2 = 0; k2 < nrc; ++k2) part *= sRr[M.reac[j][k2] * stride];
+                    R dn = 0;
                     for (int k3 = 0; k3 < M.n_net[j]; ++k3)
-                        if (M.net_sp[j][k3] == s) dn = M.net_nu[j][k3];
-                    sD[s * stride] = (R)((double)sD[s * stride] - dn * part);
+                        if (M.net_sp[j][k3] == s) dn = (R)M.net_nu[j][k3];
+                    sD[s * stride] = fma(-dn, (R)part, sD[s * stride]);
                 }
             }
         }
@@ -103,6 +106,25 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
     return best;
 }
 
+// Per-species chemistry inputs of one cell (see chemistry()).
+template <typename R, int NS>
+__device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, const double (&rs)[NS], double T, double invT,
+                                                 double lnT, double *sC, R *sCb, double *sP, double *sRr, R *sW, R *sD,
+                                                 int stride) {
+    const double lnRTp = lnT + log(RU / PATM);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const double C = rs[s] * M.invW[s];
+        const double G = exp(g_RT(M, rng, s, T, invT, lnT) + lnRTp);
+        sC[s * stride] = C;
+        if (sizeof(R) == 4) sCb[s * stride] = (R)C;
+        sP[s * stride] = C * G;
+        sRr[s * stride] = 1.0 / G;
+        sW[s * stride] = (R)0;
+        sD[s * stride] = (R)0;
+    }
+}
+
 // ----------------------------------------------------------------------------- cell state
 
 template <typename R, int NS>
@@ -112,9 +134,11 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x;
     double *sC = (double *)smem_raw;
-    double *sG = sC + NS * B;
-    R *sW = (R *)(sG + NS * B);
+    double *sP = sC + NS * B;
+    double *sRr = sP + NS * B;
+    R *sW = (R *)(sRr + NS * B);
     R *sD = sW + NS * B;
+    R *sCb = sizeof(R) == 8 ? (R *)sC : sD + NS * B;
     __shared__ double s_laser[2];
     __shared__ double s_red[3][32];
 
@@ -184,19 +208,17 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
         Q[Q_C * n + cell] = (R)c;
         Q[Q_T * n + cell] = (R)T;
         R X[NS];
+        const double irm = 1.0 / Rm;
+        const R Tb = (R)T, invTb = (R)invT;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            X[s] = (R)(Y[s] * M.RW[s] / Rm);
+            X[s] = (R)(Y[s] * M.RW[s] * irm);
             Q[(QL<NS>::X + s) * n + cell] = X[s];
-            const double hrt = h_RT(M, rng, s, T, invT);
-            Q[(QL<NS>::H + s) * n + cell] = (R)(hrt * M.RW[s] * T);
-            if (chem_on) {
-                sC[s * B + tid] = rs[s] * M.invW[s];
-                sG[s * B + tid] = hrt - s_R(M, rng, s, T, lnT);
-                sW[s * B + tid] = (R)0;
-                sD[s * B + tid] = (R)0;
-            }
+            Q[(QL<NS>::H + s) * n + cell] = h_RT_bulk(M, rng, s, Tb, invTb) * mech_RW<R>(M, s) * Tb;
         }
+        if (chem_on)
+            chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
+                                    sD + tid, B);
         R mu, lam, Dc[NS], Dmax;
         transport<R, NS>(M, rng, (R)T, (R)p, (R)rho, (R)Wbar, X, mu, lam, Dc, Dmax);
         Q[Q_MU * n + cell] = mu;
@@ -206,7 +228,8 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
 
         R *rhs = (R *)m.rhs;
         if (chem_on) {
-            r_ch = chemistry<R, NS>(M, lnT, invT, sC + tid, sG + tid, sW + tid, sD + tid, B, m.want_rates != 0);
+            r_ch = chemistry<R, NS>(M, lnT, invT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
+                                    m.want_rates != 0);
 #pragma unroll
             for (int s = 0; s < NS; ++s) rhs[s * n + cell] = (R)((double)sW[s * B + tid] * M.W[s]);
         } else {
@@ -629,8 +652,9 @@ __global__ void __launch_bounds__(64) diag_kernel(const __grid_constant__ MechDe
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x, tid = threadIdx.x;
     double *sC = (double *)smem_raw;
-    double *sG = sC + NS * B;
-    double *sW = sG + NS * B;
+    double *sP = sC + NS * B;
+    double *sRr = sP + NS * B;
+    double *sW = sRr + NS * B;
     double *sD = sW + NS * B;
     __shared__ double red[NV + 2][64];
     const long long n = m.n, cell = (long long)blockIdx.x * B + tid;
@@ -661,17 +685,12 @@ __global__ void __launch_bounds__(64) diag_kernel(const __grid_constant__ MechDe
         const double invT = 1.0 / T, lnT = log(T);
         double hs[NS];
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const double hrt = h_RT(M, rng, s, T, invT);
-            hs[s] = hrt * M.RW[s] * T;
-            sC[s * B + tid] = rs[s] * M.invW[s];
-            sG[s * B + tid] = hrt - s_R(M, rng, s, T, lnT);
-            sW[s * B + tid] = 0.0;
-            sD[s * B + tid] = 0.0;
-        }
+        for (int s = 0; s < NS; ++s) hs[s] = h_RT(M, rng, s, T, invT) * M.RW[s] * T;
         double hrr = 0.0;
         if (M.nr > 0) {
-            chemistry<double, NS>(M, lnT, invT, sC + tid, sG + tid, sW + tid, sD + tid, B, false);
+            chemistry_inputs<double, NS>(M, rng, rs, T, invT, lnT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid,
+                                         sD + tid, B);
+            chemistry<double, NS>(M, lnT, invT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B, false);
 #pragma unroll
             for (int s = 0; s < NS; ++s) hrr -= hs[s] * sW[s * B + tid] * M.W[s];
         }

@@ -62,6 +62,7 @@ _sigs = {
     "rf_rk_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _vp, _vp]),
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
+    "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
     "rf_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_longlong)]),
     "rf_diagnostics": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Diag), _vp]),
 }
@@ -192,6 +193,13 @@ def rk_step(ctx: Context, U, T, t_dev, dt_fixed: float = 0.0, cfl: float = 0.5, 
 
 def set_option(ctx: Context, key: str, value: float):
     _check(_lib.rf_set_option(ctx.handle, key.encode(), float(value)), "rf_set_option")
+
+
+def probe_peak(kind: int, stream=None) -> float:
+    """Measured FMA throughput in TFLOP/s (kind 0: FP64, 1: FP32)."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.rf_probe_peak(int(kind), ctypes.byref(v), _stream(stream)), "rf_probe_peak")
+    return v.value
 
 
 PROF_CLASSES = ("cell_state", "sweep_x", "sweep_y", "sweep_z", "other")
