@@ -116,8 +116,8 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
 # dram__bytes_write.sum, both per cell (traffic grows with the cell count, so a
 # full 256^3 launch is the per-cell figure times 256^3).  None until captured for
 # the current kernel.
-CELL_STATE_MIXED_FP64_FLOP_PER_CELL = None
-CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = None
+CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 1014      # 388 DFMA + 165 DMUL + 73 DADD per cell
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 302.5     # (99.30 + 168.28) MB / 884,736 cells
 
 
 def cell_state_bytes(ns: int, rsize: int) -> int:

@@ -155,12 +155,14 @@ __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (
     P.cv[4] = 5.0 * c[4];
 }
 
+__device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
+
 // Newton solve of e(T) = e_target, warm-started from T; returns false if the
-// update did not fall below 1e-13 T within maxit iterations.
+// update did not fall below 1e-13 T within maxit iterations.  On return P holds
+// the mixture polynomial of the range containing T.
 template <int NS>
 __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
-                                         double &T, int maxit) {
-    MixPoly P;
+                                         double &T, int maxit, MixPoly &P) {
     int r = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
     mix_poly<NS>(M, r, Y, Rm, P);
     for (int it = 0; it < maxit; ++it) {
@@ -175,9 +177,17 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
         // perturbs the convergence rate (by ~1e-7 per step), not the converged T.
         const double dT = (e - e_target) * (double)__frcp_rn((float)cv);
         T = T - dT;
-        if (fabs(dT) <= 1.0e-13 * fabs(T)) return true;
+        if (fabs(dT) <= 1.0e-13 * fabs(T)) {
+            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS>(M, nasa_range_of(M, T), Y, Rm, P);
+            return true;
+        }
     }
     return false;
+}
+
+// cv(T) of the mixture polynomial P (J/kg/K).
+__device__ __forceinline__ double mix_cv(const MixPoly &P, double T) {
+    return fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
 }
 
 __device__ __forceinline__ int nasa_range(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }

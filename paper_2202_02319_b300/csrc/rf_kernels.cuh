@@ -181,7 +181,8 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
         }
         const double e = E * irho - 0.5 * (u * u + v * v + w * w);
         double T = m.T[cell];
-        const bool ok = newton_T<NS>(M, Y, Rm, e, T, newton_maxit);
+        MixPoly P;
+        const bool ok = newton_T<NS>(M, Y, Rm, e, T, newton_maxit, P);
         if (!ok) flag_error(m, ST_NEWTON, cell);
         if (!(rho > 0.0) || !(T > 0.0) || !(T < T_MAX_ADMISSIBLE)) {
             if (isfinite(rho) && isfinite(T)) flag_error(m, ST_RANGE, cell);
@@ -193,12 +194,10 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
         const int rng = nasa_range(M, T);
         const double invT = 1.0 / T;
         const double lnT = log(T);
-        double cp = 0.0;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) cp = fma(Y[s] * M.RW[s], cp_R<double>(M, rng, s, T), cp);
-        const double cv = cp - Rm;
+        const double cv = mix_cv(P, T);
+        const double cp = cv + Rm;
         const double p = rho * Rm * T;
-        const double c = sqrt(cp / cv * Rm * T);
+        const R c = sqrt_((R)(cp / cv) * (R)(Rm * T));
         const double Wbar = RU / Rm;
         R *Q = (R *)m.Q;
         Q[Q_U * n + cell] = (R)u;
@@ -261,11 +260,11 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
             for (int v2 = 0; v2 < NV; ++v2) m.U32[v2 * n + cell] = (float)U[v2 * n + cell];
         }
         if (m.want_rates) {
-            double ac = 0.0;
-            if (m.nx > 1) ac += (fabs(u) + c) * m.invh[0];
-            if (m.ny > 1) ac += (fabs(v) + c) * m.invh[1];
-            if (m.nz > 1) ac += (fabs(w) + c) * m.invh[2];
-            r_ac = (R)ac;
+            R ac = 0;
+            if (m.nx > 1) ac += (fabs((R)u) + c) * (R)m.invh[0];
+            if (m.ny > 1) ac += (fabs((R)v) + c) * (R)m.invh[1];
+            if (m.nz > 1) ac += (fabs((R)w) + c) * (R)m.invh[2];
+            r_ac = ac;
             if (!(m.flags & F_NO_VISCOUS)) {
                 const R nu = mu / (R)rho;
                 const R al = lam / ((R)rho * (R)cp);
@@ -451,7 +450,7 @@ template <typename R, int NS, int MODE>
 __device__ __forceinline__ void cell_update(const Member &m, long long cell, const R (&dG)[NS + 4], R ih) {
     constexpr int NV = NS + 4;
     const long long n = m.n;
-    R *rhs = (R *)m.rhs;
+    R *__restrict__ rhs = (R *)m.rhs;
     if (MODE == MODE_ACCUM) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) rhs[v * n + cell] = fma(dG[v], ih, rhs[v * n + cell]);
@@ -460,12 +459,13 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
         for (int v = 0; v < NV; ++v) m.dUdt[v * n + cell] = (double)fma(dG[v], ih, rhs[v * n + cell]);
     } else {
         const double dt = m.clock[1];
+        const double *__restrict__ Uk = m.U;
+        const double *__restrict__ Un = m.Un;
+        double *__restrict__ Uo = m.Uout;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const double L = (double)fma(dG[v], ih, rhs[v * n + cell]);
-            const double uk = m.U[v * n + cell];
-            const double un = m.Un[v * n + cell];
-            m.Uout[v * n + cell] = fma(m.stage_a, un, m.stage_b * fma(dt, L, uk));
+            Uo[v * n + cell] = fma(m.stage_a, Un[v * n + cell], m.stage_b * fma(dt, L, Uk[v * n + cell]));
         }
     }
 }
@@ -679,7 +679,8 @@ __global__ void __launch_bounds__(64) diag_kernel(const __grid_constant__ MechDe
         }
         const double e = m.U[(NS + 3) * n + cell] * irho - 0.5 * (u * u + v * v + w * w);
         double T = m.T[cell];
-        if (!newton_T<NS>(M, Y, Rm, e, T, newton_maxit)) flag_error(m, ST_NEWTON, cell);
+        MixPoly P;
+        if (!newton_T<NS>(M, Y, Rm, e, T, newton_maxit, P)) flag_error(m, ST_NEWTON, cell);
         m.T[cell] = T;
         const int rng = nasa_range(M, T);
         const double invT = 1.0 / T, lnT = log(T);
