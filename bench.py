@@ -245,6 +245,9 @@ def run_ours(args):
     value64 = world * ncell * 3 * args.fp64_steps / (ms64 * 1e-3)
     del ctx64, U64, T64
 
+    # --- batched ensemble (64 members of uneven size): members/s per launch mode
+    ens = run_ensemble_leg(args, dev) if args.ensemble_members > 0 else None
+
     # --- roofline of the dominant kernel of the mixed step
     peaks = _peaks()
     fp64_peak = nv.probe_peak(0)
@@ -297,6 +300,7 @@ def run_ours(args):
                  "kernels": k64},
         "kernels": kernels,
         "roofline": roofline,
+        "ensemble": ens,
         "peaks_measured": {"fp64_tflops": round(fp64_peak, 4), "fp32_tflops": round(fp32_peak, 3),
                            "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -312,6 +316,54 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- ensemble leg
+
+def run_ensemble_leg(args, dev):
+    """Members/s of the batched-ensemble workload (members with every axis in
+    U{48..96}, laser energy U[5, 40] mJ) in the mixed path: the per-member launch
+    loop against one launch per phase in a CUDA graph and one persistent launch
+    per RK stage in a CUDA graph, after autotuning the walk segment."""
+    import torch
+    from paper_2202_02319_b300 import native as nv, synth
+    cases = synth.ensemble_members(seed=0, n_members=args.ensemble_members, device=dev)
+    mech = nv.init_mechanism(cases[0].mech)
+    ctxs, Us, Ts = [], [], []
+    for c in cases:
+        ns, n = c.mech.n_species, c.grid.ncells
+        ctx = nv.create_ctx(mech, c.grid, nv.RF_MIXED)
+        U = torch.empty((ns + 4, n), dtype=torch.float64, device=dev)
+        T = torch.empty(n, dtype=torch.float64, device=dev)
+        nv.init_state(ctx, c.prim.reshape(5 + ns, n).contiguous(), U, T)
+        ctxs.append(ctx)
+        Us.append(U)
+        Ts.append(T)
+        c.prim = None
+    t = torch.zeros(len(cases), dtype=torch.float64, device=dev)
+    e = nv.ensemble_create(ctxs, Us, Ts, [c.laser.as_tuple() for c in cases], t)
+    seg = nv.ensemble_autotune(e, nv.ENS_PERSISTENT_GRAPH, 0.5)
+    cells = sum(c.grid.ncells for c in cases)
+    out = {"members": len(cases), "cells": cells, "walk_seg_autotuned": seg, "steps": args.ensemble_steps}
+    s = torch.cuda.current_stream()
+    for name, mode in (("member_loop", nv.ENS_LOOP), ("batched_graph", nv.ENS_GRAPH),
+                       ("persistent_graph", nv.ENS_PERSISTENT_GRAPH)):
+        nv.run_ensemble(e, 1, mode, 0.5)                 # warm-up (captures the graph)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        code, st = nv.run_ensemble(e, args.ensemble_steps, mode, 0.5, raise_on_error=False)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"members_per_s": len(cases) * args.ensemble_steps / (ms * 1e-3),
+                     "cell_updates_per_s": cells * 3 * args.ensemble_steps / (ms * 1e-3),
+                     "ms_per_step": ms / args.ensemble_steps, "failed_members": sum(1 for x in st if x)}
+    out["speedup_persistent_vs_loop"] = out["persistent_graph"]["members_per_s"] / out["member_loop"]["members_per_s"]
+    out["speedup_batched_vs_loop"] = out["batched_graph"]["members_per_s"] / out["member_loop"]["members_per_s"]
+    del e, ctxs, Us, Ts
+    torch.cuda.empty_cache()
+    return out
 
 
 # ----------------------------------------------------------------------------- oracle arm
@@ -372,6 +424,8 @@ def main():
     ap.add_argument("--cpu-n", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble-members", type=int, default=64)
+    ap.add_argument("--ensemble-steps", type=int, default=2)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -187,6 +187,47 @@ int rf_status(rf_ctx *c, rf_stream s, long long *cell_out);
  * state U (with T as Newton warm start).  Synchronous (result on the host). */
 int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s);
 
+/* Batched ensembles (workload shape of the paper's ensemble studies, Results,
+ * Ensemble simulation; Methods, Diffusion flame): members are contexts of one
+ * mechanism and precision with their own grid sizes, states and lasers.
+ * rf_ensemble_create records, for member i, its context, its state U[i], T[i]
+ * (device) and laser lasers[i] (host, may be NULL for none) and t_dev[i] (device
+ * array of n doubles holding each member's time); it builds the member tables
+ * and the (member, tile) work lists of every phase.  The buffers must outlive
+ * the ensemble.  Errors: RF_EINVAL (mixed mechanisms or precisions), RF_ENOMEM. */
+typedef struct rf_ensemble rf_ensemble;
+int rf_ensemble_create(rf_ctx *const *members, int n, double *const *U, double *const *T, const rf_laser *lasers,
+                       double *t_dev, rf_ensemble **out);
+void rf_ensemble_free(rf_ensemble *e);
+
+/* Options: "walk_seg" (cells walked per thread in the y / z sweeps; rebuilds the
+ * work lists), "barrier_spins" (polls, ~100 ns each, before a grid barrier of the
+ * persistent kernel gives up; default 2e7) and "barrier_extra" (0 or 1: arrivals
+ * a barrier waits for beyond the grid, so that a test can make a wait run out). */
+int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value);
+
+/* Advances every member by nsteps SSP-RK3 steps (rules as rf_rk_step).
+ * mode 0: per-member launch loop (each member's own rf_rk_step launches);
+ * mode 1: one launch per phase over all members' work items;
+ * mode 2: mode 1 captured once as a CUDA graph of one step, replayed;
+ * mode 3: one persistent cooperative launch per RK stage (grid barriers between
+ *         the phases, each bounded: a wait that runs out returns RF_ETIMEOUT);
+ * mode 4: mode 3 captured as a CUDA graph.
+ * Modes 1-4 need every member with nx, ny, nz > 1.  A member whose state fails
+ * (Newton, non-finite, range) is frozen at its last good step and the others
+ * continue; member_status (host, n ints, may be NULL) receives each member's
+ * RF_E* code.  Synchronous.  Returns RF_ETIMEOUT if a barrier gave up, a member's
+ * code if member_status is NULL and a member failed, else RF_OK.  Each member's
+ * results are bitwise those of running it alone. */
+int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl, double dt_fixed, int32_t *member_status,
+                    rf_stream s);
+
+/* Picks the y / z walk segment length of a batched mode (1-4) by timing trial
+ * steps of the ensemble itself for 8, 16 and 32 cells, then restores every
+ * member's state and time; *seg_out (may be NULL) receives the choice.  The halo
+ * is fixed at two cells by the WENO3-Z stencil and is not a tuning parameter. */
+int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_stream s);
+
 /* Measures the FMA throughput of the current device (kind 0: FP64, 1: FP32)
  * with independent FMA chains on every SM; *tflops receives 2 x FMAs / s / 1e12.
  * Synchronous.  The FP64 figure is the ALU roofline of the cell-state kernel. */

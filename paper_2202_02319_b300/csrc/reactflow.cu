@@ -15,7 +15,7 @@
 #include <vector>
 
 #include "reactflow.h"
-#include "rf_kernels.cuh"
+#include "rf_ensemble.cuh"
 
 using namespace rf;
 
@@ -616,6 +616,434 @@ extern "C" int rf_status(rf_ctx *c, rf_stream s, long long *cell_out) {
     if (st & ST_RANGE) return fail(RF_ERANGE, "temperature or density out of range at cell %lld", cell);
     if (st & ST_TIMEOUT) return fail(RF_ETIMEOUT, "a bounded device wait gave up");
     return RF_OK;
+}
+
+
+// ----------------------------------------------------------------------------- ensembles
+
+struct rf_ensemble {
+    const rf_mech *mech = nullptr;
+    int n = 0, precision = 0, ns = 0;
+    bool all3d = true;
+    std::vector<rf_ctx *> ctx;
+    std::vector<double *> U, T;
+    std::vector<rf_laser> las;
+    double *t_dev = nullptr;
+    Member *d_tab[3] = {nullptr, nullptr, nullptr};
+    EnsItem *d_items[4] = {nullptr, nullptr, nullptr, nullptr};
+    int nitems[4] = {0, 0, 0, 0};
+    unsigned int *d_bar = nullptr;
+    int *d_timeout = nullptr;
+    int seg = 16, xblock = 128;
+    long long max_spins = 20000000;          // ~2 s of polling per barrier
+    unsigned int bar_extra = 0;              // tests: arrivals a barrier waits for beyond the grid
+    size_t smem_cell = 0, smem_x = 0;
+    int coop_blocks = 0;
+    cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+    double graph_cfl[4] = {0, 0, 0, 0}, graph_dt[4] = {0, 0, 0, 0};
+};
+
+static void ens_free_device(rf_ensemble *e) {
+    for (int k = 0; k < 3; ++k)
+        if (e->d_tab[k]) cudaFree(e->d_tab[k]), e->d_tab[k] = nullptr;
+    for (int k = 0; k < 4; ++k)
+        if (e->d_items[k]) cudaFree(e->d_items[k]), e->d_items[k] = nullptr;
+    for (int k = 0; k < 4; ++k)
+        if (e->graph[k]) cudaGraphExecDestroy(e->graph[k]), e->graph[k] = nullptr;
+}
+
+extern "C" void rf_ensemble_free(rf_ensemble *e) {
+    if (!e) return;
+    ens_free_device(e);
+    if (e->d_bar) cudaFree(e->d_bar);
+    if (e->d_timeout) cudaFree(e->d_timeout);
+    delete e;
+}
+
+// x sweep row chunking for a block of B threads (see Path::sweep)
+static void x_shape(int nx, int B, int &W, int &rpb) {
+    if (nx <= B) {
+        W = nx;
+        rpb = std::max(1, std::min(B / nx, 320 / (nx + 2)));
+    } else {
+        W = B;
+        rpb = 1;
+    }
+}
+
+// (Re)builds the descriptor tables and work lists for the current seg / xblock.
+static int ens_build(rf_ensemble *e) {
+    ens_free_device(e);
+    const double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0}, cc[3] = {0.0, 1.0, 0.5};
+    std::vector<Member> tab[3];
+    std::vector<EnsItem> items[4];
+    size_t smx = 0;
+    for (int mi = 0; mi < e->n; ++mi) {
+        rf_ctx *c = e->ctx[mi];
+        Member m = base_member(c);
+        m.T = e->T[mi];
+        m.Un = e->U[mi];
+        set_laser(m, &e->las[mi]);
+        int W, rpb;
+        x_shape(c->g.nx, e->xblock, W, rpb);
+        m.xW = W;
+        m.xrpb = rpb;
+        const double *in[3] = {e->U[mi], c->U1, c->U2};
+        double *outp[3] = {c->U1, c->U2, e->U[mi]};
+        for (int k = 0; k < 3; ++k) {
+            Member mk = m;
+            mk.U = in[k];
+            mk.Uout = outp[k];
+            mk.stage_a = a[k];
+            mk.stage_b = b[k];
+            mk.stage_c = cc[k];
+            mk.want_rates = k == 0 ? 1 : 0;
+            tab[k].push_back(mk);
+        }
+        const int nv = c->nv;
+        smx = std::max(smx, (size_t)nv * rpb * (W + 2) * c->rsize);
+        const long long ncb = (c->n + 127) / 128;
+        for (long long q = 0; q < ncb; ++q) items[0].push_back({mi, (int)q, 0, 0});
+        const int nrows = c->g.ny * c->g.nz;
+        for (int q = 0; q < (nrows + rpb - 1) / rpb; ++q) items[1].push_back({mi, q, 0, 0});
+        for (int dir = 1; dir <= 2; ++dir) {
+            const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
+            const int nd = dir == 1 ? c->g.ny : c->g.nz;
+            const int lb = (int)((lines + 127) / 128), sb = (nd + e->seg - 1) / e->seg;
+            for (int q = 0; q < lb; ++q)
+                for (int r = 0; r < sb; ++r) items[1 + dir].push_back({mi, q, r, 0});
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        CUDA_TRY(cudaMalloc((void **)&e->d_tab[k], sizeof(Member) * e->n));
+        CUDA_TRY(cudaMemcpy(e->d_tab[k], tab[k].data(), sizeof(Member) * e->n, cudaMemcpyHostToDevice));
+    }
+    for (int k = 0; k < 4; ++k) {
+        e->nitems[k] = (int)items[k].size();
+        CUDA_TRY(cudaMalloc((void **)&e->d_items[k], sizeof(EnsItem) * std::max<size_t>(1, items[k].size())));
+        CUDA_TRY(cudaMemcpy(e->d_items[k], items[k].data(), sizeof(EnsItem) * items[k].size(), cudaMemcpyHostToDevice));
+    }
+    e->smem_x = smx;
+    return RF_OK;
+}
+
+static EnsDev ens_dev(rf_ensemble *e, unsigned int grid) {
+    EnsDev E;
+    std::memset(&E, 0, sizeof E);
+    for (int k = 0; k < 3; ++k) E.tab[k] = e->d_tab[k];
+    for (int k = 0; k < 4; ++k) {
+        E.items[k] = e->d_items[k];
+        E.nitems[k] = e->nitems[k];
+    }
+    E.nmembers = e->n;
+    E.seg = e->seg;
+    E.newton_maxit = e->ctx[0]->newton_maxit;
+    E.bar = e->d_bar;
+    E.timeout = e->d_timeout;
+    E.max_spins = e->max_spins;
+    E.bar_expect = grid + e->bar_extra;
+    return E;
+}
+
+template <typename R, int NS>
+struct EnsPath {
+    using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
+
+    static int setup(rf_ensemble *e) {
+        e->smem_cell = cell_state_smem<R, NS>(128);
+        CUDA_TRY(cudaFuncSetAttribute(ens_cell_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_cell));
+        CUDA_TRY(cudaFuncSetAttribute(ens_x_kernel<R, UT, NS, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)std::max<size_t>(e->smem_x, 1)));
+        const size_t sm_stage = std::max(e->smem_cell, e->smem_x);
+        CUDA_TRY(cudaFuncSetAttribute(ens_stage_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
+        int dev = 0, sms = 0, per = 0;
+        CUDA_TRY(cudaGetDevice(&dev));
+        CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_stage_kernel<R, NS>, 128, sm_stage));
+        if (per < 1) return fail(RF_ECUDA, "ensemble: persistent stage kernel does not fit on an SM");
+        e->coop_blocks = per * sms;
+        return RF_OK;
+    }
+
+    // one step as one launch per phase (mode 1/2)
+    static int step_batched(rf_ensemble *e, cudaStream_t s) {
+        const MechDev &M = e->mech->d;
+        for (int k = 0; k < 3; ++k) {
+            EnsDev E0 = ens_dev(e, e->nitems[0]);
+            ens_cell_kernel<R, NS><<<e->nitems[0], 128, e->smem_cell, s>>>(M, E0, k);
+            LAUNCH_CHECK();
+            if (k == 0) {
+                ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);
+                LAUNCH_CHECK();
+            }
+            ens_x_kernel<R, UT, NS, MODE_ACCUM><<<e->nitems[1], 128, e->smem_x, s>>>(M, ens_dev(e, e->nitems[1]), k);
+            LAUNCH_CHECK();
+            ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM><<<e->nitems[2], 128, 0, s>>>(M, ens_dev(e, e->nitems[2]), k);
+            LAUNCH_CHECK();
+            ens_walk_kernel<R, UT, NS, 2, MODE_STAGE><<<e->nitems[3], 128, 0, s>>>(M, ens_dev(e, e->nitems[3]), k);
+            LAUNCH_CHECK();
+        }
+        ens_end_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(ens_dev(e, 1));
+        LAUNCH_CHECK();
+        return RF_OK;
+    }
+
+    // one step as one cooperative launch per RK stage (mode 3)
+    static int step_persistent(rf_ensemble *e, cudaStream_t s) {
+        const size_t sm_stage = std::max(e->smem_cell, e->smem_x);
+        for (int k = 0; k < 3; ++k) {
+            EnsDev E = ens_dev(e, e->coop_blocks);
+            cudaLaunchConfig_t cfg;
+            std::memset(&cfg, 0, sizeof cfg);
+            cfg.gridDim = dim3(e->coop_blocks);
+            cfg.blockDim = dim3(128);
+            cfg.dynamicSmemBytes = sm_stage;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeCooperative;
+            attr[0].val.cooperative = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, ens_stage_kernel<R, NS>, e->mech->d, E, k));
+        }
+        return RF_OK;
+    }
+};
+
+#define ENS_DISPATCH(e, CALL)                                                        \
+    do {                                                                             \
+        if ((e)->precision == RF_FP64) {                                             \
+            switch ((e)->ns) {                                                       \
+                case 1: return EnsPath<double, 1>::CALL;                             \
+                case 2: return EnsPath<double, 2>::CALL;                             \
+                case 4: return EnsPath<double, 4>::CALL;                             \
+                case 9: return EnsPath<double, 9>::CALL;                             \
+            }                                                                        \
+        } else {                                                                     \
+            switch ((e)->ns) {                                                       \
+                case 1: return EnsPath<float, 1>::CALL;                              \
+                case 2: return EnsPath<float, 2>::CALL;                              \
+                case 4: return EnsPath<float, 4>::CALL;                              \
+                case 9: return EnsPath<float, 9>::CALL;                              \
+            }                                                                        \
+        }                                                                            \
+        return fail(RF_EINVAL, "unsupported species count %d", (e)->ns);             \
+    } while (0)
+
+static int ens_setup(rf_ensemble *e) { ENS_DISPATCH(e, setup(e)); }
+static int ens_step_batched(rf_ensemble *e, cudaStream_t s) { ENS_DISPATCH(e, step_batched(e, s)); }
+static int ens_step_persistent(rf_ensemble *e, cudaStream_t s) { ENS_DISPATCH(e, step_persistent(e, s)); }
+
+extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *U, double *const *T, const rf_laser *lasers,
+                                  double *t_dev, rf_ensemble **out) {
+    if (!members || !U || !T || !t_dev || !out || n < 1) return fail(RF_EINVAL, "rf_ensemble_create: bad argument");
+    *out = nullptr;
+    rf_ensemble *e = new rf_ensemble();
+    e->n = n;
+    e->t_dev = t_dev;
+    for (int i = 0; i < n; ++i) {
+        rf_ctx *c = members[i];
+        if (!c || !U[i] || !T[i]) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d has a null context or buffer", i);
+        }
+        if (i == 0) {
+            e->mech = c->mech;
+            e->precision = c->precision;
+            e->ns = c->ns;
+        } else if (c->mech != e->mech || c->precision != e->precision) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d differs in mechanism or precision", i);
+        }
+        e->all3d = e->all3d && c->g.nx > 1 && c->g.ny > 1 && c->g.nz > 1;
+        e->ctx.push_back(c);
+        e->U.push_back(U[i]);
+        e->T.push_back(T[i]);
+        rf_laser L;
+        std::memset(&L, 0, sizeof L);
+        if (lasers) L = lasers[i];
+        e->las.push_back(L);
+    }
+    cudaError_t er = cudaMalloc((void **)&e->d_bar, 2 * sizeof(unsigned int));
+    if (er == cudaSuccess) er = cudaMalloc((void **)&e->d_timeout, sizeof(int));
+    if (er == cudaSuccess) er = cudaMemset(e->d_bar, 0, 2 * sizeof(unsigned int));
+    if (er == cudaSuccess) er = cudaMemset(e->d_timeout, 0, sizeof(int));
+    if (er != cudaSuccess) {
+        rf_ensemble_free(e);
+        return fail(RF_ENOMEM, "rf_ensemble_create: %s", cudaGetErrorString(er));
+    }
+    int rc = ens_build(e);
+    if (!rc) rc = ens_setup(e);
+    if (rc) {
+        rf_ensemble_free(e);
+        return rc;
+    }
+    *out = e;
+    return RF_OK;
+}
+
+extern "C" int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value) {
+    if (!e || !key) return fail(RF_EINVAL, "rf_ensemble_set_option: null argument");
+    if (!std::strcmp(key, "walk_seg")) {
+        if (value < 1 || value > 4096) return fail(RF_EINVAL, "rf_ensemble_set_option: walk_seg out of range");
+        e->seg = (int)value;
+        int rc = ens_build(e);
+        return rc ? rc : ens_setup(e);
+    }
+    if (!std::strcmp(key, "barrier_spins")) {
+        if (value < 1 || value > 1e9) return fail(RF_EINVAL, "rf_ensemble_set_option: barrier_spins out of range");
+        e->max_spins = (long long)value;
+    } else if (!std::strcmp(key, "barrier_extra")) {
+        if (value < 0 || value > 1) return fail(RF_EINVAL, "rf_ensemble_set_option: barrier_extra must be 0 or 1");
+        e->bar_extra = (unsigned int)value;
+    } else {
+        return fail(RF_EINVAL, "rf_ensemble_set_option: unknown key '%s'", key);
+    }
+    for (int k = 0; k < 4; ++k)
+        if (e->graph[k]) cudaGraphExecDestroy(e->graph[k]), e->graph[k] = nullptr;
+    return RF_OK;
+}
+
+static int ctx_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, double cfl, const rf_laser *L,
+                       cudaStream_t s) {
+    DISPATCH(c, rk_step(c, U, T, t_dev, dt_fixed, cfl, L, nullptr, s));
+}
+
+static int ens_step(rf_ensemble *e, int mode, double cfl, double dt_fixed, cudaStream_t s) {
+    if (mode == 0) {
+        for (int i = 0; i < e->n; ++i) {
+            int rc = ctx_rk_step(e->ctx[i], e->U[i], e->T[i], e->t_dev + i, dt_fixed, cfl, &e->las[i], s);
+            if (rc) return rc;
+        }
+        return RF_OK;
+    }
+    if (mode >= 3) return ens_step_persistent(e, s);
+    return ens_step_batched(e, s);
+}
+
+static int status_code(int st) {
+    if (st & ST_TIMEOUT) return RF_ETIMEOUT;
+    if (st & ST_NONFINITE) return RF_ENONFINITE;
+    if (st & ST_NEWTON) return RF_ENEWTON;
+    if (st & ST_RANGE) return RF_ERANGE;
+    return RF_OK;
+}
+
+extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl, double dt_fixed, int32_t *member_status,
+                               rf_stream stream) {
+    if (!e || nsteps < 0 || mode < 0 || mode > 4) return fail(RF_EINVAL, "rf_run_ensemble: bad argument");
+    if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_run_ensemble: need dt_fixed > 0 or cfl > 0");
+    if (mode > 0 && !e->all3d) return fail(RF_EINVAL, "rf_run_ensemble: batched modes need every member with nx, ny, nz > 1");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (mode == 0) {
+        for (int k = 0; k < nsteps; ++k) {
+            int rc = ens_step(e, 0, cfl, dt_fixed, s);
+            if (rc) return rc;
+        }
+    } else {
+        CUDA_TRY(cudaMemsetAsync(e->d_timeout, 0, sizeof(int), s));
+        CUDA_TRY(cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned int), s));
+        EnsDev E = ens_dev(e, 1);
+        ens_begin_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(E, e->t_dev, cfl, dt_fixed);
+        LAUNCH_CHECK();
+        const bool graph = mode == 2 || mode == 4;
+        if (graph && nsteps > 0 && !e->graph[mode]) {
+            cudaGraph_t g;
+            CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            int rc = ens_step(e, mode, cfl, dt_fixed, s);
+            cudaError_t ce = cudaStreamEndCapture(s, &g);
+            if (rc) return rc;
+            if (ce != cudaSuccess) return fail(RF_ECUDA, "rf_run_ensemble: graph capture: %s", cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&e->graph[mode], g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return fail(RF_ECUDA, "rf_run_ensemble: graph instantiate: %s", cudaGetErrorString(ce));
+        }
+        for (int k = 0; k < nsteps; ++k) {
+            if (graph) {
+                CUDA_TRY(cudaGraphLaunch(e->graph[mode], s));
+            } else {
+                int rc = ens_step(e, mode, cfl, dt_fixed, s);
+                if (rc) return rc;
+            }
+        }
+        ens_finish_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(E, e->t_dev);
+        LAUNCH_CHECK();
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int timeout = 0;
+    CUDA_TRY(cudaMemcpy(&timeout, e->d_timeout, sizeof(int), cudaMemcpyDeviceToHost));
+    int first = RF_OK;
+    for (int i = 0; i < e->n; ++i) {
+        rf_ctx *c = e->ctx[i];
+        int st = 0;
+        CUDA_TRY(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemset(c->status, 0, sizeof(int)));
+        CUDA_TRY(cudaMemset(c->bad_cell, 0xff, sizeof(long long)));
+        const int code = status_code(st);
+        if (member_status) member_status[i] = code;
+        if (code && !first) first = code;
+    }
+    if (timeout) {
+        CUDA_TRY(cudaMemset(e->d_timeout, 0, sizeof(int)));
+        return fail(RF_ETIMEOUT, "rf_run_ensemble: a grid barrier of the persistent kernel gave up waiting");
+    }
+    if (first && !member_status) return fail(first, "rf_run_ensemble: a member failed (pass member_status to mask it)");
+    return RF_OK;
+}
+
+extern "C" int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_stream stream) {
+    if (!e || mode < 1 || mode > 4) return fail(RF_EINVAL, "rf_ensemble_autotune: bad argument");
+    if (!e->all3d) return fail(RF_EINVAL, "rf_ensemble_autotune: batched modes need 3-D members");
+    cudaStream_t s = (cudaStream_t)stream;
+    // keep the states: trial steps run on them and are rolled back
+    size_t tot = 0;
+    for (int i = 0; i < e->n; ++i) tot += (size_t)e->ctx[i]->n * (e->ctx[i]->nv + 1);
+    double *bk = nullptr;
+    CUDA_TRY(cudaMalloc((void **)&bk, (tot + e->n) * sizeof(double)));
+    auto copy_states = [&](bool save) -> int {
+        size_t off = 0;
+        for (int i = 0; i < e->n; ++i) {
+            const size_t nu = (size_t)e->ctx[i]->n * e->ctx[i]->nv, nt = (size_t)e->ctx[i]->n;
+            CUDA_TRY(cudaMemcpyAsync(save ? bk + off : e->U[i], save ? e->U[i] : bk + off, nu * 8, cudaMemcpyDeviceToDevice, s));
+            off += nu;
+            CUDA_TRY(cudaMemcpyAsync(save ? bk + off : e->T[i], save ? e->T[i] : bk + off, nt * 8, cudaMemcpyDeviceToDevice, s));
+            off += nt;
+        }
+        CUDA_TRY(cudaMemcpyAsync(save ? bk + off : e->t_dev, save ? e->t_dev : bk + off, e->n * 8, cudaMemcpyDeviceToDevice, s));
+        return RF_OK;
+    };
+    int rc = copy_states(true);
+    const int cands[3] = {8, 16, 32};
+    int best = e->seg;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<int32_t> st(e->n);
+    for (int q = 0; q < 3 && !rc; ++q) {
+        rc = rf_ensemble_set_option(e, "walk_seg", cands[q]);
+        if (rc) break;
+        rc = rf_run_ensemble(e, 1, mode, cfl, 0.0, st.data(), stream);     // warm-up (and graph capture)
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        rc = rf_run_ensemble(e, 2, mode, cfl, 0.0, st.data(), stream);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && ms < best_ms) {
+            best_ms = ms;
+            best = cands[q];
+        }
+        if (!rc) rc = copy_states(false);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = rf_ensemble_set_option(e, "walk_seg", best);
+    cudaStreamSynchronize(s);
+    cudaFree(bk);
+    if (seg_out) *seg_out = best;
+    return rc;
 }
 
 // ----------------------------------------------------------------------------- peak probe

@@ -75,6 +75,7 @@ struct Member {
     int want_rates;
     int t_from_host;             // 1: stage time is t_host (rf_rhs), 0: clock[0] + stage_c clock[1]
     double t_host;
+    int xW, xrpb;                // x sweep row chunk width and rows per block (ensemble launches)
 };
 
 // Q field order (each field n values of type R).

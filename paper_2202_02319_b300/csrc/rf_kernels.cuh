@@ -127,11 +127,16 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
 
 // ----------------------------------------------------------------------------- cell state
 
+// Dynamic shared memory of one cell-state block of B threads.
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
-                                                         int newton_maxit) {
+__host__ __device__ constexpr size_t cell_state_smem(int B) {
+    return (size_t)B * NS * (3 * sizeof(double) + 2 * sizeof(R) + (sizeof(R) == 4 ? sizeof(R) : 0));
+}
+
+template <typename R, int NS>
+__device__ __forceinline__ void cell_state_block(const MechDev &M, const Member &m, long long blk, unsigned char *smem_raw,
+                                                 int newton_maxit) {
     constexpr int NV = NS + 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x;
     double *sC = (double *)smem_raw;
     double *sP = sC + NS * B;
@@ -144,7 +149,7 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
 
     const int tid = threadIdx.x;
     const long long n = m.n;
-    const long long cell = (long long)blockIdx.x * B + tid;
+    const long long cell = blk * B + tid;
     const bool chem_on = !(m.flags & F_NO_CHEM) && M.nr > 0;
     const bool laser_on = m.laser_on && !(m.flags & F_NO_LASER);
     if (tid == 0 && laser_on) {
@@ -299,6 +304,13 @@ __global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__
             atomic_max_pos(&m.rates[2], ch);
         }
     }
+}
+
+template <typename R, int NS>
+__global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                         int newton_maxit) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cell_state_block<R, NS>(M, m, blockIdx.x, smem_raw, newton_maxit);
 }
 
 // ----------------------------------------------------------------------------- face flux
@@ -473,16 +485,15 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
 // x sweep: each block row group processes its rows in chunks of W faces; face
 // f = c W + lx goes to slot lx+1, slot 0 carries the previous chunk's last face.
 template <typename R, typename UT, int NS, int MODE>
-__global__ void __launch_bounds__(256) sweep_x_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
-                                                      int W, int rpb) {
+__device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m, int blk, int W, int rpb,
+                                              unsigned char *smem_raw) {
     constexpr int NV = NS + 4;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     R *sG = (R *)smem_raw;                       // [NV][rpb][W + 1]
     R *s0 = sG + (size_t)NV * rpb * (W + 1);     // [NV][rpb]: face 0 of each row (periodic wrap)
     const int tid = threadIdx.x;
     const int r = tid / W, lx = tid - r * W;
     const int nrows = m.ny * m.nz;
-    const int row = blockIdx.x * rpb + r;
+    const int row = blk * rpb + r;
     const bool active = r < rpb && row < nrows;
     const int j = active ? row % m.ny : 0, k = active ? row / m.ny : 0;
     const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
@@ -522,17 +533,23 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(const __grid_constant__ Me
     }
 }
 
+template <typename R, typename UT, int NS, int MODE>
+__global__ void __launch_bounds__(256) sweep_x_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                      int W, int rpb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_x_block<R, UT, NS, MODE>(M, m, blockIdx.x, W, rpb, smem_raw);
+}
+
 // y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
 template <typename R, typename UT, int NS, int DIR, int MODE>
-__global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
-                                                         int seg) {
+__device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member &m, long long lblk, int sblk, int seg) {
     constexpr int NV = NS + 4;
-    const long long line = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long line = lblk * blockDim.x + threadIdx.x;
     const int nd = DIR == 1 ? m.ny : m.nz;
     const int no = DIR == 1 ? m.nz : m.ny;
     if (line >= (long long)m.nx * no) return;
     const int x = (int)(line % m.nx), o = (int)(line / m.nx);
-    const int c0 = blockIdx.y * seg;
+    const int c0 = sblk * seg;
     if (c0 >= nd) return;
     const int c1 = min(c0 + seg, nd);
     const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
@@ -559,6 +576,12 @@ __global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__
 #pragma unroll
         for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
     }
+}
+
+template <typename R, typename UT, int NS, int DIR, int MODE>
+__global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+                                                         int seg) {
+    sweep_walk_block<R, UT, NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
 // Grids with no axis longer than one cell: the RHS is the source alone.

@@ -63,6 +63,13 @@ _sigs = {
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
+    "rf_ensemble_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                          ctypes.POINTER(Laser), _vp, ctypes.POINTER(_vp)]),
+    "rf_ensemble_free": (None, [_vp]),
+    "rf_ensemble_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
+    "rf_run_ensemble": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_int32), _vp]),
+    "rf_ensemble_autotune": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_int), _vp]),
     "rf_status": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_longlong)]),
     "rf_diagnostics": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(Diag), _vp]),
 }
@@ -229,3 +236,53 @@ def diagnostics(ctx: Context, U, T, stream=None) -> dict:
     d = Diag()
     _check(_lib.rf_diagnostics(ctx.handle, _ptr(U), _ptr(T), ctypes.byref(d), _stream(stream)), "rf_diagnostics")
     return {"total": np.array(d.total[:d.nv]), "heat_release": d.heat_release, "max_T": d.max_T}
+
+
+ENS_LOOP, ENS_BATCHED, ENS_GRAPH, ENS_PERSISTENT, ENS_PERSISTENT_GRAPH = 0, 1, 2, 3, 4
+
+
+class Ensemble:
+    """Members (contexts with their states, lasers and times) advanced together
+    (rf_ensemble_create / rf_ensemble_free)."""
+
+    def __init__(self, ctxs, Us, Ts, lasers, t_dev):
+        n = len(ctxs)
+        self._keep = (list(ctxs), list(Us), list(Ts), t_dev)
+        hs = (_vp * n)(*[c.handle.value for c in ctxs])
+        us = (_vp * n)(*[_ptr(u) for u in Us])
+        ts = (_vp * n)(*[_ptr(t) for t in Ts])
+        ls = (Laser * n)(*[(_laser(l) if l is not None else Laser()) for l in lasers]) if lasers is not None else None
+        h = _vp()
+        _check(_lib.rf_ensemble_create(hs, n, us, ts, ls, _ptr(t_dev), ctypes.byref(h)), "rf_ensemble_create")
+        self.handle = h
+        self.n = n
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            _lib.rf_ensemble_free(self.handle)
+            self.handle = None
+
+
+def ensemble_create(ctxs, Us, Ts, lasers, t_dev) -> Ensemble:
+    return Ensemble(ctxs, Us, Ts, lasers, t_dev)
+
+
+def ensemble_set_option(e: Ensemble, key: str, value: float):
+    _check(_lib.rf_ensemble_set_option(e.handle, key.encode(), float(value)), "rf_ensemble_set_option")
+
+
+def run_ensemble(e: Ensemble, nsteps: int, mode: int = ENS_GRAPH, cfl: float = 0.5, dt_fixed: float = 0.0,
+                 stream=None, raise_on_error: bool = True):
+    """Returns (code, per-member codes)."""
+    st = (ctypes.c_int32 * e.n)()
+    code = _lib.rf_run_ensemble(e.handle, int(nsteps), int(mode), float(cfl), float(dt_fixed), st, _stream(stream))
+    if raise_on_error:
+        _check(code, "rf_run_ensemble")
+    return code, list(st)
+
+
+def ensemble_autotune(e: Ensemble, mode: int = ENS_GRAPH, cfl: float = 0.5, stream=None) -> int:
+    seg = ctypes.c_int(0)
+    _check(_lib.rf_ensemble_autotune(e.handle, int(mode), float(cfl), ctypes.byref(seg), _stream(stream)),
+           "rf_ensemble_autotune")
+    return seg.value
