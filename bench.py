@@ -342,12 +342,12 @@ def run_ensemble_leg(args, dev):
         c.prim = None
     t = torch.zeros(len(cases), dtype=torch.float64, device=dev)
     e = nv.ensemble_create(ctxs, Us, Ts, [c.laser.as_tuple() for c in cases], t)
-    seg = nv.ensemble_autotune(e, nv.ENS_PERSISTENT_GRAPH, 0.5)
+    seg = nv.ensemble_autotune(e, nv.ENS_GRAPH, 0.5)
     cells = sum(c.grid.ncells for c in cases)
     out = {"members": len(cases), "cells": cells, "walk_seg_autotuned": seg, "steps": args.ensemble_steps}
     s = torch.cuda.current_stream()
     for name, mode in (("member_loop", nv.ENS_LOOP), ("batched_graph", nv.ENS_GRAPH),
-                       ("persistent_graph", nv.ENS_PERSISTENT_GRAPH)):
+                       ("persistent", nv.ENS_PERSISTENT)):
         nv.run_ensemble(e, 1, mode, 0.5)                 # warm-up (captures the graph)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -359,7 +359,7 @@ def run_ensemble_leg(args, dev):
         out[name] = {"members_per_s": len(cases) * args.ensemble_steps / (ms * 1e-3),
                      "cell_updates_per_s": cells * 3 * args.ensemble_steps / (ms * 1e-3),
                      "ms_per_step": ms / args.ensemble_steps, "failed_members": sum(1 for x in st if x)}
-    out["speedup_persistent_vs_loop"] = out["persistent_graph"]["members_per_s"] / out["member_loop"]["members_per_s"]
+    out["speedup_persistent_vs_loop"] = out["persistent"]["members_per_s"] / out["member_loop"]["members_per_s"]
     out["speedup_batched_vs_loop"] = out["batched_graph"]["members_per_s"] / out["member_loop"]["members_per_s"]
     del e, ctxs, Us, Ts
     torch.cuda.empty_cache()

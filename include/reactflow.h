@@ -74,8 +74,10 @@ enum rf_flags {           /* switches for tests; 0 = full method */
 /* Mechanism description (host arrays, copied by rf_init_mechanism).
  * Paper: Methods, Governing equations (EOS, NASA fits, Wilke's rule,
  * mixture-averaged diffusion) and Methods, Combustion chemistry (finite-rate
- * Arrhenius reactions).  Ns in {1, 2, 4, 9}; Nr <= 64; every species uses the
- * same T_mid; at most 3 reactant and 3 product molecules per reaction. */
+ * Arrhenius reactions).  Ns in {1, 2, 4, 9}; Nr <= 32; every species uses the
+ * same T_mid; at most 3 reactant and 3 product molecules per reaction.  At most
+ * six mechanisms can be in use on a device at a time (each occupies a slot of
+ * constant memory from its first context until rf_free_mechanism). */
 typedef struct {
     int n_species;            /* Ns */
     int n_reactions;          /* Nr */
@@ -212,8 +214,8 @@ int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value);
  * mode 2: mode 1 captured once as a CUDA graph of one step, replayed;
  * mode 3: one persistent cooperative launch per RK stage (grid barriers between
  *         the phases, each bounded: a wait that runs out returns RF_ETIMEOUT);
- * mode 4: mode 3 captured as a CUDA graph.
- * Modes 1-4 need every member with nx, ny, nz > 1.  A member whose state fails
+ *         the three launches of a step are issued directly, not captured.
+ * Modes 1-3 need every member with nx, ny, nz > 1.  A member whose state fails
  * (Newton, non-finite, range) is frozen at its last good step and the others
  * continue; member_status (host, n ints, may be NULL) receives each member's
  * RF_E* code.  Synchronous.  Returns RF_ETIMEOUT if a barrier gave up, a member's
@@ -222,7 +224,7 @@ int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value);
 int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl, double dt_fixed, int32_t *member_status,
                     rf_stream s);
 
-/* Picks the y / z walk segment length of a batched mode (1-4) by timing trial
+/* Picks the y / z walk segment length of a batched mode (1-3) by timing trial
  * steps of the ensemble itself for 8, 16 and 32 cells, then restores every
  * member's state and time; *seg_out (may be NULL) receives the choice.  The halo
  * is fixed at two cells by the WENO3-Z stencil and is not a tuning parameter. */

@@ -31,7 +31,9 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     if not force and up_to_date():
         return OUT
     os.makedirs(os.path.dirname(OUT), exist_ok=True)
-    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    # -fmad=false: only explicit fma() fuses, so every kernel that inlines the same
+    # device code (single-grid and ensemble launches) rounds identically.
+    cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-fmad=false", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr",
            "-cudart", "static", *extra, *sources(), "-o", OUT + ".tmp"]
     if verbose:

@@ -38,7 +38,7 @@ static int fail(int code, const char *fmt, ...) {
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \
         if (e_ != cudaSuccess)                                                                     \
-            return fail(e_ == cudaErrorMemoryAllocation ? RF_ENOMEM : RF_ECUDA, "%s: %s (%s:%d)", #call, \
+            return (void)cudaGetLastError(), fail(e_ == cudaErrorMemoryAllocation ? RF_ENOMEM : RF_ECUDA, "%s: %s (%s:%d)", #call, \
                         cudaGetErrorString(e_), __FILE__, __LINE__);                                \
     } while (0)
 
@@ -53,15 +53,45 @@ extern "C" const char *rf_last_error(void) { return g_err.c_str(); }
 
 // ----------------------------------------------------------------------------- objects
 
+static constexpr int RF_MAX_DEVICES = 64;
+
 struct rf_mech {
     MechDev d;
     int ns, nr;
+    int slot[RF_MAX_DEVICES];        // constant-memory slot per device, -1 if not uploaded
 };
+
+// Owners of the constant-memory mechanism slots of every device.
+static std::mutex g_slot_mutex;
+static const rf_mech *g_slot_owner[RF_MAX_DEVICES][MECH_SLOTS];
+
+// Constant-memory slot of m on the current device, uploading it on first use.
+static int mech_slot(const rf_mech *mc, int *out) {
+    rf_mech *m = const_cast<rf_mech *>(mc);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_slot_mutex);
+    if (m->slot[dev] >= 0) {
+        *out = m->slot[dev];
+        return RF_OK;
+    }
+    for (int k = 0; k < MECH_SLOTS; ++k) {
+        if (g_slot_owner[dev][k]) continue;
+        CUDA_TRY(cudaMemcpyToSymbol(c_mech, &m->d, sizeof(MechDev), k * sizeof(MechDev)));
+        g_slot_owner[dev][k] = m;
+        m->slot[dev] = k;
+        *out = k;
+        return RF_OK;
+    }
+    return fail(RF_EINVAL, "at most %d mechanisms can be in use on one device (free unused ones)", MECH_SLOTS);
+}
 
 enum { PROF_CELL = 0, PROF_SWEEP_X = 1, PROF_SWEEP_Y = 2, PROF_SWEEP_Z = 3, PROF_OTHER = 4, RF_NPROF = 5 };
 
 struct rf_ctx {
     const rf_mech *mech;
+    int mslot = 0;                           // constant-memory slot of the mechanism
     rf_grid_desc g;
     int precision;
     uint32_t flags;
@@ -123,6 +153,7 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
         return fail(RF_EINVAL, "rf_init_mechanism: null reaction array");
     rf_mech *m = new rf_mech();
     std::memset(&m->d, 0, sizeof(MechDev));
+    for (int k = 0; k < RF_MAX_DEVICES; ++k) m->slot[k] = -1;
     MechDev &M = m->d;
     M.ns = ns;
     M.nr = nr;
@@ -238,7 +269,15 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
     return RF_OK;
 }
 
-extern "C" void rf_free_mechanism(rf_mech *m) { delete m; }
+extern "C" void rf_free_mechanism(rf_mech *m) {
+    if (!m) return;
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mutex);
+        for (int dev = 0; dev < RF_MAX_DEVICES; ++dev)
+            if (m->slot[dev] >= 0 && g_slot_owner[dev][m->slot[dev]] == m) g_slot_owner[dev][m->slot[dev]] = nullptr;
+    }
+    delete m;
+}
 
 static void free_ctx_buffers(rf_ctx *c) {
     void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag};
@@ -272,8 +311,14 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     for (int a = 0; a < 3; ++a)
         if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_create_ctx: bc[%d] = %d unknown", a, g->bc[a]);
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
+    int mslot = 0;
+    {
+        int rc = mech_slot(m, &mslot);
+        if (rc) return rc;
+    }
     rf_ctx *c = new rf_ctx();
     c->mech = m;
+    c->mslot = mslot;
     c->g = *g;
     c->precision = precision;
     c->flags = flags;
@@ -375,7 +420,7 @@ struct Path {
         const long long nb = (c->n + B - 1) / B;
         const size_t smem = (size_t)B * NS * (3 * sizeof(double) + 2 * sizeof(R) + (sizeof(R) == 4 ? sizeof(R) : 0));
         ProfScope ps(c, PROF_CELL, s);
-        cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mech->d, m, c->newton_maxit);
+        cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mslot, m, c->newton_maxit);
         LAUNCH_CHECK();
         return RF_OK;
     }
@@ -400,16 +445,16 @@ struct Path {
             const int blocks = (nrows + rpb - 1) / rpb;
             const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
             ProfScope ps(c, PROF_SWEEP_X, s);
-            sweep_x_kernel<R, UT, NS, MODE><<<blocks, threads, smem, s>>>(c->mech->d, m, W, rpb);
+            sweep_x_kernel<R, UT, NS, MODE><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
         } else {
             const int nd = dir == 1 ? c->g.ny : c->g.nz;
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             dim3 grid((unsigned)((lines + c->walk_block - 1) / c->walk_block), (unsigned)((nd + c->walk_seg - 1) / c->walk_seg));
             ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
             if (dir == 1)
-                sweep_walk_kernel<R, UT, NS, 1, MODE><<<grid, c->walk_block, 0, s>>>(c->mech->d, m, c->walk_seg);
+                sweep_walk_kernel<R, UT, NS, 1, MODE><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
             else
-                sweep_walk_kernel<R, UT, NS, 2, MODE><<<grid, c->walk_block, 0, s>>>(c->mech->d, m, c->walk_seg);
+                sweep_walk_kernel<R, UT, NS, 2, MODE><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
         }
         LAUNCH_CHECK();
         return RF_OK;
@@ -489,7 +534,7 @@ struct Path {
     }
 
     static int init_state(rf_ctx *c, const double *prim, double *U, double *T, cudaStream_t s) {
-        init_state_kernel<NS><<<(unsigned)((c->n + 127) / 128), 128, 0, s>>>(c->mech->d, prim, U, T, c->n);
+        init_state_kernel<NS><<<(unsigned)((c->n + 127) / 128), 128, 0, s>>>(c->mslot, prim, U, T, c->n);
         LAUNCH_CHECK();
         return RF_OK;
     }
@@ -500,7 +545,7 @@ struct Path {
         m.T = T;
         const int B = 64;
         const size_t smem = (size_t)B * NS * 5 * sizeof(double);
-        diag_kernel<NS><<<c->diag_blocks, B, smem, s>>>(c->mech->d, m, c->diag, c->newton_maxit);
+        diag_kernel<NS><<<c->diag_blocks, B, smem, s>>>(c->mslot, m, c->diag, c->newton_maxit);
         LAUNCH_CHECK();
         const int nvals = NS + 6;
         double *res = c->diag + (size_t)c->diag_blocks * nvals;
@@ -639,8 +684,11 @@ struct rf_ensemble {
     unsigned int bar_extra = 0;              // tests: arrivals a barrier waits for beyond the grid
     size_t smem_cell = 0, smem_x = 0;
     int coop_blocks = 0;
+    int mslot = 0;
     cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
-    double graph_cfl[4] = {0, 0, 0, 0}, graph_dt[4] = {0, 0, 0, 0};
+    size_t graph_nodes[4] = {0, 0, 0, 0};
+    cudaStream_t cap = nullptr;               // private stream for graph capture and replay
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;   // order the private stream after / before the caller's
 };
 
 static void ens_free_device(rf_ensemble *e) {
@@ -657,6 +705,9 @@ extern "C" void rf_ensemble_free(rf_ensemble *e) {
     ens_free_device(e);
     if (e->d_bar) cudaFree(e->d_bar);
     if (e->d_timeout) cudaFree(e->d_timeout);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->ev_in) cudaEventDestroy(e->ev_in);
+    if (e->ev_out) cudaEventDestroy(e->ev_out);
     delete e;
 }
 
@@ -767,7 +818,7 @@ struct EnsPath {
 
     // one step as one launch per phase (mode 1/2)
     static int step_batched(rf_ensemble *e, cudaStream_t s) {
-        const MechDev &M = e->mech->d;
+        const int M = e->mslot;
         for (int k = 0; k < 3; ++k) {
             EnsDev E0 = ens_dev(e, e->nitems[0]);
             ens_cell_kernel<R, NS><<<e->nitems[0], 128, e->smem_cell, s>>>(M, E0, k);
@@ -804,7 +855,7 @@ struct EnsPath {
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            CUDA_TRY(cudaLaunchKernelEx(&cfg, ens_stage_kernel<R, NS>, e->mech->d, E, k));
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, ens_stage_kernel<R, NS>, e->mslot, E, k));
         }
         return RF_OK;
     }
@@ -849,6 +900,7 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
         }
         if (i == 0) {
             e->mech = c->mech;
+            e->mslot = c->mslot;
             e->precision = c->precision;
             e->ns = c->ns;
         } else if (c->mech != e->mech || c->precision != e->precision) {
@@ -868,6 +920,9 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
     if (er == cudaSuccess) er = cudaMalloc((void **)&e->d_timeout, sizeof(int));
     if (er == cudaSuccess) er = cudaMemset(e->d_bar, 0, 2 * sizeof(unsigned int));
     if (er == cudaSuccess) er = cudaMemset(e->d_timeout, 0, sizeof(int));
+    if (er == cudaSuccess) er = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
+    if (er == cudaSuccess) er = cudaEventCreateWithFlags(&e->ev_in, cudaEventDisableTiming);
+    if (er == cudaSuccess) er = cudaEventCreateWithFlags(&e->ev_out, cudaEventDisableTiming);
     if (er != cudaSuccess) {
         rf_ensemble_free(e);
         return fail(RF_ENOMEM, "rf_ensemble_create: %s", cudaGetErrorString(er));
@@ -931,7 +986,7 @@ static int status_code(int st) {
 
 extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl, double dt_fixed, int32_t *member_status,
                                rf_stream stream) {
-    if (!e || nsteps < 0 || mode < 0 || mode > 4) return fail(RF_EINVAL, "rf_run_ensemble: bad argument");
+    if (!e || nsteps < 0 || mode < 0 || mode > 3) return fail(RF_EINVAL, "rf_run_ensemble: bad argument");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_run_ensemble: need dt_fixed > 0 or cfl > 0");
     if (mode > 0 && !e->all3d) return fail(RF_EINVAL, "rf_run_ensemble: batched modes need every member with nx, ny, nz > 1");
     cudaStream_t s = (cudaStream_t)stream;
@@ -946,22 +1001,42 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
         EnsDev E = ens_dev(e, 1);
         ens_begin_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(E, e->t_dev, cfl, dt_fixed);
         LAUNCH_CHECK();
-        const bool graph = mode == 2 || mode == 4;
+        const bool graph = mode == 2;
         if (graph && nsteps > 0 && !e->graph[mode]) {
+            // captured on the ensemble's own stream: capture records, it does not run anything
             cudaGraph_t g;
-            CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            int rc = ens_step(e, mode, cfl, dt_fixed, s);
-            cudaError_t ce = cudaStreamEndCapture(s, &g);
+            CUDA_TRY(cudaStreamBeginCapture(e->cap, cudaStreamCaptureModeThreadLocal));
+            int rc = ens_step(e, mode, cfl, dt_fixed, e->cap);
+            cudaError_t ce = cudaStreamEndCapture(e->cap, &g);
             if (rc) return rc;
             if (ce != cudaSuccess) return fail(RF_ECUDA, "rf_run_ensemble: graph capture: %s", cudaGetErrorString(ce));
-            ce = cudaGraphInstantiate(&e->graph[mode], g, 0);
+            size_t nodes = 0;
+            cudaGraphGetNodes(g, nullptr, &nodes);
+            cudaGraphExec_t ex = nullptr;
+            ce = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
-            if (ce != cudaSuccess) return fail(RF_ECUDA, "rf_run_ensemble: graph instantiate: %s", cudaGetErrorString(ce));
+            if (ce != cudaSuccess)
+                return fail(RF_ECUDA, "rf_run_ensemble: graph instantiate (%zu nodes): %s", nodes, cudaGetErrorString(ce));
+            if (!ex) return fail(RF_ECUDA, "rf_run_ensemble: graph instantiate returned no executable (%zu nodes)", nodes);
+            e->graph[mode] = ex;
+            e->graph_nodes[mode] = nodes;
         }
-        for (int k = 0; k < nsteps; ++k) {
-            if (graph) {
-                CUDA_TRY(cudaGraphLaunch(e->graph[mode], s));
-            } else {
+        if (graph && nsteps > 0) {
+            // replay on the ensemble's stream, ordered after and before the caller's stream
+            CUDA_TRY(cudaEventRecord(e->ev_in, s));
+            CUDA_TRY(cudaStreamWaitEvent(e->cap, e->ev_in, 0));
+            for (int k = 0; k < nsteps; ++k) {
+                cudaError_t le = cudaGraphLaunch(e->graph[mode], e->cap);
+                if (le != cudaSuccess) {
+                    (void)cudaGetLastError();
+                    return fail(RF_ECUDA, "rf_run_ensemble: cudaGraphLaunch (mode %d, %zu nodes, step %d): %s", mode,
+                                e->graph_nodes[mode], k, cudaGetErrorString(le));
+                }
+            }
+            CUDA_TRY(cudaEventRecord(e->ev_out, e->cap));
+            CUDA_TRY(cudaStreamWaitEvent(s, e->ev_out, 0));
+        } else {
+            for (int k = 0; k < nsteps; ++k) {
                 int rc = ens_step(e, mode, cfl, dt_fixed, s);
                 if (rc) return rc;
             }
@@ -992,7 +1067,7 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
 }
 
 extern "C" int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_stream stream) {
-    if (!e || mode < 1 || mode > 4) return fail(RF_EINVAL, "rf_ensemble_autotune: bad argument");
+    if (!e || mode < 1 || mode > 3) return fail(RF_EINVAL, "rf_ensemble_autotune: bad argument");
     if (!e->all3d) return fail(RF_EINVAL, "rf_ensemble_autotune: batched modes need 3-D members");
     cudaStream_t s = (cudaStream_t)stream;
     // keep the states: trial steps run on them and are rolled back
@@ -1143,12 +1218,18 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
         }
         base = g_noalloc_dev[dev];
     }
+    int mslot = 0;
+    {
+        int rc = mech_slot(m, &mslot);
+        if (rc) return rc;
+    }
     cudaStream_t st = (cudaStream_t)s;
     // the header persists between calls: clear the status word, reset the bad-cell index
     CUDA_TRY(cudaMemsetAsync(base, 0, sizeof(int) * 2, st));
     CUDA_TRY(cudaMemsetAsync(base + 8, 0xff, sizeof(long long), st));
     rf_ctx c;                                  // descriptor only: every buffer points into the scratch
     c.mech = m;
+    c.mslot = mslot;
     c.g = *g;
     c.precision = precision;
     c.flags = flags;

@@ -13,7 +13,7 @@
 namespace rf {
 
 constexpr int NSMAX = 9;
-constexpr int NRMAX = 64;
+constexpr int NRMAX = 32;
 constexpr double RU = 8.314462618;    // J/mol/K
 constexpr double PATM = 101325.0;     // Pa
 constexpr double EPS_WENO = 1.0e-30;
@@ -22,8 +22,7 @@ constexpr double T_MAX_ADMISSIBLE = 1.0e5;
 
 enum StatusBits : int { ST_NEWTON = 1, ST_NONFINITE = 2, ST_RANGE = 4, ST_TIMEOUT = 8 };
 
-// Mechanism constants, passed to every kernel by value (__grid_constant__),
-// so that reads come from the constant bank.
+// Mechanism constants (species, NASA-7 sets, transport, compact reactions).
 struct MechDev {
     int ns, nr, two_ranges, pad_;
     double Tmid;
@@ -49,6 +48,12 @@ struct MechDev {
     int8_t n_net[NRMAX], net_sp[NRMAX][6], net_nu[NRMAX][6];
     int8_t dnu_sum[NRMAX], rev[NRMAX];
 };
+
+// Mechanisms in use live in constant-memory slots; kernels receive the slot
+// index, so their constants are read through the constant cache and graph
+// nodes carry no large parameter block.
+constexpr int MECH_SLOTS = 6;
+__constant__ MechDev c_mech[MECH_SLOTS];
 
 // One grid and the buffers of one evaluation or RK stage.
 struct Member {

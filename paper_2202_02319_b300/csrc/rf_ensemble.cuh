@@ -100,8 +100,9 @@ __device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E
 // ----------------------------------------------------------------------------- one launch per phase
 
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) ens_cell_kernel(const __grid_constant__ MechDev M, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128) ens_cell_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                        int stage) {
+    const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok;
@@ -109,8 +110,9 @@ __global__ void __launch_bounds__(128) ens_cell_kernel(const __grid_constant__ M
 }
 
 template <typename R, typename UT, int NS, int MODE>
-__global__ void __launch_bounds__(128) ens_x_kernel(const __grid_constant__ MechDev M, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128) ens_x_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                     int stage) {
+    const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok;
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(128) ens_x_kernel(const __grid_constant__ Mech
 }
 
 template <typename R, typename UT, int NS, int DIR, int MODE>
-__global__ void __launch_bounds__(128) ens_walk_kernel(const __grid_constant__ MechDev M, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128) ens_walk_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                        int stage) {
+    const MechDev &M = c_mech[mslot];
     __shared__ Member sm;
     __shared__ int s_ok;
     ens_walk_phase<R, UT, NS, DIR, MODE>(M, E, stage, sm, s_ok);
@@ -136,7 +139,8 @@ __global__ void ens_begin_kernel(const __grid_constant__ EnsDev E, const double 
     m.rates[0] = m.rates[1] = m.rates[2] = 0ull;
 }
 
-__global__ void ens_dt_kernel(const __grid_constant__ MechDev M, const __grid_constant__ EnsDev E) {
+__global__ void ens_dt_kernel(int mslot, const __grid_constant__ EnsDev E) {
+    const MechDev &M = c_mech[mslot];
     const int mi = blockIdx.x * blockDim.x + threadIdx.x;
     if (mi >= E.nmembers) return;
     member_dt(M, E.tab[0][mi]);
@@ -199,12 +203,14 @@ __device__ __forceinline__ bool grid_barrier(const EnsDev &E, int &s_flag) {
 // time step), x, y and z sweeps, (stage 3: clock advance), separated by grid
 // barriers.  Members must have nx, ny, nz > 1 (the z sweep performs the update).
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) ens_stage_kernel(const __grid_constant__ MechDev M, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128) ens_stage_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                         int stage) {
+    const MechDev &M = c_mech[mslot];
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok, s_flag;
+    if (*(volatile int *)E.timeout) return;     // an earlier stage of this step gave up: run nothing
     ens_cell_phase<R, NS>(M, E, stage, smem_raw, sm, s_ok);
     if (!grid_barrier(E, s_flag)) return;
     if (stage == 0) {

@@ -307,8 +307,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 }
 
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) cell_state_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+__global__ void __launch_bounds__(128) cell_state_kernel(int mslot, const __grid_constant__ Member m,
                                                          int newton_maxit) {
+    const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cell_state_block<R, NS>(M, m, blockIdx.x, smem_raw, newton_maxit);
 }
@@ -534,8 +535,9 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
 }
 
 template <typename R, typename UT, int NS, int MODE>
-__global__ void __launch_bounds__(256) sweep_x_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+__global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_constant__ Member m,
                                                       int W, int rpb) {
+    const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     sweep_x_block<R, UT, NS, MODE>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
@@ -579,8 +581,9 @@ __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member 
 }
 
 template <typename R, typename UT, int NS, int DIR, int MODE>
-__global__ void __launch_bounds__(128) sweep_walk_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+__global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid_constant__ Member m,
                                                          int seg) {
+    const MechDev &M = c_mech[mslot];
     sweep_walk_block<R, UT, NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
@@ -636,8 +639,9 @@ __global__ void step_end_kernel(double *clock, double *t_out) {
 // ----------------------------------------------------------------------------- init state
 
 template <int NS>
-__global__ void init_state_kernel(const __grid_constant__ MechDev M, const double *__restrict__ prim, double *__restrict__ U,
+__global__ void init_state_kernel(int mslot, const double *__restrict__ prim, double *__restrict__ U,
                                   double *__restrict__ Tout, long long n) {
+    const MechDev &M = c_mech[mslot];
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (cell >= n) return;
     const double p = prim[cell], T = prim[n + cell];
@@ -669,8 +673,9 @@ __global__ void init_state_kernel(const __grid_constant__ MechDev M, const doubl
 // Per-block partial sums of U_v dV, HRR dV and the block max of T; a second
 // kernel folds the partials in block order (deterministic).
 template <int NS>
-__global__ void __launch_bounds__(64) diag_kernel(const __grid_constant__ MechDev M, const __grid_constant__ Member m,
+__global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_constant__ Member m,
                                                    double *partial, int newton_maxit) {
+    const MechDev &M = c_mech[mslot];
     constexpr int NV = NS + 4;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int B = blockDim.x, tid = threadIdx.x;

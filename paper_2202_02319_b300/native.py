@@ -238,7 +238,7 @@ def diagnostics(ctx: Context, U, T, stream=None) -> dict:
     return {"total": np.array(d.total[:d.nv]), "heat_release": d.heat_release, "max_T": d.max_T}
 
 
-ENS_LOOP, ENS_BATCHED, ENS_GRAPH, ENS_PERSISTENT, ENS_PERSISTENT_GRAPH = 0, 1, 2, 3, 4
+ENS_LOOP, ENS_BATCHED, ENS_GRAPH, ENS_PERSISTENT = 0, 1, 2, 3
 
 
 class Ensemble:

@@ -41,12 +41,12 @@ def test_batched_modes_equal_member_loop_bitwise(precision):
     from paper_2202_02319_b300 import native as nv
     cases = _members()
     res = {}
-    for mode in (0, 1, 2, 3, 4):
+    for mode in (0, 1, 2, 3):
         mech, ctxs, Us, Ts, t, e = _setup(cases, precision)
         code, st = nv.run_ensemble(e, 3, mode, 0.5)
         assert code == 0 and st == [0] * len(cases)
         res[mode] = ([u.cpu() for u in Us], t.cpu())
-    for mode in (1, 2, 3, 4):
+    for mode in (1, 2, 3):
         for m in range(len(cases)):
             assert torch.equal(res[mode][0][m], res[0][0][m]), (mode, m)
         assert torch.equal(res[mode][1], res[0][1])
