@@ -189,6 +189,35 @@ int rf_status(rf_ctx *c, rf_stream s, long long *cell_out);
  * state U (with T as Newton warm start).  Synchronous (result on the host). */
 int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s);
 
+/* Discrete adjoint of the FP64 RHS (paper: the sensitivity question of
+ * Application examples, Ignition of a diffusion flame / model combustor;
+ * the method's RHS as in rf_rhs).  FP64 contexts only (RF_EINVAL otherwise).
+ * Parameters p = (E, x0, y0, z0, sigma_r, ln A_0 .. ln A_{Nr-1}); grad_params
+ * (device, 5 + Nr doubles) is accumulated into, as is lam_U (device, [Ns+4][N]).
+ *
+ * rf_adjoint_rhs: lam_U += (dR/dU)^T lam_dUdt + w_hrr dH/dU and grad_params +=
+ * (dR/dp)^T lam_dUdt + w_hrr dH/dp, R = dU/dt of U at time t, H = sum over cells
+ * of the heat-release rate -sum_s h_s omega_s times the cell volume.  lam_dUdt
+ * (device, [Ns+4][N]) may be NULL (objective term only).  T (device) is the
+ * Newton warm start in and the temperature of U out.  Non-smooth points take the
+ * subgradient of the branch the forward evaluation took.  Asynchronous. */
+int rf_adjoint_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *laser, const double *lam_dUdt,
+                   double w_hrr, double *lam_U, double *grad_params, rf_stream s);
+
+/* One SSP-RK3 step at fixed dt through rf_rhs evaluations and stage
+ * combinations (the arithmetic rf_adjoint_rk_step differentiates): U and T are
+ * advanced in place and, if J (host) is not NULL, *J += dt (H(U^n) + H(U^(1)) +
+ * 4 H(U^(2))) / 6.  Synchronous. */
+int rf_rk_step_objective(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *laser, double *J,
+                         rf_stream s);
+
+/* Reverse of rf_rk_step_objective from U_n (device, not modified) and its
+ * temperature T_n: lam (device, [Ns+4][N]) holds dJ/dU_{n+1} on entry and
+ * dJ/dU_n on exit, with the step's objective term weighted by w_hrr;
+ * grad_params accumulates.  Recomputes the stages internally.  Asynchronous. */
+int rf_adjoint_rk_step(rf_ctx *c, const double *Un, const double *Tn, double t, double dt, const rf_laser *laser,
+                       double w_hrr, double *lam, double *grad_params, rf_stream s);
+
 /* Batched ensembles (workload shape of the paper's ensemble studies, Results,
  * Ensemble simulation; Methods, Diffusion flame): members are contexts of one
  * mechanism and precision with their own grid sizes, states and lasers.

@@ -16,6 +16,7 @@
 
 #include "reactflow.h"
 #include "rf_ensemble.cuh"
+#include "rf_adjoint.cuh"
 
 using namespace rf;
 
@@ -111,6 +112,8 @@ struct rf_ctx {
     int x_block = 256;                       // x sweep threads per block
     int walk_block = 128, walk_seg = 16;     // y / z sweeps
     size_t bytes = 0;
+    // adjoint workspace (FP64 contexts), allocated on first use
+    double *adj = nullptr;                   // Qbar [nq n], zero [nv n], R [nv n], lamS [nv n], Ub1, Ub2, Ln [nv n], T0, T1, T2 [n]
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
@@ -280,7 +283,7 @@ extern "C" void rf_free_mechanism(rf_mech *m) {
 }
 
 static void free_ctx_buffers(rf_ctx *c) {
-    void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag};
+    void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag, c->adj};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -1119,6 +1122,190 @@ extern "C" int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *s
     cudaFree(bk);
     if (seg_out) *seg_out = best;
     return rc;
+}
+
+
+// ----------------------------------------------------------------------------- adjoint
+
+struct AdjWs {
+    double *Qbar, *zero, *R, *lamS, *Ub1, *Ub2, *Ln, *T0, *T1, *T2;
+};
+
+static int adj_ws(rf_ctx *c, AdjWs &w) {
+    const size_t n = (size_t)c->n, nv = c->nv, nq = c->nq;
+    const size_t tot = nq * n + 6 * nv * n + 3 * n;
+    if (!c->adj) {
+        cudaError_t e = cudaMalloc((void **)&c->adj, tot * sizeof(double));
+        if (e != cudaSuccess) return fail(RF_ENOMEM, "adjoint workspace (%zu bytes): %s", tot * 8, cudaGetErrorString(e));
+        c->bytes += tot * sizeof(double);
+        CUDA_TRY(cudaMemset(c->adj, 0, tot * sizeof(double)));
+    }
+    double *p = c->adj;
+    w.Qbar = p;
+    p += nq * n;
+    w.zero = p;
+    p += nv * n;
+    w.R = p;
+    p += nv * n;
+    w.lamS = p;
+    p += nv * n;
+    w.Ub1 = p;
+    p += nv * n;
+    w.Ub2 = p;
+    p += nv * n;
+    w.Ln = p;
+    p += nv * n;
+    w.T0 = p;
+    p += n;
+    w.T1 = p;
+    p += n;
+    w.T2 = p;
+    return RF_OK;
+}
+
+static int axpby(double *y, const double *x, double a, double b, long long n, cudaStream_t s) {
+    axpby_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(y, x, a, b, n);
+    LAUNCH_CHECK();
+    return RF_OK;
+}
+
+template <int NS>
+struct AdjPath {
+    static int adjoint_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *L, const double *lam,
+                           double wH, double *lamU, double *grads, cudaStream_t s) {
+        AdjWs w;
+        int rc = adj_ws(c, w);
+        if (rc) return rc;
+        Member m = base_member(c);
+        m.U = U;
+        m.T = T;
+        m.t_from_host = 1;
+        m.t_host = t;
+        set_laser(m, L);
+        rc = Path<double, NS>::cell_state(c, m, s);        // Q and converged T of this state
+        if (rc) return rc;
+        CUDA_TRY(cudaMemsetAsync(w.Qbar, 0, (size_t)c->nq * c->n * sizeof(double), s));
+        const int n3[3] = {c->g.nx, c->g.ny, c->g.nz};
+        if (lam) {
+            for (int d = 0; d < 3; ++d) {
+                if (n3[d] <= 1) continue;
+                const long long nf = (long long)(c->g.bc[d] == RF_BC_PERIODIC ? n3[d] : n3[d] + 1) * (c->n / n3[d]);
+                const unsigned blocks = (unsigned)((nf + 127) / 128);
+                if (d == 0) adjoint_face_kernel<NS, 0><<<blocks, 128, 0, s>>>(m, lam, lamU, w.Qbar);
+                if (d == 1) adjoint_face_kernel<NS, 1><<<blocks, 128, 0, s>>>(m, lam, lamU, w.Qbar);
+                if (d == 2) adjoint_face_kernel<NS, 2><<<blocks, 128, 0, s>>>(m, lam, lamU, w.Qbar);
+                LAUNCH_CHECK();
+            }
+        }
+        adjoint_cell_kernel<NS><<<(unsigned)((c->n + 63) / 64), 64, 0, s>>>(c->mslot, m, w.Qbar, lam ? lam : w.zero, lamU,
+                                                                           grads, wH);
+        LAUNCH_CHECK();
+        return RF_OK;
+    }
+
+    // U_{n+1} from U_n through rhs evaluations and stage combinations (the same
+    // arithmetic the adjoint step differentiates); *J += dt sum_k b_k H(U^(k)).
+    static int step_objective(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *L, double *J,
+                              cudaStream_t s) {
+        AdjWs w;
+        int rc = adj_ws(c, w);
+        if (rc) return rc;
+        const long long N = c->n * c->nv;
+        const double b[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
+        const double *in[3] = {U, c->U1, c->U2};
+        const double ts[3] = {t, t + dt, t + 0.5 * dt};
+        double H[3];
+        for (int k = 0; k < 3; ++k) {
+            rf_diag dg;
+            rc = Path<double, NS>::diagnostics(c, in[k], T, &dg, s);
+            if (rc) return rc;
+            H[k] = dg.heat_release;
+            rc = Path<double, NS>::rhs(c, in[k], T, ts[k], L, w.R, s);
+            if (rc) return rc;
+            if (k == 0) {   // U1 = Un + dt R
+                CUDA_TRY(cudaMemcpyAsync(c->U1, U, N * 8, cudaMemcpyDeviceToDevice, s));
+                if ((rc = axpby(c->U1, w.R, dt, 1.0, N, s))) return rc;
+            } else if (k == 1) {   // U2 = 3/4 Un + 1/4 (U1 + dt R)
+                CUDA_TRY(cudaMemcpyAsync(c->U2, c->U1, N * 8, cudaMemcpyDeviceToDevice, s));
+                if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
+                if ((rc = axpby(c->U2, U, 0.75, 0.25, N, s))) return rc;
+            } else {   // Un+1 = 1/3 Un + 2/3 (U2 + dt R)
+                if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
+                if ((rc = axpby(U, c->U2, 2.0 / 3.0, 1.0 / 3.0, N, s))) return rc;
+            }
+        }
+        if (J) *J += dt * (b[0] * H[0] + b[1] * H[1] + b[2] * H[2]);
+        return RF_OK;
+    }
+
+    // lam <- (dU_{n+1}/dU_n)^T lam + wH dt sum_k b_k dH(U^(k))/dU_n; grads accumulate.
+    static int adjoint_step(rf_ctx *c, const double *Un, const double *Tn, double t, double dt, const rf_laser *L,
+                            double wH, double *lam, double *grads, cudaStream_t s) {
+        AdjWs w;
+        int rc = adj_ws(c, w);
+        if (rc) return rc;
+        const long long N = c->n * c->nv;
+        // forward recompute: U1, U2 and the converged temperatures
+        CUDA_TRY(cudaMemcpyAsync(w.T0, Tn, c->n * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = Path<double, NS>::rhs(c, Un, w.T0, t, L, w.R, s))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(c->U1, Un, N * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = axpby(c->U1, w.R, dt, 1.0, N, s))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(w.T1, w.T0, c->n * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = Path<double, NS>::rhs(c, c->U1, w.T1, t + dt, L, w.R, s))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(c->U2, c->U1, N * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
+        if ((rc = axpby(c->U2, Un, 0.75, 0.25, N, s))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(w.T2, w.T1, c->n * 8, cudaMemcpyDeviceToDevice, s));
+        // reverse: stage 3 (U2, t + dt/2)
+        CUDA_TRY(cudaMemsetAsync(w.Ub2, 0, N * 8, s));
+        CUDA_TRY(cudaMemsetAsync(w.lamS, 0, N * 8, s));
+        if ((rc = axpby(w.lamS, lam, 2.0 / 3.0 * dt, 0.0, N, s))) return rc;
+        if ((rc = adjoint_rhs(c, c->U2, w.T2, t + 0.5 * dt, L, w.lamS, wH * dt * (2.0 / 3.0), w.Ub2, grads, s))) return rc;
+        if ((rc = axpby(w.Ub2, lam, 2.0 / 3.0, 1.0, N, s))) return rc;
+        // stage 2 (U1, t + dt)
+        CUDA_TRY(cudaMemsetAsync(w.Ub1, 0, N * 8, s));
+        if ((rc = axpby(w.lamS, w.Ub2, 0.25 * dt, 0.0, N, s))) return rc;
+        if ((rc = adjoint_rhs(c, c->U1, w.T1, t + dt, L, w.lamS, wH * dt / 6.0, w.Ub1, grads, s))) return rc;
+        if ((rc = axpby(w.Ub1, w.Ub2, 0.25, 1.0, N, s))) return rc;
+        // stage 1 (Un, t): lam_n = 1/3 lam + 3/4 Ub2 + Ub1 + VJP(Un, dt Ub1)
+        CUDA_TRY(cudaMemcpyAsync(w.Ln, w.Ub1, N * 8, cudaMemcpyDeviceToDevice, s));
+        if ((rc = axpby(w.Ln, w.Ub2, 0.75, 1.0, N, s))) return rc;
+        if ((rc = axpby(w.Ln, lam, 1.0 / 3.0, 1.0, N, s))) return rc;
+        if ((rc = axpby(w.lamS, w.Ub1, dt, 0.0, N, s))) return rc;
+        if ((rc = adjoint_rhs(c, Un, w.T0, t, L, w.lamS, wH * dt / 6.0, w.Ln, grads, s))) return rc;
+        CUDA_TRY(cudaMemcpyAsync(lam, w.Ln, N * 8, cudaMemcpyDeviceToDevice, s));
+        return RF_OK;
+    }
+};
+
+#define ADJ_DISPATCH(c, CALL)                                                        \
+    do {                                                                             \
+        if ((c)->precision != RF_FP64) return fail(RF_EINVAL, "adjoint: FP64 contexts only"); \
+        switch ((c)->ns) {                                                           \
+            case 1: return AdjPath<1>::CALL;                                         \
+            case 2: return AdjPath<2>::CALL;                                         \
+            case 4: return AdjPath<4>::CALL;                                         \
+            case 9: return AdjPath<9>::CALL;                                         \
+        }                                                                            \
+        return fail(RF_EINVAL, "unsupported species count %d", (c)->ns);             \
+    } while (0)
+
+extern "C" int rf_adjoint_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *L, const double *lam_dUdt,
+                              double w_hrr, double *lam_U, double *grad_params, rf_stream s) {
+    if (!c || !U || !T || !lam_U || !grad_params) return fail(RF_EINVAL, "rf_adjoint_rhs: null argument");
+    ADJ_DISPATCH(c, adjoint_rhs(c, U, T, t, L, lam_dUdt, w_hrr, lam_U, grad_params, (cudaStream_t)s));
+}
+
+extern "C" int rf_rk_step_objective(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *L, double *J,
+                                    rf_stream s) {
+    if (!c || !U || !T || !(dt > 0.0)) return fail(RF_EINVAL, "rf_rk_step_objective: bad argument");
+    ADJ_DISPATCH(c, step_objective(c, U, T, t, dt, L, J, (cudaStream_t)s));
+}
+
+extern "C" int rf_adjoint_rk_step(rf_ctx *c, const double *Un, const double *Tn, double t, double dt, const rf_laser *L,
+                                  double w_hrr, double *lam, double *grad_params, rf_stream s) {
+    if (!c || !Un || !Tn || !lam || !grad_params || !(dt > 0.0)) return fail(RF_EINVAL, "rf_adjoint_rk_step: bad argument");
+    ADJ_DISPATCH(c, adjoint_step(c, Un, Tn, t, dt, L, w_hrr, lam, grad_params, (cudaStream_t)s));
 }
 
 // ----------------------------------------------------------------------------- peak probe

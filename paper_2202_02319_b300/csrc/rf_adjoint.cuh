@@ -1,0 +1,674 @@
+// Discrete adjoint of the FP64 right-hand side (vector-Jacobian products).
+//
+// dU/dt = S(cell) + sum_d (G_d(f+1) - G_d(f)) / h_d, G = face flux of the cell
+// fields Q (primitives, transport, enthalpies) and U.  Given lambda = dJ/d(dU/dt):
+//   1. face adjoint: G_bar(f) = (lambda(f-1) - lambda(f)) / h_d; the hand-written
+//      reverse of the face flux scatters into U_bar and Q_bar of the stencil cells
+//      (FP64 atomics);
+//   2. cell adjoint: U_bar(cell) += (dQ/dU)^T Q_bar + (dS/dU)^T lambda, with the
+//      per-cell Jacobians from forward-mode dual numbers over the cell's conserved
+//      variables (the temperature tangent is one Newton step at the converged T:
+//      dT = (de - sum_s (de/dY_s) dY_s) / cv, the implicit-function derivative).
+// Parameter gradients (laser E, x0, y0, z0, sigma_r; ln A_j) are analytic.
+// Non-smooth points take the subgradient of the forward branch: the LLF maximum
+// goes to the stencil cell that attains it, |beta1 - beta0| has slope 0 at equality.
+#pragma once
+
+#include "rf_kernels.cuh"
+
+namespace rf {
+
+// ----------------------------------------------------------------------------- dual numbers
+
+template <int K>
+struct Dual {
+    double v;
+    double d[K];
+};
+
+template <int K> __device__ __forceinline__ Dual<K> dconst(double a) {
+    Dual<K> r;
+    r.v = a;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = 0.0;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator+(const Dual<K> &a, const Dual<K> &b) {
+    Dual<K> r;
+    r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator-(const Dual<K> &a, const Dual<K> &b) {
+    Dual<K> r;
+    r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator*(const Dual<K> &a, const Dual<K> &b) {
+    Dual<K> r;
+    r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator*(const Dual<K> &a, double b) {
+    Dual<K> r;
+    r.v = a.v * b;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator*(double b, const Dual<K> &a) { return a * b; }
+template <int K> __device__ __forceinline__ Dual<K> operator+(const Dual<K> &a, double b) {
+    Dual<K> r = a;
+    r.v += b;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator-(const Dual<K> &a, double b) {
+    Dual<K> r = a;
+    r.v -= b;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> recip(const Dual<K> &a) {
+    Dual<K> r;
+    r.v = 1.0 / a.v;
+    const double g = -r.v * r.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> operator/(const Dual<K> &a, const Dual<K> &b) { return a * recip(b); }
+template <int K> __device__ __forceinline__ Dual<K> dexp(const Dual<K> &a) {
+    Dual<K> r;
+    r.v = exp(a.v);
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * r.v;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> dlog(const Dual<K> &a) {
+    Dual<K> r;
+    r.v = log(a.v);
+    const double g = 1.0 / a.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
+    return r;
+}
+template <int K> __device__ __forceinline__ Dual<K> dsqrt(const Dual<K> &a) {
+    Dual<K> r;
+    r.v = sqrt(a.v);
+    const double g = 0.5 / r.v;
+#pragma unroll
+    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
+    return r;
+}
+
+// ----------------------------------------------------------------------------- per-cell map
+
+// The cell-state map U -> (Q, omega, HRR) of the FP64 path, in dual arithmetic.
+// Tc is the converged temperature of the forward evaluation.  Outputs: Q[8+3NS]
+// in the Q field order, W[NS] = omega_s (kg/m^3/s), hrr = -sum_s h_s omega_s.
+// sbuf: per-thread scratch of 4*NS duals for the run-time-indexed chemistry.
+template <int K, int NS>
+__device__ void cell_map(const MechDev &M, const Dual<K> (&U)[NS + 4], double Tc, bool chem, Dual<K> *Q, Dual<K> *W,
+                         Dual<K> &hrr, Dual<K> *sC, Dual<K> *sP, Dual<K> *sR, Dual<K> *sWd) {
+    using D = Dual<K>;
+    constexpr int NQ = QL<NS>::NQ;
+    D rho = U[0];
+#pragma unroll
+    for (int s = 1; s < NS; ++s) rho = rho + U[s];
+    const D irho = recip(rho);
+    const D u = U[NS] * irho, v = U[NS + 1] * irho, w = U[NS + 2] * irho;
+    D Y[NS];
+    D Rm = dconst<K>(0.0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        Y[s] = U[s] * irho;
+        Rm = Rm + Y[s] * M.RW[s];
+    }
+    const D e = U[NS + 3] * irho - 0.5 * (u * u + v * v + w * w);
+    // temperature: one Newton step in dual arithmetic from the converged value
+    const int rng = nasa_range(M, Tc);
+    const double invTc = 1.0 / Tc;
+    D em = dconst<K>(0.0), cvm = dconst<K>(0.0);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const double es = (h_RT(M, rng, s, Tc, invTc) - 1.0) * M.RW[s] * Tc;
+        const double cvs = (cp_R<double>(M, rng, s, Tc) - 1.0) * M.RW[s];
+        em = em + Y[s] * es;
+        cvm = cvm + Y[s] * cvs;
+    }
+    const D T = dconst<K>(Tc) - (em - e) / cvm;
+    const D invT = recip(T);
+    // cp(T), h_s(T) as polynomials in the dual temperature
+    D cpm = dconst<K>(0.0);
+    D hs[NS], cps[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const double *a = M.cpc[rng][s];
+        cps[s] = ((((T * a[4] + a[3]) * T + a[2]) * T + a[1]) * T + a[0]) * M.RW[s];
+        cpm = cpm + Y[s] * cps[s];
+        const double *c = M.ec[rng][s];
+        const D hrt = ((((T * c[4] + c[3]) * T + c[2]) * T + c[1]) * T + c[0]) + invT * c[5];
+        hs[s] = hrt * T * M.RW[s];
+    }
+    const D cv = cpm - Rm;
+    const D p = rho * Rm * T;
+    const D c = dsqrt(cpm / cv * Rm * T);
+    Q[Q_U] = u;
+    Q[Q_V] = v;
+    Q[Q_W] = w;
+    Q[Q_P] = p;
+    Q[Q_C] = c;
+    Q[Q_T] = T;
+    D X[NS];
+    const D irm = recip(Rm);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        X[s] = Y[s] * M.RW[s] * irm;
+        Q[QL<NS>::X + s] = X[s];
+        Q[QL<NS>::H + s] = hs[s];
+    }
+    // transport
+    const D lnTs = dlog(T * (1.0 / 300.0));
+    D mus[NS], sq[NS], isq[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        mus[s] = dexp(lnTs * M.mu_exp[s]) * M.mu_ref[s];
+        sq[s] = dsqrt(mus[s]);
+        isq[s] = recip(sq[s]);
+    }
+    D mu = dconst<K>(0.0), lam = dconst<K>(0.0);
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        D den = dconst<K>(0.0);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const D a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
+            den = den + X[j] * (a * a) * M.wd[i][j];
+        }
+        const D xr = X[i] / den;
+        mu = mu + xr * mus[i];
+        lam = lam + xr * mus[i] * (cps[i] + M.eucken[i]);
+    }
+    Q[Q_MU] = mu;
+    Q[Q_LAM] = lam;
+    if (NS == 1) {
+        Q[QL<NS>::DC] = dconst<K>(0.0);
+    } else {
+        const D fT = dexp(lnTs * 1.75) * PATM / p;
+        D Xe[NS];
+        D Wbe = dconst<K>(0.0);
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            Xe[j] = X[j] + EPS_D;
+            Wbe = Wbe + Xe[j] * M.W[j];
+        }
+        const D rhoW = rho * Rm * (1.0 / RU);          // rho / Wbar
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            D num = dconst<K>(0.0), den = dconst<K>(0.0);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                if (j == s) continue;
+                num = num + Xe[j] * M.W[j];
+                den = den + Xe[j] * M.invDref[s][j];
+            }
+            const D Dm = num * fT / (Wbe * den);
+            Q[QL<NS>::DC + s] = rhoW * Dm * M.W[s];
+        }
+    }
+    // chemistry
+#pragma unroll
+    for (int s = 0; s < NS; ++s) W[s] = dconst<K>(0.0);
+    hrr = dconst<K>(0.0);
+    if (chem && M.nr > 0) {
+        const D lnT = dlog(T);
+        const D lnRTp = lnT + log(RU / PATM);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double *g = M.gc[rng][s];
+            const D gs = (((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6];
+            const D G = dexp(gs + lnRTp);
+            sC[s] = U[s] * M.invW[s];
+            sP[s] = sC[s] * G;
+            sR[s] = recip(G);
+            sWd[s] = dconst<K>(0.0);
+        }
+        for (int j = 0; j < M.nr; ++j) {
+            const D kf = dexp(lnT * M.b[j] - invT * M.Theta[j] + M.lnA[j]);
+            D cf = kf;
+            for (int k = 0; k < M.n_reac[j]; ++k) cf = cf * sC[M.reac[j][k]];
+            D q = cf;
+            if (M.rev[j]) {
+                D pr = kf;
+                for (int k = 0; k < M.n_prod[j]; ++k) pr = pr * sP[M.prod[j][k]];
+                for (int k = 0; k < M.n_reac[j]; ++k) pr = pr * sR[M.reac[j][k]];
+                q = q - pr;
+            }
+            for (int k = 0; k < M.n_net[j]; ++k) {
+                const int s = M.net_sp[j][k];
+                sWd[s] = sWd[s] + q * (double)M.net_nu[j][k];
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            W[s] = sWd[s] * M.W[s];
+            hrr = hrr - hs[s] * W[s];
+        }
+    }
+    (void)NQ;
+}
+
+// Rate of progress q_j of every reaction at a cell (FP64 values), for the
+// ln A_j gradients: d omega_s / d ln A_j = W_s nu_sj q_j.
+template <int NS>
+__device__ void rates_of_progress(const MechDev &M, const double (&rs)[NS], double T, double *qout, double *sG) {
+    const int rng = nasa_range(M, T);
+    const double invT = 1.0 / T, lnT = log(T), lnRTp = lnT + log(RU / PATM);
+    for (int s = 0; s < NS; ++s) sG[s] = exp(g_RT(M, rng, s, T, invT, lnT) + lnRTp);
+    for (int j = 0; j < M.nr; ++j) {
+        const double kf = exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
+        double cf = kf;
+        for (int k = 0; k < M.n_reac[j]; ++k) cf *= rs[M.reac[j][k]] * M.invW[M.reac[j][k]];
+        double q = cf;
+        if (M.rev[j]) {
+            double pr = kf;
+            for (int k = 0; k < M.n_prod[j]; ++k) {
+                const int s = M.prod[j][k];
+                pr *= rs[s] * M.invW[s] * sG[s];
+            }
+            for (int k = 0; k < M.n_reac[j]; ++k) pr /= sG[M.reac[j][k]];
+            q -= pr;
+        }
+        qout[j] = q;
+    }
+}
+
+// ----------------------------------------------------------------------------- cell adjoint
+
+// U_bar(cell) += (dQ/dU)^T Q_bar + (d omega/dU)^T lambda_species + wH (dHRR/dU) dV;
+// grads[5 + j] += sum_s (lambda_s + wH dV (-h_s)) W_s nu_sj q_j (ln A_j);
+// grads[0..4] += lambda_E dq_L/d(E, x0, y0, z0, sigma_r).
+template <int NS>
+__global__ void __launch_bounds__(64) adjoint_cell_kernel(int mslot, const __grid_constant__ Member m,
+                                                          const double *__restrict__ Qbar, const double *__restrict__ lam,
+                                                          double *__restrict__ Ubar, double *__restrict__ grads,
+                                                          double wH) {
+    const MechDev &M = c_mech[mslot];
+    constexpr int NV = NS + 4, NQ = QL<NS>::NQ, K = 4;
+    using D = Dual<K>;
+    const long long n = m.n;
+    const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double red[5 + NRMAX][64];
+    double gl[5 + NRMAX];
+    for (int q = 0; q < 5 + NRMAX; ++q) gl[q] = 0.0;
+    const bool chem = !(m.flags & F_NO_CHEM);
+    const double dV = m.h[0] * m.h[1] * m.h[2];
+    if (cell < n) {
+        double Uv[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Uv[v] = m.U[v * n + cell];
+        const double Tc = m.T[cell];
+        D Uin[NV], Qo[NQ], Wo[NS], hrr, sC[NS], sP[NS], sR[NS], sWd[NS];
+        for (int k0 = 0; k0 < NV; k0 += K) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Uin[v] = dconst<K>(Uv[v]);
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (v == k0 + k) Uin[v].d[k] = 1.0;
+            }
+            cell_map<K, NS>(M, Uin, Tc, chem, Qo, Wo, hrr, sC, sP, sR, sWd);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (k0 + k >= NV) break;
+                double acc = 0.0;
+                for (int q = 0; q < NQ; ++q) acc = fma(Qbar[(size_t)q * n + cell], Qo[q].d[k], acc);
+#pragma unroll
+                for (int s = 0; s < NS; ++s) acc = fma(lam[(size_t)s * n + cell], Wo[s].d[k], acc);
+                acc = fma(wH * dV, hrr.d[k], acc);
+                Ubar[(size_t)(k0 + k) * n + cell] += acc;
+            }
+        }
+        // parameter gradients
+        if (chem && M.nr > 0) {
+            double rs[NS], qj[NRMAX], sG[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rs[s] = Uv[s];
+            rates_of_progress<NS>(M, rs, Tc, qj, sG);
+            const int rng = nasa_range(M, Tc);
+            double cw[NS];
+#pragma unroll
+            for (int s = 0; s < NS; ++s)
+                cw[s] = (lam[(size_t)s * n + cell] - wH * dV * h_RT(M, rng, s, Tc, 1.0 / Tc) * M.RW[s] * Tc) * M.W[s];
+            for (int j = 0; j < M.nr; ++j) {
+                double a = 0.0;
+                for (int k = 0; k < M.n_net[j]; ++k) a += cw[M.net_sp[j][k]] * (double)M.net_nu[j][k];
+                gl[5 + j] = a * qj[j];
+            }
+        }
+        if (m.laser_on && !(m.flags & F_NO_LASER)) {
+            const long long nxy = (long long)m.nx * m.ny;
+            const int k = (int)(cell / nxy);
+            const long long rem = cell - (long long)k * nxy;
+            const int j = (int)(rem / m.nx), i = (int)(rem - (long long)j * m.nx);
+            const double t = m.t_host;
+            const double sr = m.las[4], st = m.las[6];
+            const double dx = (i + 0.5) * m.h[0] - m.las[1], dy = (j + 0.5) * m.h[1] - m.las[2];
+            double dz = 0.0, dims = 2.0;
+            if (m.nz > 1) {
+                dz = (k + 0.5) * m.h[2] - m.las[3];
+                dims = 3.0;
+            }
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            const double tt = (t - m.las[5]) / st;
+            const double two_pi = 6.283185307179586;
+            const double norm = m.nz == 1 ? m.las[0] / (two_pi * sqrt(two_pi) * sr * sr * st)
+                                          : m.las[0] / (two_pi * two_pi * sr * sr * sr * st);
+            const double qL = norm * exp(-0.5 * tt * tt) * exp(-0.5 * r2 / (sr * sr));
+            const double lE = lam[(size_t)(NS + 3) * n + cell];
+            gl[0] = lE * qL / m.las[0];
+            gl[1] = lE * qL * dx / (sr * sr);
+            gl[2] = lE * qL * dy / (sr * sr);
+            gl[3] = m.nz > 1 ? lE * qL * dz / (sr * sr) : 0.0;
+            gl[4] = lE * qL * (r2 / (sr * sr * sr) - dims / sr);
+        }
+    }
+    // block reduction in fixed order, one atomic per block and parameter
+    const int np = 5 + M.nr;
+    for (int q = 0; q < np; ++q) red[q][threadIdx.x] = gl[q];
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double a = 0.0;
+        for (int t = 0; t < blockDim.x; ++t) a += red[threadIdx.x][t];
+        if (a != 0.0) atomicAdd(&grads[threadIdx.x], a);
+    }
+}
+
+// ----------------------------------------------------------------------------- face adjoint
+
+// Reverse of weno3z(a, b, c): adds wbar * dW/d(a, b, c) into (ga, gb, gc).
+__device__ __forceinline__ void weno3z_adj(double a, double b, double c, double wbar, double &ga, double &gb, double &gc) {
+    const double q0 = -0.5 * a + 1.5 * b, q1 = 0.5 * b + 0.5 * c;
+    const double d0 = b - a, d1 = c - b;
+    const double b0 = d0 * d0, b1 = d1 * d1;
+    const double tau = fabs(b1 - b0);
+    const double e0 = b0 + EPS_WENO, e1 = b1 + EPS_WENO;
+    const double al0 = (1.0 / 3.0) * (1.0 + tau / e0), al1 = (2.0 / 3.0) * (1.0 + tau / e1);
+    const double S = al0 + al1;
+    const double w = (al0 * q0 + al1 * q1) / S;
+    const double q0b = wbar * al0 / S, q1b = wbar * al1 / S;
+    const double al0b = wbar * (q0 - w) / S, al1b = wbar * (q1 - w) / S;
+    const double taub = al0b * (1.0 / 3.0) / e0 + al1b * (2.0 / 3.0) / e1;
+    const double sg = b1 > b0 ? 1.0 : (b1 < b0 ? -1.0 : 0.0);
+    const double b0b = -al0b * (1.0 / 3.0) * tau / (e0 * e0) - sg * taub;
+    const double b1b = -al1b * (2.0 / 3.0) * tau / (e1 * e1) + sg * taub;
+    ga += -0.5 * q0b - 2.0 * d0 * b0b;
+    gb += 1.5 * q0b + 0.5 * q1b + 2.0 * d0 * b0b - 2.0 * d1 * b1b;
+    gc += 0.5 * q1b + 2.0 * d1 * b1b;
+}
+
+// One face of axis DIR per thread: face f (left face of cell f) with
+// G_bar = (lambda(L) - lambda(R)) / h, L = f - 1, R = f (a side outside the grid
+// of a zero-gradient axis has no RHS and contributes nothing).
+template <int NS, int DIR>
+__global__ void __launch_bounds__(128) adjoint_face_kernel(const __grid_constant__ Member m, const double *__restrict__ lam,
+                                                           double *__restrict__ Ubar, double *__restrict__ Qbar) {
+    constexpr int NV = NS + 4;
+    const long long n = m.n;
+    const int nd = DIR == 0 ? m.nx : (DIR == 1 ? m.ny : m.nz);
+    const bool periodic = m.bc[DIR] == 0;
+    const int nf = periodic ? nd : nd + 1;
+    const int n0 = DIR == 0 ? m.ny : m.nx;            // the two other axes
+    const int n1 = DIR == 2 ? m.ny : m.nz;
+    const long long gid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= (long long)nf * n0 * n1) return;
+    const int f = (int)(gid % nf);
+    const long long rest = gid / nf;
+    const int a0 = (int)(rest % n0), a1 = (int)(rest / n0);
+    int cc[3];
+    cc[DIR] = f;
+    if (DIR == 0) {
+        cc[1] = a0;
+        cc[2] = a1;
+    } else if (DIR == 1) {
+        cc[0] = a0;
+        cc[2] = a1;
+    } else {
+        cc[0] = a0;
+        cc[1] = a1;
+    }
+    const long long st[3] = {1, m.nx, (long long)m.nx * m.ny};
+    const long long base = (long long)cc[0] * st[0] + (long long)cc[1] * st[1] + (long long)cc[2] * st[2] -
+                           (long long)cc[DIR] * st[DIR];
+    long long id[4];
+#pragma unroll
+    for (int o = 0; o < 4; ++o) id[o] = base + (long long)map_idx(f + o - 2, nd, m.bc[DIR]) * st[DIR];
+    const double ih = m.invh[DIR];
+    const bool hasL = periodic || f >= 1, hasR = periodic || f < nd;
+    const long long cL = id[1], cR = id[2];
+    double Gb[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double lL = hasL ? lam[(size_t)v * n + cL] : 0.0;
+        const double lR = hasR ? lam[(size_t)v * n + cR] : 0.0;
+        Gb[v] = (lL - lR) * ih;
+    }
+    const double *Q = (const double *)m.Q;
+    const double *U = m.U;
+    auto addQ = [&](int field, long long cell, double x) {
+        if (x != 0.0) atomicAdd(&Qbar[(size_t)field * n + cell], x);
+    };
+    auto addU = [&](int var, long long cell, double x) {
+        if (x != 0.0) atomicAdd(&Ubar[(size_t)var * n + cell], x);
+    };
+    double rhoL = 0.0, rhoR = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        rhoL += U[(size_t)s * n + cL];
+        rhoR += U[(size_t)s * n + cR];
+    }
+    if (!(m.flags & F_NO_INVISCID)) {
+        double un[4], pp[4], cs[4], unb[4] = {0, 0, 0, 0}, ppb[4] = {0, 0, 0, 0};
+        double alpha = 0.0;
+        int amax = 0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            un[o] = Q[(size_t)(Q_U + DIR) * n + id[o]];
+            pp[o] = Q[(size_t)Q_P * n + id[o]];
+            cs[o] = Q[(size_t)Q_C * n + id[o]];
+            const double l = fabs(un[o]) + cs[o];
+            if (o == 0 || l > alpha) {
+                alpha = l;
+                amax = o;
+            }
+        }
+        double alphab = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double Uv[4], fp[4], fm[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                Uv[o] = U[(size_t)v * n + id[o]];
+                double F = un[o] * Uv[o];
+                if (v == NS + DIR) F += pp[o];
+                if (v == NS + 3) F += pp[o] * un[o];
+                fp[o] = 0.5 * (F + alpha * Uv[o]);
+                fm[o] = 0.5 * (F - alpha * Uv[o]);
+            }
+            double fpb[4] = {0, 0, 0, 0}, fmb[4] = {0, 0, 0, 0};
+            weno3z_adj(fp[0], fp[1], fp[2], -Gb[v], fpb[0], fpb[1], fpb[2]);
+            weno3z_adj(fm[3], fm[2], fm[1], -Gb[v], fmb[3], fmb[2], fmb[1]);
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const double Fb = 0.5 * (fpb[o] + fmb[o]);
+                double Ub = 0.5 * alpha * (fpb[o] - fmb[o]) + un[o] * Fb;
+                alphab += 0.5 * Uv[o] * (fpb[o] - fmb[o]);
+                unb[o] += Uv[o] * Fb;
+                if (v == NS + DIR) ppb[o] += Fb;
+                if (v == NS + 3) {
+                    ppb[o] += un[o] * Fb;
+                    unb[o] += pp[o] * Fb;
+                }
+                addU(v, id[o], Ub);
+            }
+        }
+        unb[amax] += alphab * (un[amax] > 0.0 ? 1.0 : (un[amax] < 0.0 ? -1.0 : 0.0));
+        addQ(Q_C, id[amax], alphab);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            addQ(Q_U + DIR, id[o], unb[o]);
+            addQ(Q_P, id[o], ppb[o]);
+        }
+    }
+    if (!(m.flags & F_NO_VISCOUS)) {
+        double velL[3], velR[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            velL[q] = Q[(size_t)(Q_U + q) * n + cL];
+            velR[q] = Q[(size_t)(Q_U + q) * n + cR];
+        }
+        const double mu = 0.5 * (Q[(size_t)Q_MU * n + cL] + Q[(size_t)Q_MU * n + cR]);
+        const double lamf = 0.5 * (Q[(size_t)Q_LAM * n + cL] + Q[(size_t)Q_LAM * n + cR]);
+        double dn[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) dn[q] = (velR[q] - velL[q]) * ih;
+        double dtd[3] = {0, 0, 0}, dtt[3] = {0, 0, 0};
+        long long op[3] = {0, 0, 0}, om[3] = {0, 0, 0};
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == DIR) continue;
+            const int nt = t == 0 ? m.nx : (t == 1 ? m.ny : m.nz);
+            op[t] = (long long)(map_idx(cc[t] + 1, nt, m.bc[t]) - cc[t]) * st[t];
+            om[t] = (long long)(map_idx(cc[t] - 1, nt, m.bc[t]) - cc[t]) * st[t];
+            const double q4 = 0.25 * m.invh[t];
+            const double *vd = Q + (size_t)(Q_U + DIR) * n;
+            const double *vt = Q + (size_t)(Q_U + t) * n;
+            dtd[t] = ((vd[cL + op[t]] - vd[cL + om[t]]) + (vd[cR + op[t]] - vd[cR + om[t]])) * q4;
+            dtt[t] = ((vt[cL + op[t]] - vt[cL + om[t]]) + (vt[cR + op[t]] - vt[cR + om[t]])) * q4;
+        }
+        double div = dn[DIR];
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t != DIR) div += dtt[t];
+        double tau[3];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) tau[q] = q == DIR ? mu * (2.0 * dn[DIR]) - (2.0 / 3.0) * mu * div : mu * (dtd[q] + dn[q]);
+        double dX[NS], Dcf[NS], Yf[NS], hf[NS], YL[NS], YR[NS];
+        double corr = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            dX[s] = (Q[(size_t)(QL<NS>::X + s) * n + cR] - Q[(size_t)(QL<NS>::X + s) * n + cL]) * ih;
+            Dcf[s] = 0.5 * (Q[(size_t)(QL<NS>::DC + s) * n + cL] + Q[(size_t)(QL<NS>::DC + s) * n + cR]);
+            YL[s] = U[(size_t)s * n + cL] / rhoL;
+            YR[s] = U[(size_t)s * n + cR] / rhoR;
+            Yf[s] = 0.5 * (YL[s] + YR[s]);
+            hf[s] = 0.5 * (Q[(size_t)(QL<NS>::H + s) * n + cL] + Q[(size_t)(QL<NS>::H + s) * n + cR]);
+            corr += Dcf[s] * dX[s];
+        }
+        double J[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) J[s] = -Dcf[s] * dX[s] + Yf[s] * corr;
+        // reverse
+        const double qbar = -Gb[NS + 3], workb = Gb[NS + 3];
+        double taub[3], ufb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            taub[k] = Gb[NS + k] + workb * 0.5 * (velL[k] + velR[k]);
+            ufb[k] = workb * tau[k];
+        }
+        double velLb[3], velRb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) velLb[k] = velRb[k] = 0.5 * ufb[k];
+        const double TL = Q[(size_t)Q_T * n + cL], TR = Q[(size_t)Q_T * n + cR];
+        const double lamb = -qbar * (TR - TL) * ih;
+        addQ(Q_T, cR, -qbar * lamf * ih);
+        addQ(Q_T, cL, qbar * lamf * ih);
+        addQ(Q_LAM, cL, 0.5 * lamb);
+        addQ(Q_LAM, cR, 0.5 * lamb);
+        double Jb[NS], corrb = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            Jb[s] = -Gb[s] + qbar * hf[s];
+            const double hfb = qbar * J[s];
+            addQ(QL<NS>::H + s, cL, 0.5 * hfb);
+            addQ(QL<NS>::H + s, cR, 0.5 * hfb);
+            corrb += Jb[s] * Yf[s];
+        }
+        double YLb[NS], YRb[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double Dcfb = -Jb[s] * dX[s] + corrb * dX[s];
+            const double dXb = -Jb[s] * Dcf[s] + corrb * Dcf[s];
+            const double Yfb = Jb[s] * corr;
+            addQ(QL<NS>::DC + s, cL, 0.5 * Dcfb);
+            addQ(QL<NS>::DC + s, cR, 0.5 * Dcfb);
+            addQ(QL<NS>::X + s, cR, dXb * ih);
+            addQ(QL<NS>::X + s, cL, -dXb * ih);
+            YLb[s] = YRb[s] = 0.5 * Yfb;
+        }
+        // Y_s = U_s / rho: dY_s/dU_k = (delta_sk - Y_s) / rho
+        double sL = 0.0, sR = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            sL += YLb[s] * YL[s];
+            sR += YRb[s] * YR[s];
+        }
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            addU(s, cL, (YLb[s] - sL) / rhoL);
+            addU(s, cR, (YRb[s] - sR) / rhoR);
+        }
+        double mub = 0.0, dnb[3] = {0, 0, 0}, dtdb[3] = {0, 0, 0}, dttb[3] = {0, 0, 0}, divb = 0.0;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (q == DIR) {
+                mub += taub[q] * (2.0 * dn[DIR] - (2.0 / 3.0) * div);
+                dnb[DIR] += taub[q] * 2.0 * mu;
+                divb += -taub[q] * (2.0 / 3.0) * mu;
+            } else {
+                mub += taub[q] * (dtd[q] + dn[q]);
+                dtdb[q] += taub[q] * mu;
+                dnb[q] += taub[q] * mu;
+            }
+        }
+        dnb[DIR] += divb;
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+            if (t != DIR) dttb[t] += divb;
+        addQ(Q_MU, cL, 0.5 * mub);
+        addQ(Q_MU, cR, 0.5 * mub);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            velRb[q] += dnb[q] * ih;
+            velLb[q] -= dnb[q] * ih;
+            addQ(Q_U + q, cL, velLb[q]);
+            addQ(Q_U + q, cR, velRb[q]);
+        }
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == DIR) continue;
+            const double q4 = 0.25 * m.invh[t];
+            const double gd = dtdb[t] * q4, gt = dttb[t] * q4;
+            addQ(Q_U + DIR, cL + op[t], gd);
+            addQ(Q_U + DIR, cL + om[t], -gd);
+            addQ(Q_U + DIR, cR + op[t], gd);
+            addQ(Q_U + DIR, cR + om[t], -gd);
+            addQ(Q_U + t, cL + op[t], gt);
+            addQ(Q_U + t, cL + om[t], -gt);
+            addQ(Q_U + t, cR + op[t], gt);
+            addQ(Q_U + t, cR + om[t], -gt);
+        }
+    }
+}
+
+// y = a x + b y over n values
+__global__ void axpby_kernel(double *__restrict__ y, const double *__restrict__ x, double a, double b, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = fma(a, x[i], b * y[i]);
+}
+
+}  // namespace rf

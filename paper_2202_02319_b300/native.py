@@ -63,6 +63,12 @@ _sigs = {
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
+    "rf_adjoint_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Laser), _vp, ctypes.c_double, _vp,
+                                      _vp, _vp]),
+    "rf_rk_step_objective": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _dp,
+                                            _vp]),
+    "rf_adjoint_rk_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser),
+                                          ctypes.c_double, _vp, _vp, _vp]),
     "rf_ensemble_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                           ctypes.POINTER(Laser), _vp, ctypes.POINTER(_vp)]),
     "rf_ensemble_free": (None, [_vp]),
@@ -286,3 +292,26 @@ def ensemble_autotune(e: Ensemble, mode: int = ENS_GRAPH, cfl: float = 0.5, stre
     _check(_lib.rf_ensemble_autotune(e.handle, int(mode), float(cfl), ctypes.byref(seg), _stream(stream)),
            "rf_ensemble_autotune")
     return seg.value
+
+
+def adjoint_rhs(ctx: Context, U, T, t: float, laser, lam_dUdt, w_hrr: float, lam_U, grad_params, stream=None):
+    """lam_U += (dR/dU)^T lam_dUdt + w_hrr dH/dU; grad_params += the parameter part."""
+    L = _laser(laser)
+    _check(_lib.rf_adjoint_rhs(ctx.handle, _ptr(U), _ptr(T), float(t), ctypes.byref(L) if L else None,
+                               _ptr(lam_dUdt) if lam_dUdt is not None else None, float(w_hrr), _ptr(lam_U),
+                               _ptr(grad_params), _stream(stream)), "rf_adjoint_rhs")
+
+
+def rk_step_objective(ctx: Context, U, T, t: float, dt: float, laser=None, stream=None) -> float:
+    """Advances U, T by one RK3 step; returns this step's dt sum_k b_k H(U^(k))."""
+    L = _laser(laser)
+    J = ctypes.c_double(0.0)
+    _check(_lib.rf_rk_step_objective(ctx.handle, _ptr(U), _ptr(T), float(t), float(dt), ctypes.byref(L) if L else None,
+                                     ctypes.byref(J), _stream(stream)), "rf_rk_step_objective")
+    return J.value
+
+
+def adjoint_rk_step(ctx: Context, Un, Tn, t: float, dt: float, laser, w_hrr: float, lam, grad_params, stream=None):
+    L = _laser(laser)
+    _check(_lib.rf_adjoint_rk_step(ctx.handle, _ptr(Un), _ptr(Tn), float(t), float(dt), ctypes.byref(L) if L else None,
+                                   float(w_hrr), _ptr(lam), _ptr(grad_params), _stream(stream)), "rf_adjoint_rk_step")
