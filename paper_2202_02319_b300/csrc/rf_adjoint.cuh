@@ -502,11 +502,15 @@ __global__ void __launch_bounds__(128) adjoint_face_kernel(const __grid_constant
             double fpb[4] = {0, 0, 0, 0}, fmb[4] = {0, 0, 0, 0};
             weno3z_adj(fp[0], fp[1], fp[2], -Gb[v], fpb[0], fpb[1], fpb[2]);
             weno3z_adj(fm[3], fm[2], fm[1], -Gb[v], fmb[3], fmb[2], fmb[1]);
+            // d Fhat / d alpha = (Uhat+ - Uhat-) / 2 is a difference of two
+            // reconstructions; the partial derivatives of each reconstruction sum to
+            // one, so a reference value U_L can be taken out of the sum exactly,
+            // which keeps it free of cancellation between O(U) terms.
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const double Fb = 0.5 * (fpb[o] + fmb[o]);
                 double Ub = 0.5 * alpha * (fpb[o] - fmb[o]) + un[o] * Fb;
-                alphab += 0.5 * Uv[o] * (fpb[o] - fmb[o]);
+                alphab += 0.5 * (Uv[o] - Uv[1]) * (fpb[o] - fmb[o]);
                 unb[o] += Uv[o] * Fb;
                 if (v == NS + DIR) ppb[o] += Fb;
                 if (v == NS + 3) {
