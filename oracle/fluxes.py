@@ -15,7 +15,8 @@ Readings:
   * WENO3-Z at i+1/2 from (a, b, c) = (f_{i-1}, f_i, f_{i+1}):
       q0 = -a/2 + 3b/2, q1 = b/2 + c/2, beta0 = (b-a)^2, beta1 = (c-b)^2,
       tau = |beta1 - beta0|, alpha_k = d_k (1 + tau / (beta_k + eps)),
-      d = (1/3, 2/3), eps = 1e-30, result = (alpha0 q0 + alpha1 q1) / (alpha0 + alpha1).
+      d = (1/3, 2/3), eps = 1e-30, result = (alpha0 q0 + alpha1 q1) / (alpha0 + alpha1),
+      evaluated as q1 + omega0 (q0 - q1) (see weno3z).
   * Diffusive, at the face between cells L and R: normal derivatives by the
     two-point difference, tangential derivatives by the mean of the two cells'
     central differences, coefficients by arithmetic means.  Stokes hypothesis,
@@ -65,15 +66,20 @@ def cells(P: torch.Tensor, grid, d: int, off: int, tan: dict | None = None) -> t
 
 
 def weno3z(a, b, c):
-    """Upwind-biased WENO3-Z value at i+1/2 from (f_{i-1}, f_i, f_{i+1})."""
-    q0 = -0.5 * a + 1.5 * b
+    """Upwind-biased WENO3-Z value at i+1/2 from (f_{i-1}, f_i, f_{i+1}).
+
+    The weighted sum omega0 q0 + omega1 q1 is written q1 + omega0 (q0 - q1), the
+    same value since omega0 + omega1 = 1, with q0 - q1 = ((b - a) - (c - b)) / 2:
+    reverse-mode derivatives of the weights then multiply differences of f, not
+    values of f, and stay accurate where f varies by far less than its size."""
     q1 = 0.5 * b + 0.5 * c
     beta0 = (b - a) ** 2
     beta1 = (c - b) ** 2
     tau = (beta1 - beta0).abs()
     alpha0 = (1.0 / 3.0) * (1.0 + tau / (beta0 + EPS_WENO))
     alpha1 = (2.0 / 3.0) * (1.0 + tau / (beta1 + EPS_WENO))
-    return (alpha0 * q0 + alpha1 * q1) / (alpha0 + alpha1)
+    omega0 = alpha0 / (alpha0 + alpha1)
+    return q1 + omega0 * (0.5 * ((b - a) - (c - b)))
 
 
 def euler_flux(U: torch.Tensor, vel, p: torch.Tensor, d: int, ns: int) -> torch.Tensor:

@@ -392,23 +392,27 @@ __global__ void __launch_bounds__(64) adjoint_cell_kernel(int mslot, const __gri
 
 // Reverse of weno3z(a, b, c): adds wbar * dW/d(a, b, c) into (ga, gb, gc).
 __device__ __forceinline__ void weno3z_adj(double a, double b, double c, double wbar, double &ga, double &gb, double &gc) {
-    const double q0 = -0.5 * a + 1.5 * b, q1 = 0.5 * b + 0.5 * c;
+    // w = q1 + omega0 (q0 - q1), q0 - q1 = (d0 - d1) / 2: every factor of the
+    // reverse pass is a difference of f (no q - w of O(f) values that cancel)
     const double d0 = b - a, d1 = c - b;
+    const double dq = 0.5 * (d0 - d1);
     const double b0 = d0 * d0, b1 = d1 * d1;
     const double tau = fabs(b1 - b0);
     const double e0 = b0 + EPS_WENO, e1 = b1 + EPS_WENO;
     const double al0 = (1.0 / 3.0) * (1.0 + tau / e0), al1 = (2.0 / 3.0) * (1.0 + tau / e1);
     const double S = al0 + al1;
-    const double w = (al0 * q0 + al1 * q1) / S;
-    const double q0b = wbar * al0 / S, q1b = wbar * al1 / S;
-    const double al0b = wbar * (q0 - w) / S, al1b = wbar * (q1 - w) / S;
+    const double om0 = al0 / S, om1 = al1 / S;
+    const double dqb = wbar * om0, om0b = wbar * dq;
+    const double al0b = om0b * om1 / S, al1b = -om0b * om0 / S;
     const double taub = al0b * (1.0 / 3.0) / e0 + al1b * (2.0 / 3.0) / e1;
     const double sg = b1 > b0 ? 1.0 : (b1 < b0 ? -1.0 : 0.0);
     const double b0b = -al0b * (1.0 / 3.0) * tau / (e0 * e0) - sg * taub;
     const double b1b = -al1b * (2.0 / 3.0) * tau / (e1 * e1) + sg * taub;
-    ga += -0.5 * q0b - 2.0 * d0 * b0b;
-    gb += 1.5 * q0b + 0.5 * q1b + 2.0 * d0 * b0b - 2.0 * d1 * b1b;
-    gc += 0.5 * q1b + 2.0 * d1 * b1b;
+    const double d0b = 0.5 * dqb + 2.0 * d0 * b0b;
+    const double d1b = -0.5 * dqb + 2.0 * d1 * b1b;
+    ga += -d0b;
+    gb += 0.5 * wbar + d0b - d1b;
+    gc += 0.5 * wbar + d1b;
 }
 
 // One face of axis DIR per thread: face f (left face of cell f) with
