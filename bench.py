@@ -111,13 +111,14 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
 
 
 # Counts of the mixed-precision cell-state kernel (9 species, 19 reactions) from one
-# ncu capture of the 96^3 case (profiles/cell_state_mixed_jet96.md):
-# FP64 FLOP = 2 DFMA + DMUL + DADD thread instructions, DRAM = dram__bytes_read.sum +
-# dram__bytes_write.sum, both per cell (traffic grows with the cell count, so a
-# full 256^3 launch is the per-cell figure times 256^3).  None until captured for
-# the current kernel.
-CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 1014      # 388 DFMA + 165 DMUL + 73 DADD per cell
-CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 302.5     # (99.30 + 168.28) MB / 884,736 cells
+# ncu capture of the 96^3 case (profiles/cell_state_mixed_jet96.md), per cell:
+# FP64 thread instructions (DFMA, DMUL, DADD; FLOP = 2 DFMA + DMUL + DADD) and
+# DRAM = dram__bytes_read.sum + dram__bytes_write.sum (traffic grows with the cell
+# count, so a full 256^3 launch is the per-cell figure times 256^3).  None until
+# captured for the current kernel.
+CELL_STATE_MIXED_FP64_INST = (257.2, 178.1, 85.0)        # DFMA, DMUL, DADD per cell
+CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 2 * CELL_STATE_MIXED_FP64_INST[0] + sum(CELL_STATE_MIXED_FP64_INST[1:])
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = None
 
 
 def cell_state_bytes(ns: int, rsize: int) -> int:
@@ -279,10 +280,15 @@ def run_ours(args):
         ms_k = prof["cell_state"][0] / prof["cell_state"][1]
         ach = CELL_STATE_MIXED_FP64_FLOP_PER_CELL * ncell / (ms_k * 1e-3) / 1e12
         traffic = (CELL_STATE_MIXED_DRAM_BYTES_PER_CELL * ncell) if CELL_STATE_MIXED_DRAM_BYTES_PER_CELL else None
+        # the FP64 pipe issues one DFMA, DMUL or DADD per slot: instruction-issue fraction
+        inst = sum(CELL_STATE_MIXED_FP64_INST)
+        ach_i = inst * ncell / (ms_k * 1e-3) / 1e12
         roofline = {"kernel": dom, "bound": "alu", "achieved": round(ach, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(ach / fp64_peak, 4), "traffic": traffic,
                     "peak_source": "FP64 FMA rate measured in this run (rf_probe_peak)",
-                    "flop_per_cell": CELL_STATE_MIXED_FP64_FLOP_PER_CELL}
+                    "flop_per_cell": round(CELL_STATE_MIXED_FP64_FLOP_PER_CELL, 1),
+                    "fp64_issue": {"inst_per_cell": round(inst, 1), "achieved_tinst_s": round(ach_i, 4),
+                                   "peak_tinst_s": round(fp64_peak / 2, 4), "frac": round(ach_i / (fp64_peak / 2), 4)}}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": d["achieved_gbs"], "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": d["hbm_frac"], "traffic": None,

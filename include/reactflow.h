@@ -264,6 +264,14 @@ int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_
  * Synchronous.  The FP64 figure is the ALU roofline of the cell-state kernel. */
 int rf_probe_peak(int kind, double *tflops, rf_stream s);
 
+/* Self-test of the FP64 exponential pair the cell-state kernel uses for the
+ * Gibbs factors G_s = exp(g_s/RT) RT/p_atm and 1/G_s (equilibrium constants,
+ * Methods, chemistry): ep[i] = exp(x[i]) and em[i] = exp(-x[i]) from one
+ * argument reduction (Tang's table-driven method), |x| clamped to 707.
+ * x, ep, em: device arrays of n doubles (caller-owned).  Asynchronous on s;
+ * RF_EINVAL for n < 0 or a null array with n > 0. */
+int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s);
+
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Computes the same dU/dt as rf_rhs for a
  * mechanism and grid without a context, for callers that cannot allocate device

@@ -66,13 +66,31 @@ struct rf_mech {
 static std::mutex g_slot_mutex;
 static const rf_mech *g_slot_owner[RF_MAX_DEVICES][MECH_SLOTS];
 
-// Constant-memory slot of m on the current device, uploading it on first use.
+static bool g_exp_tab_done[RF_MAX_DEVICES];
+
+// Table of the FP64 exponential pair (2^(j/32) and 2^(-j/32), j = 0..31, rounded
+// from extended precision) on device dev; the caller holds g_slot_mutex.
+static int upload_exp_table(int dev) {
+    if (g_exp_tab_done[dev]) return RF_OK;
+    double tab[64];
+    for (int j = 0; j < 32; ++j) {
+        tab[j] = (double)std::exp2l((long double)j / 32.0L);
+        tab[32 + j] = (double)std::exp2l(-(long double)j / 32.0L);
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(g_exp_tab, tab, sizeof(tab)));
+    g_exp_tab_done[dev] = true;
+    return RF_OK;
+}
+
+// Constant-memory slot of m on the current device, uploading it (and the
+// exponential table) on first use.
 static int mech_slot(const rf_mech *mc, int *out) {
     rf_mech *m = const_cast<rf_mech *>(mc);
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
     std::lock_guard<std::mutex> lock(g_slot_mutex);
+    if (int rc = upload_exp_table(dev)) return rc;
     if (m->slot[dev] >= 0) {
         *out = m->slot[dev];
         return RF_OK;
@@ -195,13 +213,14 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             M.sc[r][s][3] = a[3] / 3.0;
             M.sc[r][s][4] = a[4] / 4.0;
             M.sc[r][s][5] = a[6];
-            M.gc[r][s][0] = a[0] - a[6];
+            // ln G_s = g_s/RT + ln(R T / p_atm): the constant and the ln T coefficient absorb the second term
+            M.gc[r][s][0] = a[0] - a[6] + std::log(RU / PATM);
             M.gc[r][s][1] = -a[1] / 2.0;
             M.gc[r][s][2] = -a[2] / 6.0;
             M.gc[r][s][3] = -a[3] / 12.0;
             M.gc[r][s][4] = -a[4] / 20.0;
             M.gc[r][s][5] = a[5];
-            M.gc[r][s][6] = -a[0];
+            M.gc[r][s][6] = 1.0 - a[0];
             for (int k = 0; k < 5; ++k) M.cpcf[r][s][k] = (float)a[k];
             for (int k = 0; k < 6; ++k) M.ecf[r][s][k] = (float)M.ec[r][s][k];
         }
@@ -1350,6 +1369,27 @@ extern "C" int rf_probe_peak(int kind, double *tflops, rf_stream s) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     *tflops = 2.0 * 8.0 * iters * (double)blocks * threads / (ms * 1e-3) / 1e12;
+    return RF_OK;
+}
+
+__global__ void exp_pair_probe_kernel(const double *x, double *ep, double *em, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) exp_pair(x[i], ep[i], em[i]);
+}
+
+extern "C" int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s) {
+    if (n < 0 || (n > 0 && (!x || !ep || !em))) return fail(RF_EINVAL, "rf_probe_exp_pair: bad argument");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mutex);
+        if (int rc = upload_exp_table(dev)) return rc;
+    }
+    if (n == 0) return RF_OK;
+    const int threads = 256;
+    exp_pair_probe_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)s>>>(x, ep, em, n);
+    LAUNCH_CHECK();
     return RF_OK;
 }
 

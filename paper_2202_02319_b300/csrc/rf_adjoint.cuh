@@ -226,12 +226,11 @@ __device__ void cell_map(const MechDev &M, const Dual<K> (&U)[NS + 4], double Tc
     hrr = dconst<K>(0.0);
     if (chem && M.nr > 0) {
         const D lnT = dlog(T);
-        const D lnRTp = lnT + log(RU / PATM);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const double *g = M.gc[rng][s];
-            const D gs = (((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6];
-            const D G = dexp(gs + lnRTp);
+            const D lnGs = (((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6];
+            const D G = dexp(lnGs);
             sC[s] = U[s] * M.invW[s];
             sP[s] = sC[s] * G;
             sR[s] = recip(G);
@@ -267,8 +266,8 @@ __device__ void cell_map(const MechDev &M, const Dual<K> (&U)[NS + 4], double Tc
 template <int NS>
 __device__ void rates_of_progress(const MechDev &M, const double (&rs)[NS], double T, double *qout, double *sG) {
     const int rng = nasa_range(M, T);
-    const double invT = 1.0 / T, lnT = log(T), lnRTp = lnT + log(RU / PATM);
-    for (int s = 0; s < NS; ++s) sG[s] = exp(g_RT(M, rng, s, T, invT, lnT) + lnRTp);
+    const double invT = 1.0 / T, lnT = log(T);
+    for (int s = 0; s < NS; ++s) sG[s] = exp(lnG(M, rng, s, T, invT, lnT));
     for (int j = 0; j < M.nr; ++j) {
         const double kf = exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
         double cf = kf;

@@ -30,7 +30,7 @@ struct MechDev {
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
     double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
     double sc[2][NSMAX][6];                    // a1 (x lnT), a2, a3/2, a4/3, a5/4, a7
-    double gc[2][NSMAX][7];                    // g/RT = gc0 + T(gc1 + T(gc2 + T(gc3 + T gc4))) + gc5/T + gc6 lnT
+    double gc[2][NSMAX][7];                    // ln G = g/RT + ln(RT/p_atm) = gc0 + T(gc1 + ... T gc4) + gc5/T + gc6 lnT
     float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
     double invDref[NSMAX][NSMAX];
@@ -128,6 +128,40 @@ template <typename R> __device__ __forceinline__ R mech_cpc(const MechDev &M, in
 template <> __device__ __forceinline__ double mech_cpc<double>(const MechDev &M, int r, int s, int k) { return M.cpc[r][s][k]; }
 template <> __device__ __forceinline__ float mech_cpc<float>(const MechDev &M, int r, int s, int k) { return M.cpcf[r][s][k]; }
 
+// ----------------------------------------------------------------------------- exponential pair
+
+// exp(x) and exp(-x) in FP64 from one argument reduction, after Tang's
+// table-driven exponential (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
+// x = k ln2/32 + r with k = 32 m + j, 0 <= j < 32, |r| <= ln2/64, and
+//   exp(+-x) = 2^(+-m) 2^(+-j/32) (E(r) +- O(r)),
+// E, O the even and odd parts of the Taylor series of exp(r) through r^6
+// (first omitted term r^7/7! < 4e-18 relative).  ln2/32 is split into its
+// double value and the remainder so that r keeps full precision for every k;
+// 2^(+-m) is added to the exponent fields of the correctly rounded table
+// entries.  A few ulp from exp itself for |x| <= 707; beyond that (up to
+// |x| ~ 4e7) the power of two is clamped to 2^(+-1020) and the results saturate.
+constexpr double LN2_32_HI = 0.6931471805599453094 / 32.0;   // double(ln 2) / 32, exact
+constexpr double LN2_32_LO = 2.3190468138462996e-17 / 32.0;  // (ln 2 - double(ln 2)) / 32
+__device__ double g_exp_tab[64];                             // 2^(j/32), then 2^(-j/32), j = 0..31
+
+__device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
+    const double shifter = 6755399441055744.0;               // 1.5 * 2^52: rounds to an integer in the low bits
+    const double t = fma(x, 46.16624130844683 /* 32 / ln 2 */, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(-kd, LN2_32_HI, x);
+    r = fma(-kd, LN2_32_LO, r);
+    const double r2 = r * r;
+    const double E = fma(r2, fma(r2, fma(r2, 1.0 / 720.0, 1.0 / 24.0), 0.5), 1.0);
+    const double O = fma(r * r2, fma(r2, 1.0 / 120.0, 1.0 / 6.0), r);
+    const int j = k & 31, m = min(max(k >> 5, -1020), 1020);
+    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[32 + j]);
+    const double sp = __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp));
+    const double sm = __hiloint2double(__double2hiint(tm) - (m << 20), __double2loint(tm));
+    ep = sp * (E + O);
+    em = sm * (E - O);
+}
+
 // ----------------------------------------------------------------------------- thermo
 
 // Mixture polynomial of the specific internal energy for one NASA range:
@@ -210,8 +244,8 @@ __device__ __forceinline__ double s_R(const MechDev &M, int r, int s, double T, 
     return fma(c[0], lnT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[5]));
 }
 
-// g_s/RT = h_s/RT - s_s/R of species s in one Horner pass.
-__device__ __forceinline__ double g_RT(const MechDev &M, int r, int s, double T, double invT, double lnT) {
+// ln G_s = g_s/RT + ln(R T / p_atm), g_s/RT = h_s/RT - s_s/R, of species s in one Horner pass.
+__device__ __forceinline__ double lnG(const MechDev &M, int r, int s, double T, double invT, double lnT) {
     const double *c = M.gc[r][s];
     return fma(c[6], lnT, fma(c[5], invT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[0])));
 }

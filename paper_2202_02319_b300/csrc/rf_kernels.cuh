@@ -36,7 +36,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) 
 // Reversible mass-action rates.  Per-species inputs sit in per-thread
 // shared-memory columns (stride = block size) so the compact stoichiometry can
 // index species at run time:
-//   sC  = C_s (FP64), sCb = C_s in the bulk type,
+//   sC  = C_s (FP64 path; the mixed path keeps G_s there), sCb = C_s in the bulk type,
 //   sP  = C_s G_s and sRr = 1 / G_s (FP64), G_s = exp(g_s/RT) R T / p_atm,
 // so that k_f / K_c,j * prod_s C_s^nu''_sj = k_f prod_prod (C G)_s prod_reac (1/G)_s,
 // i.e. the equilibrium constant costs one FP64 exponential per species rather than
@@ -83,7 +83,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             if (M.rev[j]) {
                 for (int k = 0; k < npd; ++k) {
                     const int s = M.prod[j][k];
-                    double part = (double)kf / sRr[s * stride];
+                    double part = sizeof(R) == 4 ? (double)kf * sC[s * stride] : (double)kf / sRr[s * stride];
                     for (int k2 = 0; k2 < npd; ++k2)
                         if (k2 != k) part *= sP[M.prod[j][k2] * stride];
                     for (int k2 = 0; k2 < nrc; ++k2) part *= sRr[M.reac[j][k2] * stride];
@@ -111,15 +111,19 @@ template <typename R, int NS>
 __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, const double (&rs)[NS], double T, double invT,
                                                  double lnT, double *sC, R *sCb, double *sP, double *sRr, R *sW, R *sD,
                                                  int stride) {
-    const double lnRTp = lnT + log(RU / PATM);
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const double C = rs[s] * M.invW[s];
-        const double G = exp(g_RT(M, rng, s, T, invT, lnT) + lnRTp);
-        sC[s * stride] = C;
-        if (sizeof(R) == 4) sCb[s * stride] = (R)C;
+        double G, iG;
+        exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
+        if (sizeof(R) == 4) {
+            sC[s * stride] = G;
+            sCb[s * stride] = (R)C;
+        } else {
+            sC[s * stride] = C;
+        }
         sP[s * stride] = C * G;
-        sRr[s * stride] = 1.0 / G;
+        sRr[s * stride] = iG;
         sW[s * stride] = (R)0;
         sD[s * stride] = (R)0;
     }
@@ -203,7 +207,8 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const double cp = cv + Rm;
         const double p = rho * Rm * T;
         const R c = sqrt_((R)(cp / cv) * (R)(Rm * T));
-        const double Wbar = RU / Rm;
+        const double irm = 1.0 / Rm;
+        const double Wbar = RU * irm;
         R *Q = (R *)m.Q;
         Q[Q_U * n + cell] = (R)u;
         Q[Q_V * n + cell] = (R)v;
@@ -212,11 +217,10 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         Q[Q_C * n + cell] = (R)c;
         Q[Q_T * n + cell] = (R)T;
         R X[NS];
-        const double irm = 1.0 / Rm;
-        const R Tb = (R)T, invTb = (R)invT;
+        const R Tb = (R)T, invTb = (R)invT, irmb = (R)irm;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            X[s] = (R)(Y[s] * M.RW[s] * irm);
+            X[s] = (R)Y[s] * (mech_RW<R>(M, s) * irmb);
             Q[(QL<NS>::X + s) * n + cell] = X[s];
             Q[(QL<NS>::H + s) * n + cell] = h_RT_bulk(M, rng, s, Tb, invTb) * mech_RW<R>(M, s) * Tb;
         }
@@ -235,7 +239,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             r_ch = chemistry<R, NS>(M, lnT, invT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
                                     m.want_rates != 0);
 #pragma unroll
-            for (int s = 0; s < NS; ++s) rhs[s * n + cell] = (R)((double)sW[s * B + tid] * M.W[s]);
+            for (int s = 0; s < NS; ++s) rhs[s * n + cell] = sW[s * B + tid] * mech_W<R>(M, s);
         } else {
 #pragma unroll
             for (int s = 0; s < NS; ++s) rhs[s * n + cell] = (R)0;

@@ -1,0 +1,44 @@
+"""The FP64 exponential pair of the cell-state kernel (G_s and 1/G_s of the
+equilibrium constants) against CUDA's exp (through torch) and numpy's exp."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _pair(x):
+    from paper_2202_02319_b300 import native as nv
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    ep, em = torch.empty_like(xd), torch.empty_like(xd)
+    nv.probe_exp_pair(xd, ep, em)
+    torch.cuda.synchronize()
+    return xd, ep, em
+
+
+def test_exp_pair_within_a_few_ulp():
+    g = np.random.default_rng(11)
+    ln2_64 = np.log(2.0) / 64.0
+    k = np.arange(-200, 201)
+    x = np.concatenate([
+        g.uniform(-700.0, 700.0, 400_000), g.uniform(-1.0, 1.0, 200_000), g.uniform(-30.0, 30.0, 200_000),
+        k * ln2_64, np.nextafter(k * ln2_64, np.inf), np.nextafter(k * ln2_64, -np.inf),
+        [0.0, -0.0, 1e-300, -1e-300, 706.9, -706.9],
+    ])
+    xd, ep, em = _pair(x)
+    ref = np.exp(x)
+    for got, want in ((ep.cpu().numpy(), ref), (em.cpu().numpy(), np.exp(-x))):
+        assert float(np.max(np.abs(got - want) / want)) < 1e-15
+    for got, want in ((ep, torch.exp(xd)), (em, torch.exp(-xd))):
+        assert float(((got - want).abs() / want).max()) < 1e-15
+    assert float((ep * em - 1.0).abs().max()) < 2e-15
+
+
+def test_exp_pair_saturates_beyond_707_and_handles_empty():
+    xd, ep, em = _pair(np.array([800.0, -800.0, 1e6, -1e6]))
+    ep, em = ep.cpu().numpy(), em.cpu().numpy()
+    assert np.isfinite(ep).all() and np.isfinite(em).all() and (ep > 0).all() and (em > 0).all()
+    big = np.exp(706.0)
+    assert ep[0] >= big and em[1] >= big and ep[2] >= big and em[3] >= big
+    assert em[0] <= 1.0 / big and ep[1] <= 1.0 / big
+    _pair(np.zeros(0))
