@@ -165,7 +165,7 @@ int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, 
  *   "newton_maxit" Newton iteration cap (default 30; 0 forces RF_ENEWTON, for tests)
  *   "x_block"      threads per block of the x sweep (multiple of 32, <= 256; default 256)
  *   "walk_block"   threads per block of the y / z sweeps (multiple of 32, <= 128; default 128)
- *   "walk_seg"     cells walked per thread in the y / z sweeps (default 16)
+ *   "walk_seg"     cells walked per thread in the y / z sweeps (default 16 in FP64, 32 in mixed precision)
  *   "profile"      1: record a CUDA event pair on the launching stream around every
  *                  kernel launch of this context (read with rf_profile_read); 0: off
  * Errors: RF_EINVAL for an unknown key or a value out of range. */

@@ -128,7 +128,8 @@ struct rf_ctx {
     int diag_blocks = 0;
     int newton_maxit = 30;
     int x_block = 256;                       // x sweep threads per block
-    int walk_block = 128, walk_seg = 16;     // y / z sweeps
+    int walk_block = 128, walk_seg = 16;     // y / z sweeps (FP64 path)
+    int walk_seg_staged = 32;                // y / z sweeps (staged FP32-bulk path): cells per segment
     size_t bytes = 0;
     // adjoint workspace (FP64 contexts), allocated on first use
     double *adj = nullptr;                   // Qbar [nq n], zero [nv n], R [nv n], lamS [nv n], Ub1, Ub2, Ln [nv n], T0, T1, T2 [n]
@@ -324,6 +325,8 @@ extern "C" void rf_free_ctx(rf_ctx *c) {
 
 extern "C" size_t rf_ctx_workspace_bytes(const rf_ctx *c) { return c ? c->bytes : 0; }
 
+static int prepare_ctx(rf_ctx *c);
+
 extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precision, uint32_t flags, rf_ctx **out) {
     if (!m || !g || !out) return fail(RF_EINVAL, "rf_create_ctx: null argument");
     *out = nullptr;
@@ -391,6 +394,11 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
         delete c;
         return fail(RF_ECUDA, "rf_create_ctx: %s", cudaGetErrorString(e));
     }
+    if (int rc = prepare_ctx(c)) {
+        free_ctx_buffers(c);
+        delete c;
+        return rc;
+    }
     *out = c;
     return RF_OK;
 }
@@ -437,6 +445,20 @@ template <typename R, int NS>
 struct Path {
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
 
+    // kernel attributes, set once per context before any launch (or capture)
+    static int prepare(rf_ctx *) {
+        if constexpr (sizeof(R) == 4) {
+            const int sm = (int)walk_smem<R, NS>();
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 1, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 1, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        }
+        return RF_OK;
+    }
+
     static int cell_state(rf_ctx *c, const Member &m, cudaStream_t s) {
         const int B = 128;
         const long long nb = (c->n + B - 1) / B;
@@ -468,6 +490,18 @@ struct Path {
             const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
             ProfScope ps(c, PROF_SWEEP_X, s);
             sweep_x_kernel<R, UT, NS, MODE><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+        } else if (sizeof(R) == 4) {
+            // staged walk: 32 x 4 line tiles, planes streamed through shared memory
+            const int nd = dir == 1 ? c->g.ny : c->g.nz;
+            const int no = dir == 1 ? c->g.nz : c->g.ny;
+            const int seg = c->walk_seg_staged;
+            dim3 grid((unsigned)walk_tiles<R, NS>(c->g.nx, no), (unsigned)((nd + seg - 1) / seg));
+            const size_t smem = walk_smem<R, NS>();
+            ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
+            if (dir == 1)
+                sweep_walk_staged_kernel<NS, 1, MODE><<<grid, 128, smem, s>>>(c->mslot, m, seg);
+            else
+                sweep_walk_staged_kernel<NS, 2, MODE><<<grid, 128, smem, s>>>(c->mslot, m, seg);
         } else {
             const int nd = dir == 1 ? c->g.ny : c->g.nz;
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
@@ -605,6 +639,10 @@ struct Path {
         return fail(RF_EINVAL, "unsupported species count %d", (c)->ns);             \
     } while (0)
 
+// Kernel attributes of a context's precision and species count (dynamic shared
+// memory above the default 48 KB).
+static int prepare_ctx(rf_ctx *c) { DISPATCH(c, prepare(c)); }
+
 extern "C" int rf_init_state(rf_ctx *c, const double *prim, double *U, double *T, rf_stream s) {
     if (!c || !prim || !U || !T) return fail(RF_EINVAL, "rf_init_state: null argument");
     DISPATCH(c, init_state(c, prim, U, T, (cudaStream_t)s));
@@ -646,6 +684,7 @@ extern "C" int rf_set_option(rf_ctx *c, const char *key, double value) {
     } else if (!std::strcmp(key, "walk_seg")) {
         if (v < 1 || v > 4096) return fail(RF_EINVAL, "rf_set_option: walk_seg %d outside [1, 4096]", v);
         c->walk_seg = v;
+        c->walk_seg_staged = v;
     } else {
         return fail(RF_EINVAL, "rf_set_option: unknown key '%s'", key);
     }
@@ -782,7 +821,10 @@ static int ens_build(rf_ensemble *e) {
         for (int dir = 1; dir <= 2; ++dir) {
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             const int nd = dir == 1 ? c->g.ny : c->g.nz;
-            const int lb = (int)((lines + 127) / 128), sb = (nd + e->seg - 1) / e->seg;
+            const int lb = (int)(c->precision == RF_MIXED ? walk_tiles<float, 1>(c->g.nx, dir == 1 ? c->g.nz : c->g.ny)
+                                                          : walk_tiles<double, 1>(c->g.nx, dir == 1 ? c->g.nz : c->g.ny));
+            const int sb = (nd + e->seg - 1) / e->seg;
+            (void)lines;
             for (int q = 0; q < lb; ++q)
                 for (int r = 0; r < sb; ++r) items[1 + dir].push_back({mi, q, r, 0});
         }
@@ -827,7 +869,12 @@ struct EnsPath {
         CUDA_TRY(cudaFuncSetAttribute(ens_cell_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_cell));
         CUDA_TRY(cudaFuncSetAttribute(ens_x_kernel<R, UT, NS, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)std::max<size_t>(e->smem_x, 1)));
-        const size_t sm_stage = std::max(e->smem_cell, e->smem_x);
+        if constexpr (sizeof(R) == 4) {
+            const int sw = (int)walk_smem<R, NS>();
+            CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
+            CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 2, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
+        }
+        const size_t sm_stage = std::max(std::max(e->smem_cell, e->smem_x), walk_smem<R, NS>());
         CUDA_TRY(cudaFuncSetAttribute(ens_stage_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
         int dev = 0, sms = 0, per = 0;
         CUDA_TRY(cudaGetDevice(&dev));
@@ -851,9 +898,9 @@ struct EnsPath {
             }
             ens_x_kernel<R, UT, NS, MODE_ACCUM><<<e->nitems[1], 128, e->smem_x, s>>>(M, ens_dev(e, e->nitems[1]), k);
             LAUNCH_CHECK();
-            ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM><<<e->nitems[2], 128, 0, s>>>(M, ens_dev(e, e->nitems[2]), k);
+            ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM><<<e->nitems[2], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[2]), k);
             LAUNCH_CHECK();
-            ens_walk_kernel<R, UT, NS, 2, MODE_STAGE><<<e->nitems[3], 128, 0, s>>>(M, ens_dev(e, e->nitems[3]), k);
+            ens_walk_kernel<R, UT, NS, 2, MODE_STAGE><<<e->nitems[3], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[3]), k);
             LAUNCH_CHECK();
         }
         ens_end_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(ens_dev(e, 1));
@@ -863,7 +910,7 @@ struct EnsPath {
 
     // one step as one cooperative launch per RK stage (mode 3)
     static int step_persistent(rf_ensemble *e, cudaStream_t s) {
-        const size_t sm_stage = std::max(e->smem_cell, e->smem_x);
+        const size_t sm_stage = std::max(std::max(e->smem_cell, e->smem_x), walk_smem<R, NS>());
         for (int k = 0; k < 3; ++k) {
             EnsDev E = ens_dev(e, e->coop_blocks);
             cudaLaunchConfig_t cfg;
@@ -1472,6 +1519,17 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
     c.Q = base + RF_NOALLOC_HEADER;
     c.rhs = base + RF_NOALLOC_HEADER + bq;
     c.U32 = precision == RF_MIXED ? (float *)(base + RF_NOALLOC_HEADER + bq + br) : nullptr;
+    {
+        // kernel attributes once per device, precision and species count
+        static std::mutex mu;
+        static bool done[RF_NOALLOC_MAX_DEVICES][2][NSMAX + 1];
+        std::lock_guard<std::mutex> lock(mu);
+        bool &d = done[dev][precision == RF_MIXED ? 1 : 0][ns];
+        if (!d) {
+            if (int rc = prepare_ctx(&c)) return rc;
+            d = true;
+        }
+    }
     int rc = noalloc_rhs_dispatch(&c, U, T, t, L, dUdt, st);
     if (rc) return rc;
     int status = 0;

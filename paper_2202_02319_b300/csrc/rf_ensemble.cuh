@@ -87,13 +87,19 @@ __device__ __forceinline__ void ens_x_phase(const MechDev &M, const EnsDev &E, i
     }
 }
 
+// y / z work items: (tile, segment); a tile is a 32 x 4 line group of the staged
+// walk in the FP32-bulk path and a block of 128 lines otherwise.
 template <typename R, typename UT, int NS, int DIR, int MODE>
-__device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E, int stage, Member &sm, int &s_ok) {
+__device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E, int stage, unsigned char *smem,
+                                               Member &sm, int &s_ok) {
     const int k = DIR == 1 ? 2 : 3;
     for (int w = blockIdx.x; w < E.nitems[k]; w += gridDim.x) {
         const EnsItem it = E.items[k][w];
         if (!load_member(E.tab[stage], it.m, sm, s_ok)) continue;
-        sweep_walk_block<R, UT, NS, DIR, MODE>(M, sm, it.a, it.b, E.seg);
+        if constexpr (sizeof(R) == 4)
+            sweep_walk_staged_block<NS, DIR, MODE>(M, sm, it.a, it.b, E.seg, (float *)smem);
+        else
+            sweep_walk_block<R, UT, NS, DIR, MODE>(M, sm, it.a, it.b, E.seg);
     }
 }
 
@@ -123,9 +129,10 @@ template <typename R, typename UT, int NS, int DIR, int MODE>
 __global__ void __launch_bounds__(128) ens_walk_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                        int stage) {
     const MechDev &M = c_mech[mslot];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok;
-    ens_walk_phase<R, UT, NS, DIR, MODE>(M, E, stage, sm, s_ok);
+    ens_walk_phase<R, UT, NS, DIR, MODE>(M, E, stage, smem_raw, sm, s_ok);
 }
 
 // Step prologue (run start): t from the caller, CFL, fixed dt, cleared maxima.
@@ -220,9 +227,9 @@ __global__ void __launch_bounds__(128) ens_stage_kernel(int mslot, const __grid_
     }
     ens_x_phase<R, UT, NS, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok);
     if (!grid_barrier(E, s_flag)) return;
-    ens_walk_phase<R, UT, NS, 1, MODE_ACCUM>(M, E, stage, sm, s_ok);
+    ens_walk_phase<R, UT, NS, 1, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok);
     if (!grid_barrier(E, s_flag)) return;
-    ens_walk_phase<R, UT, NS, 2, MODE_STAGE>(M, E, stage, sm, s_ok);
+    ens_walk_phase<R, UT, NS, 2, MODE_STAGE>(M, E, stage, smem_raw, sm, s_ok);
     if (stage == 2) {
         if (!grid_barrier(E, s_flag)) return;
         if (blockIdx.x == 0)

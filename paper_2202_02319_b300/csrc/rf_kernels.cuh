@@ -340,21 +340,46 @@ __device__ __forceinline__ R weno3z(R a, R b, R c) {
     return fma(a0, q0, a1 * q1) * rcp(a0 + a1);
 }
 
-// Flux G = -Fhat^a + F^d at the face between cells (coord-1) and coord along DIR.
-// `cc` holds the cell's coordinates (i, j, k) with cc[DIR] = coord.
-template <typename R, typename UT, int NS, int DIR>
-__device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict__ U, const R *__restrict__ Q, const int (&cc)[3],
-                                          R (&G)[NS + 4]) {
-    constexpr int NV = NS + 4;
-    const long long n = m.n;
-    const long long sx = 1, sy = m.nx, sz = (long long)m.nx * m.ny;
-    const long long st[3] = {sx, sy, sz};
-    const int nd = DIR == 0 ? m.nx : (DIR == 1 ? m.ny : m.nz);
-    const long long base = (long long)cc[0] * sx + (long long)cc[1] * sy + (long long)cc[2] * sz - (long long)cc[DIR] * st[DIR];
+// Stencil of one face along DIR read from global memory.  Cells o = 0..3 are
+// f-2, f-1 (L), f (R), f+1 along DIR; qt reads the tangential neighbours of L or R.
+template <typename R, typename UT, int DIR>
+struct GlobalStencil {
+    const UT *__restrict__ U;
+    const R *__restrict__ Q;
+    long long n;
     long long id[4];
+    long long tp[3], tm[3];        // offsets of the +1 / -1 neighbour along each tangential axis
+
+    __device__ __forceinline__ GlobalStencil(const Member &m, const UT *U_, const R *Q_, const int (&cc)[3])
+        : U(U_), Q(Q_), n(m.n) {
+        const long long st[3] = {1, m.nx, (long long)m.nx * m.ny};
+        const int nd = DIR == 0 ? m.nx : (DIR == 1 ? m.ny : m.nz);
+        const long long base = (long long)cc[0] * st[0] + (long long)cc[1] * st[1] + (long long)cc[2] * st[2] -
+                               (long long)cc[DIR] * st[DIR];
 #pragma unroll
-    for (int o = 0; o < 4; ++o) id[o] = base + (long long)map_idx(cc[DIR] + o - 2, nd, m.bc[DIR]) * st[DIR];
-    // id[1] = L (coord-1), id[2] = R (coord)
+        for (int o = 0; o < 4; ++o) id[o] = base + (long long)map_idx(cc[DIR] + o - 2, nd, m.bc[DIR]) * st[DIR];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == DIR) {
+                tp[t] = tm[t] = 0;
+                continue;
+            }
+            const int nt = t == 0 ? m.nx : (t == 1 ? m.ny : m.nz);
+            tp[t] = (long long)(map_idx(cc[t] + 1, nt, m.bc[t]) - cc[t]) * st[t];
+            tm[t] = (long long)(map_idx(cc[t] - 1, nt, m.bc[t]) - cc[t]) * st[t];
+        }
+    }
+    __device__ __forceinline__ R u(int v, int o) const { return (R)U[v * n + id[o]]; }
+    __device__ __forceinline__ R q(int f, int o) const { return Q[f * n + id[o]]; }
+    __device__ __forceinline__ R qt(int f, int o, int t, bool plus) const { return Q[f * n + id[o] + (plus ? tp[t] : tm[t])]; }
+};
+
+// Flux G = -Fhat^a + F^d at the face between cells L = f-1 and R = f along DIR, from
+// the stencil accessor st (u: conserved variables, q: Q fields, qt: tangential
+// neighbours of L / R).  Every sweep variant computes its faces with this code.
+template <typename R, int NS, int DIR, class S>
+__device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (&G)[NS + 4]) {
+    constexpr int NV = NS + 4;
 #pragma unroll
     for (int v = 0; v < NV; ++v) G[v] = 0;
     R rhoL = 0, rhoR = 0;
@@ -363,9 +388,9 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
         R alpha = 0;
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
-            un[o] = Q[(Q_U + DIR) * n + id[o]];
-            pp[o] = Q[Q_P * n + id[o]];
-            const R lam = fabs(un[o]) + Q[Q_C * n + id[o]];
+            un[o] = st.q(Q_U + DIR, o);
+            pp[o] = st.q(Q_P, o);
+            const R lam = fabs(un[o]) + st.q(Q_C, o);
             alpha = lam > alpha ? lam : alpha;
         }
 #pragma unroll
@@ -373,7 +398,7 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
             R fp[4], fm[4];
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
-                const R Uv = (R)U[v * n + id[o]];
+                const R Uv = st.u(v, o);
                 if (v < NS) {
                     if (o == 1) rhoL += Uv;
                     if (o == 2) rhoR += Uv;
@@ -391,20 +416,19 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
         if (m.flags & F_NO_INVISCID) {
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
-                rhoL += (R)U[s * n + id[1]];
-                rhoR += (R)U[s * n + id[2]];
+                rhoL += st.u(s, 1);
+                rhoR += st.u(s, 2);
             }
         }
-        const long long iL = id[1], iR = id[2];
         const R ih = (R)m.invh[DIR];
         R velL[3], velR[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            velL[q] = Q[(Q_U + q) * n + iL];
-            velR[q] = Q[(Q_U + q) * n + iR];
+            velL[q] = st.q(Q_U + q, 1);
+            velR[q] = st.q(Q_U + q, 2);
         }
-        const R mu = R(0.5) * (Q[Q_MU * n + iL] + Q[Q_MU * n + iR]);
-        const R lam = R(0.5) * (Q[Q_LAM * n + iL] + Q[Q_LAM * n + iR]);
+        const R mu = R(0.5) * (st.q(Q_MU, 1) + st.q(Q_MU, 2));
+        const R lam = R(0.5) * (st.q(Q_LAM, 1) + st.q(Q_LAM, 2));
         R dn[3];
 #pragma unroll
         for (int q = 0; q < 3; ++q) dn[q] = (velR[q] - velL[q]) * ih;
@@ -413,14 +437,11 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
 #pragma unroll
         for (int t = 0; t < 3; ++t) {
             if (t == DIR) continue;
-            const int nt = t == 0 ? m.nx : (t == 1 ? m.ny : m.nz);
-            const long long op = (long long)(map_idx(cc[t] + 1, nt, m.bc[t]) - cc[t]) * st[t];
-            const long long om = (long long)(map_idx(cc[t] - 1, nt, m.bc[t]) - cc[t]) * st[t];
             const R q4 = R(0.25) * (R)m.invh[t];
-            const R *vd = Q + (Q_U + DIR) * n;
-            const R *vt = Q + (Q_U + t) * n;
-            dtd[t] = ((vd[iL + op] - vd[iL + om]) + (vd[iR + op] - vd[iR + om])) * q4;
-            dtt[t] = ((vt[iL + op] - vt[iL + om]) + (vt[iR + op] - vt[iR + om])) * q4;
+            dtd[t] = ((st.qt(Q_U + DIR, 1, t, true) - st.qt(Q_U + DIR, 1, t, false)) +
+                      (st.qt(Q_U + DIR, 2, t, true) - st.qt(Q_U + DIR, 2, t, false))) * q4;
+            dtt[t] = ((st.qt(Q_U + t, 1, t, true) - st.qt(Q_U + t, 1, t, false)) +
+                      (st.qt(Q_U + t, 2, t, true) - st.qt(Q_U + t, 2, t, false))) * q4;
         }
         R div = dn[DIR];
 #pragma unroll
@@ -436,23 +457,23 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
         R corr = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R dX = (Q[(QL<NS>::X + s) * n + iR] - Q[(QL<NS>::X + s) * n + iL]) * ih;
-            const R Dcf = R(0.5) * (Q[(QL<NS>::DC + s) * n + iL] + Q[(QL<NS>::DC + s) * n + iR]);
+            const R dX = (st.q(QL<NS>::X + s, 2) - st.q(QL<NS>::X + s, 1)) * ih;
+            const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
             corr = fma(Dcf, dX, corr);
         }
         const R irL = rcp(rhoL), irR = rcp(rhoR);
         R qh = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R dX = (Q[(QL<NS>::X + s) * n + iR] - Q[(QL<NS>::X + s) * n + iL]) * ih;
-            const R Dcf = R(0.5) * (Q[(QL<NS>::DC + s) * n + iL] + Q[(QL<NS>::DC + s) * n + iR]);
-            const R Yf = R(0.5) * ((R)U[s * n + iL] * irL + (R)U[s * n + iR] * irR);
+            const R dX = (st.q(QL<NS>::X + s, 2) - st.q(QL<NS>::X + s, 1)) * ih;
+            const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
+            const R Yf = R(0.5) * (st.u(s, 1) * irL + st.u(s, 2) * irR);
             const R J = fma(Yf, corr, -Dcf * dX);
-            const R hf = R(0.5) * (Q[(QL<NS>::H + s) * n + iL] + Q[(QL<NS>::H + s) * n + iR]);
+            const R hf = R(0.5) * (st.q(QL<NS>::H + s, 1) + st.q(QL<NS>::H + s, 2));
             qh = fma(J, hf, qh);
             G[s] -= J;
         }
-        const R q = fma(-lam, (Q[Q_T * n + iR] - Q[Q_T * n + iL]) * ih, qh);
+        const R q = fma(-lam, (st.q(Q_T, 2) - st.q(Q_T, 1)) * ih, qh);
         R work = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -461,6 +482,15 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
         }
         G[NS + 3] += work - q;
     }
+}
+
+// Face flux from global memory; `cc` holds the cell's coordinates (i, j, k) with
+// cc[DIR] = f.
+template <typename R, typename UT, int NS, int DIR>
+__device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict__ U, const R *__restrict__ Q, const int (&cc)[3],
+                                          R (&G)[NS + 4]) {
+    const GlobalStencil<R, UT, DIR> st(m, U, Q, cc);
+    face_flux_core<R, NS, DIR>(m, st, G);
 }
 
 template <typename R, int NS, int MODE>
@@ -589,6 +619,222 @@ __global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid
                                                          int seg) {
     const MechDev &M = c_mech[mslot];
     sweep_walk_block<R, UT, NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg);
+}
+
+// ----------------------------------------------------------------------------- staged y / z sweep (FP32 bulk)
+
+// Asynchronous global -> shared copies (cp.async, completion tracked per thread by
+// commit groups).  Global sources must be 4- or 16-byte aligned as the size says.
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Tile of the staged walk: 32 lines along x (one warp) times 4 lines along the
+// other axis o (o = z for the y sweep, y for the z sweep), 128 threads, one line
+// per thread.  Shared memory holds rings of planes (cells of the tile at one
+// position along DIR):
+//   ring I (depth 5): the NS + 4 conserved variables (FP32 copy), u_DIR, p, c of
+//                     every line: the four stencil planes of a face plus one ahead;
+//   ring V (depth 3): the Q fields T, mu, lambda, X_s, Dc_s, h_s: planes L, R, ahead;
+//   slab   (depth 3): u, v, w on the tile plus a one-cell halo in x and o, for the
+//                     tangential derivatives of the viscous flux.
+template <int NS>
+struct WalkTile {
+    static constexpr int TX = 32, TY = 4, NL = TX * TY;
+    static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS;
+    static constexpr int SX = TX + 2, SY = TY + 2, NSL = SX * SY;
+    static constexpr int DI = 5, DV = 3;
+    static constexpr int I_FLOATS = DI * NI * NL, V_FLOATS = DV * NVV * NL, S_FLOATS = DV * 3 * NSL;
+    static constexpr size_t SMEM = sizeof(float) * (size_t)(I_FLOATS + V_FLOATS + S_FLOATS);
+};
+
+template <int NS, int DIR>
+struct WalkStencil {
+    using W = WalkTile<NS>;
+    const float *I[4];      // ring I slots of cells f-2 .. f+1: [NI][NL]
+    const float *V[2];      // ring V slots of L, R: [NVV][NL]
+    const float *S[2];      // slab slots of L, R: [3][NSL]
+    int l, sl;              // the thread's line in the ring and in the slab
+    __device__ __forceinline__ float u(int v, int o) const { return I[o][v * W::NL + l]; }
+    __device__ __forceinline__ float q(int f, int o) const {
+        if (f == Q_U + DIR) return I[o][(W::NV + 0) * W::NL + l];
+        if (f == Q_P) return I[o][(W::NV + 1) * W::NL + l];
+        if (f == Q_C) return I[o][(W::NV + 2) * W::NL + l];
+        if (f < 3) return S[o - 1][f * W::NSL + sl];
+        return V[o - 1][(f - Q_T) * W::NL + l];
+    }
+    __device__ __forceinline__ float qt(int f, int o, int t, bool plus) const {
+        const int d = t == 0 ? 1 : W::SX;
+        return S[o - 1][f * W::NSL + sl + (plus ? d : -d)];
+    }
+};
+
+// One tile line group walking faces c0 .. c1 of its segment [c0, c1) along DIR:
+// face f needs planes f-2 .. f+1 (ring I) and f-1, f (ring V, slab); while face f is
+// computed the planes f+2 / f+1 are in flight.  Faces are computed by
+// face_flux_core from shared memory, cells updated one face behind.
+template <int NS, int DIR, int MODE>
+__device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const Member &m, int tile, int sblk, int seg,
+                                                        float *smem) {
+    using W = WalkTile<NS>;
+    constexpr int NV = W::NV, NL = W::NL;
+    const int nd = DIR == 1 ? m.ny : m.nz;
+    const int no = DIR == 1 ? m.nz : m.ny;
+    const int bco = DIR == 1 ? m.bc[2] : m.bc[1];
+    const int c0 = sblk * seg;
+    if (c0 >= nd) return;
+    const int c1 = min(c0 + seg, nd);
+    const int ntx = (m.nx + W::TX - 1) / W::TX;
+    const int x0 = (tile % ntx) * W::TX, o0 = (tile / ntx) * W::TY;
+    const int l = threadIdx.x, tx = l & 31, ty = l >> 5;
+    const int x = x0 + tx, o = o0 + ty;
+    const bool active = x < m.nx && o < no;
+    const long long n = m.n;
+    const long long sd = DIR == 1 ? (long long)m.nx : (long long)m.nx * m.ny;
+    const long long so = DIR == 1 ? (long long)m.nx * m.ny : (long long)m.nx;
+    const float *__restrict__ U = m.U32;
+    const float *__restrict__ Q = (const float *)m.Q;
+    float *ringI = smem;
+    float *ringV = ringI + W::I_FLOATS;
+    float *slab = ringV + W::V_FLOATS;
+    // 16-byte copies when every row of the tile is whole and 16-byte aligned
+    const bool vec = (m.nx % 4 == 0) && (x0 + W::TX <= m.nx);
+    auto pmod = [](int c, int d) { return ((c % d) + d) % d; };
+
+    auto stage_I = [&](int c) {
+        const int cm = map_idx(c, nd, m.bc[DIR]);
+        float *dst = ringI + pmod(c, W::DI) * W::NI * NL;
+        auto src = [&](int f) -> const float * {
+            return f < NV ? U + (long long)f * n : Q + (long long)(f == NV ? Q_U + DIR : (f == NV + 1 ? Q_P : Q_C)) * n;
+        };
+        if (vec) {
+            for (int q = l; q < W::NI * W::TY * 8; q += NL) {
+                const int f = q / (W::TY * 8), r = (q >> 3) % W::TY, k = q & 7;
+                if (o0 + r >= no) continue;
+                const long long cell = (long long)(x0 + 4 * k) + (long long)(o0 + r) * so + (long long)cm * sd;
+                cp_async16(dst + f * NL + r * W::TX + 4 * k, src(f) + cell);
+            }
+        } else if (active) {
+            const long long cell = (long long)x + (long long)o * so + (long long)cm * sd;
+#pragma unroll
+            for (int f = 0; f < W::NI; ++f) cp_async4(dst + f * NL + l, src(f) + cell);
+        }
+    };
+    auto stage_V = [&](int c) {
+        const int cm = map_idx(c, nd, m.bc[DIR]);
+        const int slot = pmod(c, W::DV);
+        float *dst = ringV + slot * W::NVV * NL;
+        const float *qv = Q + (long long)Q_T * n;
+        if (vec) {
+            for (int q = l; q < W::NVV * W::TY * 8; q += NL) {
+                const int f = q / (W::TY * 8), r = (q >> 3) % W::TY, k = q & 7;
+                if (o0 + r >= no) continue;
+                const long long cell = (long long)(x0 + 4 * k) + (long long)(o0 + r) * so + (long long)cm * sd;
+                cp_async16(dst + f * NL + r * W::TX + 4 * k, qv + (long long)f * n + cell);
+            }
+        } else if (active) {
+            const long long cell = (long long)x + (long long)o * so + (long long)cm * sd;
+#pragma unroll
+            for (int f = 0; f < W::NVV; ++f) cp_async4(dst + f * NL + l, qv + (long long)f * n + cell);
+        }
+        float *sdst = slab + slot * 3 * W::NSL;
+        for (int e = l; e < 3 * W::NSL; e += NL) {
+            const int f = e / W::NSL, p = e - f * W::NSL;
+            const int sy = p / W::SX, sx = p - sy * W::SX;
+            const int X = map_idx(x0 - 1 + sx, m.nx, m.bc[0]);
+            const int O = map_idx(o0 - 1 + sy, no, bco);
+            cp_async4(sdst + e, Q + (long long)f * n + (long long)X + (long long)O * so + (long long)cm * sd);
+        }
+    };
+
+    stage_I(c0 - 2);
+    stage_I(c0 - 1);
+    stage_I(c0);
+    stage_I(c0 + 1);
+    stage_V(c0 - 1);
+    stage_V(c0);
+    cp_async_commit();
+
+    const float ih = (float)m.invh[DIR];
+    const long long lbase = (long long)x + (long long)o * so;
+    float Gp[NV];
+    for (int f = c0; f <= c1; ++f) {
+        if (f + 2 <= c1 + 1) stage_I(f + 2);
+        if (f + 1 <= c1) stage_V(f + 1);
+        cp_async_commit();
+        // the update's inputs of cell f-1, loaded before the wait so their latency overlaps it
+        const bool upd = active && f > c0;
+        const long long cell = lbase + (long long)(f - 1) * sd;
+        float racc[NV];
+        double uk[MODE == MODE_STAGE ? NV : 1], un[MODE == MODE_STAGE ? NV : 1];
+        double dt = 0.0;
+        if (upd) {
+            if (MODE == MODE_STAGE) dt = m.clock[1];
+            const float *__restrict__ rhs = (const float *)m.rhs;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) racc[v] = rhs[v * n + cell];
+            if (MODE == MODE_STAGE) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    uk[v] = m.U[v * n + cell];
+                    un[v] = m.Un[v * n + cell];
+                }
+            }
+        }
+        cp_async_wait_all_but_one();
+        __syncthreads();
+        if (active) {
+            WalkStencil<NS, DIR> st;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) st.I[q] = ringI + pmod(f - 2 + q, W::DI) * W::NI * NL;
+            st.V[0] = ringV + pmod(f - 1, W::DV) * W::NVV * NL;
+            st.V[1] = ringV + pmod(f, W::DV) * W::NVV * NL;
+            st.S[0] = slab + pmod(f - 1, W::DV) * 3 * W::NSL;
+            st.S[1] = slab + pmod(f, W::DV) * 3 * W::NSL;
+            st.l = l;
+            st.sl = (ty + 1) * W::SX + tx + 1;
+            float Gn[NV];
+            face_flux_core<float, NS, DIR>(m, st, Gn);
+            if (upd) {
+                // as cell_update, from the preloaded inputs
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const float L = fma(Gn[v] - Gp[v], ih, racc[v]);
+                    if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
+                    else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
+                    else m.Uout[v * n + cell] = fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
+        }
+        __syncthreads();
+    }
+    cp_async_wait_all();
+}
+
+// Work tiles of a y / z sweep (128-thread blocks) and their dynamic shared memory.
+template <typename R, int NS>
+__host__ __device__ inline long long walk_tiles(int nx, int no) {
+    if (sizeof(R) == 4) return (long long)((nx + WalkTile<NS>::TX - 1) / WalkTile<NS>::TX) * ((no + WalkTile<NS>::TY - 1) / WalkTile<NS>::TY);
+    return ((long long)nx * no + 127) / 128;
+}
+template <typename R, int NS>
+__host__ __device__ constexpr size_t walk_smem() { return sizeof(R) == 4 ? WalkTile<NS>::SMEM : 0; }
+
+template <int NS, int DIR, int MODE>
+__global__ void __launch_bounds__(128) sweep_walk_staged_kernel(int mslot, const __grid_constant__ Member m, int seg) {
+    const MechDev &M = c_mech[mslot];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_walk_staged_block<NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg, (float *)smem_raw);
 }
 
 // Grids with no axis longer than one cell: the RHS is the source alone.
