@@ -455,6 +455,10 @@ struct Path {
             CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
             CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
             CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 2, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            const int sx = (int)XTile<NS>::SMEM;
+            CUDA_TRY(cudaFuncSetAttribute(sweep_x_staged_kernel<NS, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_x_staged_kernel<NS, MODE_RHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx));
+            CUDA_TRY(cudaFuncSetAttribute(sweep_x_staged_kernel<NS, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sx));
         }
         return RF_OK;
     }
@@ -472,7 +476,13 @@ struct Path {
     template <int MODE>
     static int sweep(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
-        if (dir == 0) {
+        if (dir == 0 && sizeof(R) == 4) {
+            // staged x sweep: a row per warp, four rows per block
+            const int nrows = c->g.ny * c->g.nz;
+            const int blocks = (nrows + XTile<NS>::WARPS - 1) / XTile<NS>::WARPS;
+            ProfScope ps(c, PROF_SWEEP_X, s);
+            sweep_x_staged_kernel<NS, MODE><<<blocks, 128, XTile<NS>::SMEM, s>>>(c->mslot, m);
+        } else if (dir == 0) {
             const int nx = c->g.nx;
             int W, rpb;
             if (nx <= c->x_block) {
@@ -813,11 +823,15 @@ static int ens_build(rf_ensemble *e) {
             tab[k].push_back(mk);
         }
         const int nv = c->nv;
-        smx = std::max(smx, (size_t)nv * rpb * (W + 2) * c->rsize);
+        const bool staged = c->precision == RF_MIXED;
+        // staged x sweep (FP32 bulk): four rows per block, window buffers as XTile
+        const size_t x_staged = sizeof(float) * ((size_t)4 * 2 * (4 * c->ns + 20) * 40 + 4 * 16);
+        smx = std::max(smx, staged ? x_staged : (size_t)nv * rpb * (W + 2) * c->rsize);
         const long long ncb = (c->n + 127) / 128;
         for (long long q = 0; q < ncb; ++q) items[0].push_back({mi, (int)q, 0, 0});
         const int nrows = c->g.ny * c->g.nz;
-        for (int q = 0; q < (nrows + rpb - 1) / rpb; ++q) items[1].push_back({mi, q, 0, 0});
+        const int rows_per_item = staged ? 4 : rpb;
+        for (int q = 0; q < (nrows + rows_per_item - 1) / rows_per_item; ++q) items[1].push_back({mi, q, 0, 0});
         for (int dir = 1; dir <= 2; ++dir) {
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             const int nd = dir == 1 ? c->g.ny : c->g.nz;

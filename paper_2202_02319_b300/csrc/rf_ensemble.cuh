@@ -83,7 +83,10 @@ __device__ __forceinline__ void ens_x_phase(const MechDev &M, const EnsDev &E, i
     for (int w = blockIdx.x; w < E.nitems[1]; w += gridDim.x) {
         const EnsItem it = E.items[1][w];
         if (!load_member(E.tab[stage], it.m, sm, s_ok)) continue;
-        sweep_x_block<R, UT, NS, MODE>(M, sm, it.a, sm.xW, sm.xrpb, smem);
+        if constexpr (sizeof(R) == 4)
+            sweep_x_staged_block<NS, MODE>(M, sm, it.a, (float *)smem);
+        else
+            sweep_x_block<R, UT, NS, MODE>(M, sm, it.a, sm.xW, sm.xrpb, smem);
     }
 }
 

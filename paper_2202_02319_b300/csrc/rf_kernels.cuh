@@ -821,6 +821,192 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
     cp_async_wait_all();
 }
 
+// ----------------------------------------------------------------------------- staged x sweep (FP32 bulk)
+
+// Each warp of a 128-thread block takes one row (fixed y, z) and walks it in chunks
+// of 32 faces, lane l computing face F = F0 + l.  A chunk's window of 40 cells,
+// starting at the 4-aligned cell 32 k - 4, is copied by cp.async into one of two
+// per-warp buffers while the previous chunk is computed:
+//   I   fields: the NS + 4 conserved variables (FP32 copy), u, p, c;
+//   V   fields: T, mu, lambda, X_s, Dc_s, h_s;
+//   vel rows:   v, w of the row and (u, v) of rows y -+ 1, (u, w) of rows z -+ 1.
+// Periodic rows compute faces 1 .. nx (face nx has the stencil of face 0) and
+// update cell 0 last; other rows compute faces 0 .. nx.
+template <int NS>
+struct XTile {
+    static constexpr int WARPS = 4, WIN = 40;
+    static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS, NVEL = 10;
+    static constexpr int NFR = NI + NVV + NVEL;                // field-rows of a window
+    static constexpr int BUF = NFR * WIN;                     // floats of one window
+    static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * 2 * BUF + (size_t)WARPS * 16);
+};
+
+template <int NS>
+struct XStencil {
+    using X = XTile<NS>;
+    const float *b;          // window buffer
+    int po;                  // window position of the face's cell f-2
+    __device__ __forceinline__ float at(int fr, int o) const { return b[fr * X::WIN + po + o]; }
+    __device__ __forceinline__ float u(int v, int o) const { return at(v, o); }
+    __device__ __forceinline__ float q(int f, int o) const {
+        if (f == Q_U) return at(X::NV + 0, o);
+        if (f == Q_P) return at(X::NV + 1, o);
+        if (f == Q_C) return at(X::NV + 2, o);
+        if (f == Q_V) return at(X::NI + X::NVV + 0, o);
+        if (f == Q_W) return at(X::NI + X::NVV + 1, o);
+        return at(X::NI + f - Q_T, o);
+    }
+    __device__ __forceinline__ float qt(int f, int o, int t, bool plus) const {
+        // vel rows 2..9: (u, v) at y-1, y+1, then (u, w) at z-1, z+1
+        const int r = 2 + (t == 1 ? 0 : 4) + (plus ? 2 : 0) + (f == Q_U ? 0 : 1);
+        return at(X::NI + X::NVV + r, o);
+    }
+};
+
+template <int NS, int MODE>
+__device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Member &m, int blk, float *smem) {
+    using X = XTile<NS>;
+    constexpr int NV = NS + 4, WIN = X::WIN;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nx = m.nx;
+    const int nrows = m.ny * m.nz;
+    const int row = blk * X::WARPS + warp;
+    if (row >= nrows) return;                              // whole warp: no block-wide barrier below
+    const int j = row % m.ny, k = row / m.ny;
+    const long long n = m.n;
+    const float *__restrict__ U = m.U32;
+    const float *__restrict__ Q = (const float *)m.Q;
+    float *buf0 = smem + (size_t)warp * 2 * X::BUF;
+    float *stash = smem + (size_t)X::WARPS * 2 * X::BUF + warp * 16;
+    const bool periodic = m.bc[0] == 0;
+    const int fs = periodic ? 1 : 0;                       // first face computed
+    const int nf = periodic ? nx : nx + 1;                 // faces fs .. fs + nf - 1
+    const int nchunks = (nf + 31) / 32;
+    const long long rowc = ((long long)k * m.ny + j) * nx;
+    const int jm = map_idx(j - 1, m.ny, m.bc[1]), jp = map_idx(j + 1, m.ny, m.bc[1]);
+    const int km = map_idx(k - 1, m.nz, m.bc[2]), kp = map_idx(k + 1, m.nz, m.bc[2]);
+    const long long rjm = ((long long)k * m.ny + jm) * nx, rjp = ((long long)k * m.ny + jp) * nx;
+    const long long rkm = ((long long)km * m.ny + j) * nx, rkp = ((long long)kp * m.ny + j) * nx;
+    const bool vec_ok = nx % 4 == 0;
+
+    // source of field-row fr (pointer to the row's cell 0)
+    auto src = [&](int fr) -> const float * {
+        if (fr < NV) return U + (long long)fr * n + rowc;
+        if (fr == NV) return Q + (long long)Q_U * n + rowc;
+        if (fr == NV + 1) return Q + (long long)Q_P * n + rowc;
+        if (fr == NV + 2) return Q + (long long)Q_C * n + rowc;
+        if (fr < X::NI + X::NVV) return Q + (long long)(Q_T + fr - X::NI) * n + rowc;
+        const int r = fr - X::NI - X::NVV;
+        switch (r) {
+            case 0: return Q + (long long)Q_V * n + rowc;
+            case 1: return Q + (long long)Q_W * n + rowc;
+            case 2: return Q + (long long)Q_U * n + rjm;
+            case 3: return Q + (long long)Q_V * n + rjm;
+            case 4: return Q + (long long)Q_U * n + rjp;
+            case 5: return Q + (long long)Q_V * n + rjp;
+            case 6: return Q + (long long)Q_U * n + rkm;
+            case 7: return Q + (long long)Q_W * n + rkm;
+            case 8: return Q + (long long)Q_U * n + rkp;
+            default: return Q + (long long)Q_W * n + rkp;
+        }
+    };
+    auto stage = [&](int c, float *dst) {
+        const int A = 32 * c - 4;
+        for (int e = lane; e < X::NFR * (WIN / 4); e += 32) {
+            const int fr = e / (WIN / 4), q4 = e - fr * (WIN / 4);
+            const int x4 = A + 4 * q4;
+            const float *sp = src(fr);
+            float *dp = dst + fr * WIN + 4 * q4;
+            if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
+                cp_async16(dp, sp + x4);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cp_async4(dp + i, sp + map_idx(x4 + i, nx, m.bc[0]));
+            }
+        }
+    };
+
+    const float ih = (float)m.invh[0];
+    float Gc[NV];                      // lane 31's flux of the previous chunk
+    stage(0, buf0);
+    cp_async_commit();
+    for (int c = 0; c < nchunks; ++c) {
+        float *cur = buf0 + (c & 1) * X::BUF;
+        if (c + 1 < nchunks) stage(c + 1, buf0 + ((c + 1) & 1) * X::BUF);
+        cp_async_commit();
+        const int F = fs + 32 * c + lane;
+        const bool has_face = F < fs + nf;
+        // this lane updates cell F - 1 (cell 0 of a periodic row comes last)
+        const bool upd = has_face && F >= 1 && !(periodic && F == 1);
+        const long long cell = rowc + (F - 1);
+        float racc[NV];
+        double uk[MODE == MODE_STAGE ? NV : 1], un[MODE == MODE_STAGE ? NV : 1];
+        double dt = 0.0;
+        if (upd) {
+            const float *__restrict__ rhs = (const float *)m.rhs;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) racc[v] = rhs[v * n + cell];
+            if (MODE == MODE_STAGE) {
+                dt = m.clock[1];
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    uk[v] = m.U[v * n + cell];
+                    un[v] = m.Un[v * n + cell];
+                }
+            }
+        }
+        cp_async_wait_all_but_one();
+        __syncwarp();
+        float G[NV];
+        if (has_face) {
+            XStencil<NS> st;
+            st.b = cur;
+            st.po = F - 2 - (32 * c - 4);
+            face_flux_core<float, NS, 0>(m, st, G);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) G[v] = 0.f;
+        }
+        float Gl[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            const float up = __shfl_up_sync(0xffffffffu, G[v], 1);
+            Gl[v] = lane == 0 ? Gc[v] : up;
+            Gc[v] = __shfl_sync(0xffffffffu, G[v], 31);
+        }
+        if (periodic && c == 0 && lane == 0) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) stash[v] = G[v];           // face 1, for cell 0
+        }
+        if (upd) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const float L = fma(G[v] - Gl[v], ih, racc[v]);
+                if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
+                else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
+                else m.Uout[v * n + cell] = fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+            }
+        }
+        __syncwarp();
+        if (periodic && F == nx) {
+            // face nx = face 0: cell 0 from G(1) - G(nx)
+            float dG[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) dG[v] = stash[v] - G[v];
+            cell_update<float, NS, MODE>(m, rowc, dG, ih);
+        }
+        __syncwarp();
+    }
+    cp_async_wait_all();
+}
+
+template <int NS, int MODE>
+__global__ void __launch_bounds__(128) sweep_x_staged_kernel(int mslot, const __grid_constant__ Member m) {
+    const MechDev &M = c_mech[mslot];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_x_staged_block<NS, MODE>(M, m, blockIdx.x, (float *)smem_raw);
+}
+
 // Work tiles of a y / z sweep (128-thread blocks) and their dynamic shared memory.
 template <typename R, int NS>
 __host__ __device__ inline long long walk_tiles(int nx, int no) {
