@@ -447,6 +447,8 @@ struct Path {
 
     // kernel attributes, set once per context before any launch (or capture)
     static int prepare(rf_ctx *) {
+        CUDA_TRY(cudaFuncSetAttribute(cell_state_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)cell_state_smem<R, NS>(128)));
         if constexpr (sizeof(R) == 4) {
             const int sm = (int)walk_smem<R, NS>();
             CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -466,7 +468,7 @@ struct Path {
     static int cell_state(rf_ctx *c, const Member &m, cudaStream_t s) {
         const int B = 128;
         const long long nb = (c->n + B - 1) / B;
-        const size_t smem = (size_t)B * NS * (3 * sizeof(double) + 2 * sizeof(R) + (sizeof(R) == 4 ? sizeof(R) : 0));
+        const size_t smem = cell_state_smem<R, NS>(B);
         ProfScope ps(c, PROF_CELL, s);
         cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mslot, m, c->newton_maxit);
         LAUNCH_CHECK();

@@ -90,6 +90,17 @@ template <int NS> struct QL {
 };
 
 __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+
+// 1/x in FP64 by Newton-Raphson iteration r <- r + r (1 - x r) from an FP32 seed:
+// two steps take the seed's ~2^-23 relative error to rounding level.  For x whose
+// magnitude lies in the FP32 normal range (densities, temperatures, gas constants).
+__device__ __forceinline__ double rcp64(double x) {
+    double r = (double)__frcp_rn((float)x);
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }

@@ -180,7 +180,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         }
         const double mx = U[(NS + 0) * n + cell], my = U[(NS + 1) * n + cell], mz = U[(NS + 2) * n + cell];
         const double E = U[(NS + 3) * n + cell];
-        const double irho = 1.0 / rho;
+        const double irho = rcp64(rho);
         const double u = mx * irho, v = my * irho, w = mz * irho;
         double Rm = 0.0;
 #pragma unroll
@@ -201,13 +201,22 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         m.T[cell] = T;
 
         const int rng = nasa_range(M, T);
-        const double invT = 1.0 / T;
+        const double invT = rcp64(T);
         const double lnT = log(T);
         const double cv = mix_cv(P, T);
         const double cp = cv + Rm;
-        const double p = rho * Rm * T;
-        const R c = sqrt_((R)(cp / cv) * (R)(Rm * T));
-        const double irm = 1.0 / Rm;
+        double p;
+        R c;
+        if constexpr (sizeof(R) == 4) {
+            // bulk quantities of the mixed path: gamma, c and p from FP32 factors
+            const float Tf = (float)T, Rmf = (float)Rm;
+            p = (double)((float)rho * (Rmf * Tf));
+            c = sqrtf((float)cp * rcp((float)cv) * (Rmf * Tf));
+        } else {
+            p = rho * Rm * T;
+            c = sqrt_((R)(cp / cv) * (R)(Rm * T));
+        }
+        const double irm = rcp64(Rm);
         const double Wbar = RU * irm;
         R *Q = (R *)m.Q;
         Q[Q_U * n + cell] = (R)u;
