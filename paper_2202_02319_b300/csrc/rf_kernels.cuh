@@ -349,6 +349,34 @@ __device__ __forceinline__ R weno3z(R a, R b, R c) {
     return fma(a0, q0, a1 * q1) * rcp(a0 + a1);
 }
 
+// FP32 reciprocal from the SFU (rcp.approx: about 1 ulp), for weights and
+// factors of the FP32-bulk face arithmetic whose arguments are normal numbers.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_face(float x) { return rcp_approx(x); }
+__device__ __forceinline__ double rcp_face(double x) { return 1.0 / x; }
+
+// The same WENO3-Z value in FP32 with the fused operations written out: with
+// d0 = b - a, d1 = c - b the candidates are q0 = b + d0/2, q1 = b + d1/2, and
+// omega0 q0 + omega1 q1 = q1 + omega0 (d0 - d1)/2.  S >= 2 eps and a0 + a1 >= 1/12 are
+// normal, so the SFU reciprocals apply.
+template <>
+__device__ __forceinline__ float weno3z<float>(float a, float b, float c) {
+    const float d0 = b - a, d1 = c - b;
+    const float beta0 = d0 * d0, beta1 = d1 * d1;
+    const float iS = rcp_approx((beta0 + beta1) + (float)(2.0 * EPS_WENO));
+    const float eS = (float)EPS_WENO * iS;
+    const float b0 = fmaf(beta0, iS, eS), b1 = fmaf(beta1, iS, eS);
+    const float t = fabsf(beta1 - beta0) * iS;
+    const float a0 = (1.0f / 3.0f) * (b1 * (b0 + t));
+    const float a1 = (2.0f / 3.0f) * (b0 * (b1 + t));
+    const float om0 = a0 * rcp_approx(a0 + a1);
+    return fmaf(om0, 0.5f * (d0 - d1), fmaf(0.5f, d1, b));
+}
+
 // Stencil of one face along DIR read from global memory.  Cells o = 0..3 are
 // f-2, f-1 (L), f (R), f+1 along DIR; qt reads the tangential neighbours of L or R.
 template <typename R, typename UT, int DIR>
@@ -402,6 +430,18 @@ __device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (
             const R lam = fabs(un[o]) + st.q(Q_C, o);
             alpha = lam > alpha ? lam : alpha;
         }
+        // f+- = (F(U) +- alpha U) / 2 = (u_n/2 +- alpha/2) U + (p/2 or p u_n/2 for the
+        // momentum along DIR and the energy)
+        const R ha = R(0.5) * alpha;
+        R lp[4], lm[4], hp[4], hpu[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const R h = R(0.5) * un[o];
+            lp[o] = h + ha;
+            lm[o] = h - ha;
+            hp[o] = R(0.5) * pp[o];
+            hpu[o] = hp[o] * un[o];
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R fp[4], fm[4];
@@ -412,11 +452,16 @@ __device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (
                     if (o == 1) rhoL += Uv;
                     if (o == 2) rhoR += Uv;
                 }
-                R F = un[o] * Uv;
-                if (v == NS + DIR) F += pp[o];
-                if (v == NS + 3) F = fma(pp[o], un[o], F);
-                fp[o] = R(0.5) * fma(alpha, Uv, F);
-                fm[o] = R(0.5) * fma(-alpha, Uv, F);
+                fp[o] = lp[o] * Uv;
+                fm[o] = lm[o] * Uv;
+                if (v == NS + DIR) {
+                    fp[o] += hp[o];
+                    fm[o] += hp[o];
+                }
+                if (v == NS + 3) {
+                    fp[o] += hpu[o];
+                    fm[o] += hpu[o];
+                }
             }
             G[v] = -(weno3z<R>(fp[0], fp[1], fp[2]) + weno3z<R>(fm[3], fm[2], fm[1]));
         }
@@ -470,7 +515,7 @@ __device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (
             const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
             corr = fma(Dcf, dX, corr);
         }
-        const R irL = rcp(rhoL), irR = rcp(rhoR);
+        const R irL = rcp_face(rhoL), irR = rcp_face(rhoR);
         R qh = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
@@ -758,8 +803,9 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
         for (int e = l; e < 3 * W::NSL; e += NL) {
             const int f = e / W::NSL, p = e - f * W::NSL;
             const int sy = p / W::SX, sx = p - sy * W::SX;
-            const int X = map_idx(x0 - 1 + sx, m.nx, m.bc[0]);
-            const int O = map_idx(o0 - 1 + sy, no, bco);
+            int X = x0 - 1 + sx, O = o0 - 1 + sy;
+            if ((unsigned)X >= (unsigned)m.nx) X = map_idx(X, m.nx, m.bc[0]);
+            if ((unsigned)O >= (unsigned)no) O = map_idx(O, no, bco);
             cp_async4(sdst + e, Q + (long long)f * n + (long long)X + (long long)O * so + (long long)cm * sd);
         }
     };
@@ -847,7 +893,8 @@ struct XTile {
     static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS, NVEL = 10;
     static constexpr int NFR = NI + NVV + NVEL;                // field-rows of a window
     static constexpr int BUF = NFR * WIN;                     // floats of one window
-    static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * 2 * BUF + (size_t)WARPS * 16);
+    static constexpr int AUX = 16 + 2 * ((NFR + 1) / 2 * 2);    // floats per warp: G(1) stash, then NFR pointers
+    static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * 2 * BUF + (size_t)WARPS * AUX);
 };
 
 template <int NS>
@@ -886,7 +933,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     const float *__restrict__ U = m.U32;
     const float *__restrict__ Q = (const float *)m.Q;
     float *buf0 = smem + (size_t)warp * 2 * X::BUF;
-    float *stash = smem + (size_t)X::WARPS * 2 * X::BUF + warp * 16;
+    float *stash = smem + (size_t)X::WARPS * 2 * X::BUF + warp * X::AUX;
     const bool periodic = m.bc[0] == 0;
     const int fs = periodic ? 1 : 0;                       // first face computed
     const int nf = periodic ? nx : nx + 1;                 // faces fs .. fs + nf - 1
@@ -898,8 +945,8 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     const long long rkm = ((long long)km * m.ny + j) * nx, rkp = ((long long)kp * m.ny + j) * nx;
     const bool vec_ok = nx % 4 == 0;
 
-    // source of field-row fr (pointer to the row's cell 0)
-    auto src = [&](int fr) -> const float * {
+    // source of field-row fr (pointer to the row's cell 0), tabulated once per row
+    auto src_of = [&](int fr) -> const float * {
         if (fr < NV) return U + (long long)fr * n + rowc;
         if (fr == NV) return Q + (long long)Q_U * n + rowc;
         if (fr == NV + 1) return Q + (long long)Q_P * n + rowc;
@@ -919,12 +966,15 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
             default: return Q + (long long)Q_W * n + rkp;
         }
     };
+    const float **tab = (const float **)(stash + 16) ;
+    for (int fr = lane; fr < X::NFR; fr += 32) tab[fr] = src_of(fr);
+    __syncwarp();
     auto stage = [&](int c, float *dst) {
         const int A = 32 * c - 4;
         for (int e = lane; e < X::NFR * (WIN / 4); e += 32) {
             const int fr = e / (WIN / 4), q4 = e - fr * (WIN / 4);
             const int x4 = A + 4 * q4;
-            const float *sp = src(fr);
+            const float *sp = tab[fr];
             float *dp = dst + fr * WIN + 4 * q4;
             if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
                 cp_async16(dp, sp + x4);
