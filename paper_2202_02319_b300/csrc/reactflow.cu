@@ -68,14 +68,14 @@ static const rf_mech *g_slot_owner[RF_MAX_DEVICES][MECH_SLOTS];
 
 static bool g_exp_tab_done[RF_MAX_DEVICES];
 
-// Table of the FP64 exponential pair (2^(j/32) and 2^(-j/32), j = 0..31, rounded
+// Table of the FP64 exponential pair (2^(j/64) and 2^(-j/64), j = 0..63, rounded
 // from extended precision) on device dev; the caller holds g_slot_mutex.
 static int upload_exp_table(int dev) {
     if (g_exp_tab_done[dev]) return RF_OK;
-    double tab[64];
-    for (int j = 0; j < 32; ++j) {
-        tab[j] = (double)std::exp2l((long double)j / 32.0L);
-        tab[32 + j] = (double)std::exp2l(-(long double)j / 32.0L);
+    double tab[128];
+    for (int j = 0; j < 64; ++j) {
+        tab[j] = (double)std::exp2l((long double)j / 64.0L);
+        tab[64 + j] = (double)std::exp2l(-(long double)j / 64.0L);
     }
     CUDA_TRY(cudaMemcpyToSymbol(g_exp_tab, tab, sizeof(tab)));
     g_exp_tab_done[dev] = true;

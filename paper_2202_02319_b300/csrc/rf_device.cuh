@@ -143,30 +143,31 @@ template <> __device__ __forceinline__ float mech_cpc<float>(const MechDev &M, i
 
 // exp(x) and exp(-x) in FP64 from one argument reduction, after Tang's
 // table-driven exponential (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
-// x = k ln2/32 + r with k = 32 m + j, 0 <= j < 32, |r| <= ln2/64, and
-//   exp(+-x) = 2^(+-m) 2^(+-j/32) (E(r) +- O(r)),
-// E, O the even and odd parts of the Taylor series of exp(r) through r^6
-// (first omitted term r^7/7! < 4e-18 relative).  ln2/32 is split into its
-// double value and the remainder so that r keeps full precision for every k;
-// 2^(+-m) is added to the exponent fields of the correctly rounded table
-// entries.  A few ulp from exp itself for |x| <= 707; beyond that (up to
-// |x| ~ 4e7) the power of two is clamped to 2^(+-1020) and the results saturate.
-constexpr double LN2_32_HI = 0.6931471805599453094 / 32.0;   // double(ln 2) / 32, exact
-constexpr double LN2_32_LO = 2.3190468138462996e-17 / 32.0;  // (ln 2 - double(ln 2)) / 32
-__device__ double g_exp_tab[64];                             // 2^(j/32), then 2^(-j/32), j = 0..31
+// x = k ln2/64 + r with k = 64 m + j, 0 <= j < 64, |r| <= ln2/128, and
+//   exp(+-x) = 2^(+-m) 2^(+-j/64) (E(r) +- O(r)),
+// E = 1 + r^2/2 + r^4/24 and O = r + r^3/6 + r^5/120 the even and odd parts of the
+// Taylor series of exp(r) (first omitted terms r^6/720 < 4e-17 and r^7/7! < 3e-20
+// relative).  ln2/64 is split into its double value and the remainder so that r
+// keeps full precision for every k; 2^(+-m) is added to the exponent fields of
+// the correctly rounded table entries.  A few ulp from exp itself for |x| <= 707;
+// beyond that (up to |x| ~ 2e7) the power of two is clamped to 2^(+-1020) and the
+// results saturate.
+constexpr double LN2_64_HI = 0.6931471805599453094 / 64.0;   // double(ln 2) / 64, exact
+constexpr double LN2_64_LO = 2.3190468138462996e-17 / 64.0;  // (ln 2 - double(ln 2)) / 64
+__device__ double g_exp_tab[128];                            // 2^(j/64), then 2^(-j/64), j = 0..63
 
 __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     const double shifter = 6755399441055744.0;               // 1.5 * 2^52: rounds to an integer in the low bits
-    const double t = fma(x, 46.16624130844683 /* 32 / ln 2 */, shifter);
+    const double t = fma(x, 92.33248261689366 /* 64 / ln 2 */, shifter);
     const int k = __double2loint(t);
     const double kd = t - shifter;
-    double r = fma(-kd, LN2_32_HI, x);
-    r = fma(-kd, LN2_32_LO, r);
+    double r = fma(-kd, LN2_64_HI, x);
+    r = fma(-kd, LN2_64_LO, r);
     const double r2 = r * r;
-    const double E = fma(r2, fma(r2, fma(r2, 1.0 / 720.0, 1.0 / 24.0), 0.5), 1.0);
+    const double E = fma(r2, fma(r2, 1.0 / 24.0, 0.5), 1.0);
     const double O = fma(r * r2, fma(r2, 1.0 / 120.0, 1.0 / 6.0), r);
-    const int j = k & 31, m = min(max(k >> 5, -1020), 1020);
-    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[32 + j]);
+    const int j = k & 63, m = min(max(k >> 6, -1020), 1020);
+    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[64 + j]);
     const double sp = __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp));
     const double sm = __hiloint2double(__double2hiint(tm) - (m << 20), __double2loint(tm));
     ep = sp * (E + O);
@@ -216,19 +217,25 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
                                          double &T, int maxit, MixPoly &P) {
     int r = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
     mix_poly<NS>(M, r, Y, Rm, P);
+    double e5 = P.e[5] - e_target;
+    // |dT| <= 1e-13 T, with T taken at the start: the iterates differ from it by
+    // far less than the tolerance's own precision
+    const double tol = 1.0e-13 * fabs(T);
     for (int it = 0; it < maxit; ++it) {
         const int rn = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
         if (rn != r) {
             r = rn;
             mix_poly<NS>(M, r, Y, Rm, P);
+            e5 = P.e[5] - e_target;
         }
-        const double e = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), P.e[5]);
+        // residual e(T) - e_target with the target folded into the constant term
+        const double res = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), e5);
         const double cv = fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
         // The root is fixed by e(T) = e_target alone; an FP32 reciprocal of cv only
         // perturbs the convergence rate (by ~1e-7 per step), not the converged T.
-        const double dT = (e - e_target) * (double)__frcp_rn((float)cv);
+        const double dT = res * (double)__frcp_rn((float)cv);
         T = T - dT;
-        if (fabs(dT) <= 1.0e-13 * fabs(T)) {
+        if (fabs(dT) <= tol) {
             if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS>(M, nasa_range_of(M, T), Y, Rm, P);
             return true;
         }

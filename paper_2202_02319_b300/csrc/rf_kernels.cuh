@@ -56,14 +56,14 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
         const int nrc = M.n_reac[j], npd = M.n_prod[j];
         R cf = kf;
         for (int k = 0; k < nrc; ++k) cf *= sCb[M.reac[j][k] * stride];
-        double rv = 0.0;
+        R q = cf;
         if (M.rev[j]) {
-            double pr = (double)kf;
-            for (int k = 0; k < npd; ++k) pr *= sP[M.prod[j][k] * stride];
+            // k_f (cf / k_f - prod_prod (C G) prod_reac (1/G)) with the reverse term in FP64
+            double pr = npd > 0 ? sP[M.prod[j][0] * stride] : 1.0;
+            for (int k = 1; k < npd; ++k) pr *= sP[M.prod[j][k] * stride];
             for (int k = 0; k < nrc; ++k) pr *= sRr[M.reac[j][k] * stride];
-            rv = pr;
+            q = (R)fma(-(double)kf, pr, (double)cf);
         }
-        const R q = (R)((double)cf - rv);
         for (int k = 0; k < M.n_net[j]; ++k) {
             const int s = M.net_sp[j][k];
             sW[s * stride] = fma((R)M.net_nu[j][k], q, sW[s * stride]);
@@ -262,12 +262,12 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             const int k = (int)(cell / nxy);
             const long long rem = cell - (long long)k * nxy;
             const int j = (int)(rem / m.nx), i = (int)(rem - (long long)j * m.nx);
-            const double dx = (i + 0.5) * m.h[0] - m.las[1];
-            const double dy = (j + 0.5) * m.h[1] - m.las[2];
-            double r2 = dx * dx + dy * dy;
+            const double dx = fma((double)i, m.h[0], fma(0.5, m.h[0], -m.las[1]));
+            const double dy = fma((double)j, m.h[1], fma(0.5, m.h[1], -m.las[2]));
+            double r2 = fma(dx, dx, dy * dy);
             if (m.nz > 1) {
-                const double dz = (k + 0.5) * m.h[2] - m.las[3];
-                r2 += dz * dz;
+                const double dz = fma((double)k, m.h[2], fma(0.5, m.h[2], -m.las[3]));
+                r2 = fma(dz, dz, r2);
             }
             if (sizeof(R) == 8) qL = s_laser[0] * exp(s_laser[1] * r2);
             else qL = s_laser[0] * (double)expf((float)(s_laser[1] * r2));
