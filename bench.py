@@ -249,6 +249,9 @@ def run_ours(args):
     # --- batched ensemble (64 members of uneven size): members/s per launch mode
     ens = run_ensemble_leg(args, dev) if args.ensemble_members > 0 else None
 
+    # --- discrete adjoint: checkpointed ignition gradient of one 64^3 member (FP64)
+    adj = run_adjoint_leg(args, dev) if args.adjoint_steps > 0 else None
+
     # --- roofline of the dominant kernel of the mixed step
     peaks = _peaks()
     fp64_peak = nv.probe_peak(0)
@@ -307,6 +310,7 @@ def run_ours(args):
         "kernels": kernels,
         "roofline": roofline,
         "ensemble": ens,
+        "adjoint": adj,
         "peaks_measured": {"fp64_tflops": round(fp64_peak, 4), "fp32_tflops": round(fp32_peak, 3),
                            "hbm_gbs": peaks["hbm_gbs"], "hbm_source": peaks["source"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -322,6 +326,41 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- adjoint leg
+
+def run_adjoint_leg(args, dev):
+    """Gradient of the time-integrated heat release with respect to (E, x0, y0, z0,
+    sigma_r, ln A_j) for one jet member: forward run with checkpoints, then the
+    reverse sweep (recomputation within segments, RK-step adjoints), both FP64.
+    The pulse is centred inside the window so that every laser gradient is nonzero."""
+    import time
+    import torch
+    from paper_2202_02319_b300 import adjoint, synth
+    n, nsteps, dt = args.adjoint_n, args.adjoint_steps, 1e-9
+    case = synth.case_jet(0, n, device=dev)
+    case.laser.t0 = 0.5 * nsteps * dt
+    prob = adjoint.HeatReleaseProblem(case.mech, case.grid, case.prim, case.laser, nsteps=nsteps, dt=dt,
+                                      checkpoint_every=max(1, nsteps // 2), device=dev)
+    p0 = prob.default_params()
+    prob.run(p0, keep=False)                      # warm-up (also builds the kernels' first launches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prob.run(p0, keep=False)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J = prob.run(p0, keep=True)
+    g = prob.gradient()
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    cells = case.grid.ncells
+    return {"cells": cells, "steps": nsteps, "dt_s": dt, "checkpoint_every": prob.ck, "params": int(p0.numel()),
+            "forward_ms": round(t_fwd * 1e3, 2), "forward_and_gradient_ms": round(t_grad * 1e3, 2),
+            "gradient_over_forward": round(t_grad / t_fwd, 2),
+            "cell_updates_per_s_forward": cells * 3 * nsteps / t_fwd, "J": J,
+            "dJ_dE": float(g[0]), "timing": "host clock around synchronised calls, FP64"}
 
 
 # ----------------------------------------------------------------------------- ensemble leg
@@ -432,6 +471,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble-members", type=int, default=64)
     ap.add_argument("--ensemble-steps", type=int, default=2)
+    ap.add_argument("--adjoint-n", type=int, default=64)
+    ap.add_argument("--adjoint-steps", type=int, default=20)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
