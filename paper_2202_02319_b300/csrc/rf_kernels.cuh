@@ -563,10 +563,13 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
         const double *__restrict__ Uk = m.U;
         const double *__restrict__ Un = m.Un;
         double *__restrict__ Uo = m.Uout;
+        // first stage (a = 0, b = 1): U + dt L, the same value without U^n
+        const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             const double L = (double)fma(dG[v], ih, rhs[v * n + cell]);
-            Uo[v * n + cell] = fma(m.stage_a, Un[v * n + cell], m.stage_b * fma(dt, L, Uk[v * n + cell]));
+            Uo[v * n + cell] = euler ? fma(dt, L, Uk[v * n + cell])
+                                     : fma(m.stage_a, Un[v * n + cell], m.stage_b * fma(dt, L, Uk[v * n + cell]));
         }
     }
 }
@@ -820,6 +823,7 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
 
     const float ih = (float)m.invh[DIR];
     const long long lbase = (long long)x + (long long)o * so;
+    const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
     float Gp[NV];
     for (int f = c0; f <= c1; ++f) {
         if (f + 2 <= c1 + 1) stage_I(f + 2);
@@ -840,7 +844,7 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     uk[v] = m.U[v * n + cell];
-                    un[v] = m.Un[v * n + cell];
+                    un[v] = euler ? 0.0 : m.Un[v * n + cell];
                 }
             }
         }
@@ -865,7 +869,8 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
                     const float L = fma(Gn[v] - Gp[v], ih, racc[v]);
                     if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
                     else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
-                    else m.Uout[v * n + cell] = fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+                    else m.Uout[v * n + cell] = euler ? fma(dt, (double)L, uk[v])
+                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
                 }
             }
 #pragma unroll
@@ -986,6 +991,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     };
 
     const float ih = (float)m.invh[0];
+    const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
     float Gc[NV];                      // lane 31's flux of the previous chunk
     stage(0, buf0);
     cp_async_commit();
@@ -1010,7 +1016,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     uk[v] = m.U[v * n + cell];
-                    un[v] = m.Un[v * n + cell];
+                    un[v] = euler ? 0.0 : m.Un[v * n + cell];
                 }
             }
         }
@@ -1043,7 +1049,8 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
                 const float L = fma(G[v] - Gl[v], ih, racc[v]);
                 if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
                 else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
-                else m.Uout[v * n + cell] = fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+                else m.Uout[v * n + cell] = euler ? fma(dt, (double)L, uk[v])
+                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
             }
         }
         __syncwarp();
