@@ -357,7 +357,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 __device__ __forceinline__ float rcp_face(float x) { return rcp_approx(x); }
-__device__ __forceinline__ double rcp_face(double x) { return 1.0 / x; }
+__device__ __forceinline__ double rcp_face(double x) { return rcp64(x); }
 
 // The same WENO3-Z value in FP32 with the fused operations written out: with
 // d0 = b - a, d1 = c - b the candidates are q0 = b + d0/2, q1 = b + d1/2, and
@@ -375,6 +375,25 @@ __device__ __forceinline__ float weno3z<float>(float a, float b, float c) {
     const float a1 = (2.0f / 3.0f) * (b0 * (b1 + t));
     const float om0 = a0 * rcp_approx(a0 + a1);
     return fmaf(om0, 0.5f * (d0 - d1), fmaf(0.5f, d1, b));
+}
+
+// The same value in FP64.  The weights are invariant under a common scale of the
+// betas, so S is normalised by the exact power of two 2^-E(S) (E the exponent of S,
+// read from its bits): no rounding, and no division.  a0 + a1 lies in [1/12, 4], so
+// the one remaining reciprocal is the Newton-Raphson rcp64.
+template <>
+__device__ __forceinline__ double weno3z<double>(double a, double b, double c) {
+    const double d0 = b - a, d1 = c - b;
+    const double beta0 = d0 * d0, beta1 = d1 * d1;
+    const double S = (beta0 + beta1) + 2.0 * EPS_WENO;
+    const double iS = __hiloint2double((2046 - ((__double2hiint(S) >> 20) & 0x7ff)) << 20, 0);
+    const double eS = EPS_WENO * iS;
+    const double b0 = fma(beta0, iS, eS), b1 = fma(beta1, iS, eS);
+    const double t = fabs(beta1 - beta0) * iS;
+    const double a0 = (1.0 / 3.0) * (b1 * (b0 + t));
+    const double a1 = (2.0 / 3.0) * (b0 * (b1 + t));
+    const double om0 = a0 * rcp64(a0 + a1);
+    return fma(om0, 0.5 * (d0 - d1), fma(0.5, d1, b));
 }
 
 // Stencil of one face along DIR read from global memory.  Cells o = 0..3 are
