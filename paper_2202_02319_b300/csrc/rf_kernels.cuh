@@ -320,7 +320,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 }
 
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) cell_state_kernel(int mslot, const __grid_constant__ Member m,
+__global__ void __launch_bounds__(128, 5) cell_state_kernel(int mslot, const __grid_constant__ Member m,
                                                          int newton_maxit) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
