@@ -207,7 +207,8 @@ int rf_adjoint_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_las
 /* One SSP-RK3 step at fixed dt through rf_rhs evaluations and stage
  * combinations (the arithmetic rf_adjoint_rk_step differentiates): U and T are
  * advanced in place and, if J (host) is not NULL, *J += dt (H(U^n) + H(U^(1)) +
- * 4 H(U^(2))) / 6.  Synchronous. */
+ * 4 H(U^(2))) / 6 (with J NULL no heat release is evaluated: a plain step of the
+ * same arithmetic, as the checkpoint recomputation needs).  Synchronous. */
 int rf_rk_step_objective(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *laser, double *J,
                          rf_stream s);
 

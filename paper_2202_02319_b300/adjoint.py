@@ -79,7 +79,7 @@ class HeatReleaseProblem:
             for k in range(k0, k1):                # recompute the segment's step inputs
                 seg.append((U.clone(), T.clone()))
                 if k + 1 < k1:
-                    nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las)
+                    nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las, want_J=False)
             for k in range(k1 - 1, k0 - 1, -1):
                 Un, Tn = seg[k - k0]
                 nv.adjoint_rk_step(ctx, Un, Tn, self.t0 + k * self.dt, self.dt, las, 1.0, lam, grads)

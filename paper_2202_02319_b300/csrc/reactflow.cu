@@ -617,7 +617,7 @@ struct Path {
         LAUNCH_CHECK();
         const int nvals = NS + 6;
         double *res = c->diag + (size_t)c->diag_blocks * nvals;
-        diag_fold_kernel<<<1, 32, 0, s>>>(c->diag, c->diag_blocks, nvals, res);
+        diag_fold_kernel<<<1, 32 * nvals, 0, s>>>(c->diag, c->diag_blocks, nvals, res);
         LAUNCH_CHECK();
         double host[32];
         CUDA_TRY(cudaMemcpyAsync(host, res, nvals * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1299,10 +1299,13 @@ struct AdjPath {
         const double ts[3] = {t, t + dt, t + 0.5 * dt};
         double H[3];
         for (int k = 0; k < 3; ++k) {
-            rf_diag dg;
-            rc = Path<double, NS>::diagnostics(c, in[k], T, &dg, s);
-            if (rc) return rc;
-            H[k] = dg.heat_release;
+            H[k] = 0.0;
+            if (J) {           // the heat release only when the objective is requested
+                rf_diag dg;
+                rc = Path<double, NS>::diagnostics(c, in[k], T, &dg, s);
+                if (rc) return rc;
+                H[k] = dg.heat_release;
+            }
             rc = Path<double, NS>::rhs(c, in[k], T, ts[k], L, w.R, s);
             if (rc) return rc;
             if (k == 0) {   // U1 = Un + dt R

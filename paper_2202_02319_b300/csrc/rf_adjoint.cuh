@@ -5,10 +5,9 @@
 //   1. face adjoint: G_bar(f) = (lambda(f-1) - lambda(f)) / h_d; the hand-written
 //      reverse of the face flux scatters into U_bar and Q_bar of the stencil cells
 //      (FP64 atomics);
-//   2. cell adjoint: U_bar(cell) += (dQ/dU)^T Q_bar + (dS/dU)^T lambda, with the
-//      per-cell Jacobians from forward-mode dual numbers over the cell's conserved
-//      variables (the temperature tangent is one Newton step at the converged T:
-//      dT = (de - sum_s (de/dY_s) dY_s) / cv, the implicit-function derivative).
+//   2. cell adjoint: U_bar(cell) += (dQ/dU)^T Q_bar + (dS/dU)^T lambda by a
+//      hand-written reverse pass of the cell-state map (the temperature's adjoint
+//      through one Newton step at the converged T: the implicit-function derivative).
 // Parameter gradients (laser E, x0, y0, z0, sigma_r; ln A_j) are analytic.
 // Non-smooth points take the subgradient of the forward branch: the LLF maximum
 // goes to the stencil cell that attains it, |beta1 - beta0| has slope 0 at equality.
@@ -18,247 +17,311 @@
 
 namespace rf {
 
-// ----------------------------------------------------------------------------- dual numbers
-
-template <int K>
-struct Dual {
-    double v;
-    double d[K];
-};
-
-template <int K> __device__ __forceinline__ Dual<K> dconst(double a) {
-    Dual<K> r;
-    r.v = a;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = 0.0;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator+(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v + b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] + b.d[k];
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator-(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v - b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] - b.d[k];
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator*(const Dual<K> &a, const Dual<K> &b) {
-    Dual<K> r;
-    r.v = a.v * b.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator*(const Dual<K> &a, double b) {
-    Dual<K> r;
-    r.v = a.v * b;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * b;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator*(double b, const Dual<K> &a) { return a * b; }
-template <int K> __device__ __forceinline__ Dual<K> operator+(const Dual<K> &a, double b) {
-    Dual<K> r = a;
-    r.v += b;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator-(const Dual<K> &a, double b) {
-    Dual<K> r = a;
-    r.v -= b;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> recip(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = 1.0 / a.v;
-    const double g = -r.v * r.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> operator/(const Dual<K> &a, const Dual<K> &b) { return a * recip(b); }
-template <int K> __device__ __forceinline__ Dual<K> dexp(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = exp(a.v);
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * r.v;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> dlog(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = log(a.v);
-    const double g = 1.0 / a.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
-    return r;
-}
-template <int K> __device__ __forceinline__ Dual<K> dsqrt(const Dual<K> &a) {
-    Dual<K> r;
-    r.v = sqrt(a.v);
-    const double g = 0.5 / r.v;
-#pragma unroll
-    for (int k = 0; k < K; ++k) r.d[k] = a.d[k] * g;
-    return r;
-}
-
 // ----------------------------------------------------------------------------- per-cell map
 
-// The cell-state map U -> (Q, omega, HRR) of the FP64 path, in dual arithmetic.
-// Tc is the converged temperature of the forward evaluation.  Outputs: Q[8+3NS]
-// in the Q field order, W[NS] = omega_s (kg/m^3/s), hrr = -sum_s h_s omega_s.
-// sbuf: per-thread scratch of 4*NS duals for the run-time-indexed chemistry.
-template <int K, int NS>
-__device__ void cell_map(const MechDev &M, const Dual<K> (&U)[NS + 4], double Tc, bool chem, Dual<K> *Q, Dual<K> *W,
-                         Dual<K> &hrr, Dual<K> *sC, Dual<K> *sP, Dual<K> *sR, Dual<K> *sWd) {
-    using D = Dual<K>;
-    constexpr int NQ = QL<NS>::NQ;
-    D rho = U[0];
+// Reverse (vector-Jacobian product) of the FP64 cell-state map U -> (Q, omega,
+// HRR) in one pass: the forward values are recomputed, then
+//   Ub += (dQ/dU)^T Qb + (d omega/dU)^T lamS + hb (dHRR/dU),
+// where Qb(q) = Qbar[q * n + cell].  The temperature is one Newton
+// step T = Tc - (e(Tc; Y) - e) / cv(Tc; Y) from the converged Tc, so its adjoint is
+// the implicit-function derivative.  Species arrays indexed by the compact
+// stoichiometry at run time (C, C G, 1/G and their adjoints) live in per-thread
+// local memory.
+template <int NS>
+__device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], double Tc, bool chem,
+                                 const double *__restrict__ Qbar, long long n, long long cell,
+                                 const double *__restrict__ lam, double hb, double (&Ub)[NS + 4]) {
+    constexpr int NV = NS + 4;
+    auto QB = [&](int q) { return Qbar[(size_t)q * n + cell]; };
+    // ---------------------------------------------------------------- forward values
+    double rho = U[0];
 #pragma unroll
-    for (int s = 1; s < NS; ++s) rho = rho + U[s];
-    const D irho = recip(rho);
-    const D u = U[NS] * irho, v = U[NS + 1] * irho, w = U[NS + 2] * irho;
-    D Y[NS];
-    D Rm = dconst<K>(0.0);
+    for (int s = 1; s < NS; ++s) rho += U[s];
+    const double irho = 1.0 / rho;
+    const double u = U[NS] * irho, v = U[NS + 1] * irho, w = U[NS + 2] * irho;
+    double Y[NS], Rm = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         Y[s] = U[s] * irho;
-        Rm = Rm + Y[s] * M.RW[s];
+        Rm += Y[s] * M.RW[s];
     }
-    const D e = U[NS + 3] * irho - 0.5 * (u * u + v * v + w * w);
-    // temperature: one Newton step in dual arithmetic from the converged value
+    const double e = U[NS + 3] * irho - 0.5 * (u * u + v * v + w * w);
     const int rng = nasa_range(M, Tc);
     const double invTc = 1.0 / Tc;
-    D em = dconst<K>(0.0), cvm = dconst<K>(0.0);
+    double es[NS], cvs[NS], em = 0.0, cvm = 0.0;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const double es = (h_RT(M, rng, s, Tc, invTc) - 1.0) * M.RW[s] * Tc;
-        const double cvs = (cp_R<double>(M, rng, s, Tc) - 1.0) * M.RW[s];
-        em = em + Y[s] * es;
-        cvm = cvm + Y[s] * cvs;
+        es[s] = (h_RT(M, rng, s, Tc, invTc) - 1.0) * M.RW[s] * Tc;
+        cvs[s] = (cp_R<double>(M, rng, s, Tc) - 1.0) * M.RW[s];
+        em += Y[s] * es[s];
+        cvm += Y[s] * cvs[s];
     }
-    const D T = dconst<K>(Tc) - (em - e) / cvm;
-    const D invT = recip(T);
-    // cp(T), h_s(T) as polynomials in the dual temperature
-    D cpm = dconst<K>(0.0);
-    D hs[NS], cps[NS];
+    const double icv = 1.0 / cvm, res = em - e;
+    const double T = Tc - res * icv;
+    const double invT = 1.0 / T;
+    double cps[NS], cpm = 0.0, hs[NS], dhs[NS], dcps[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const double *a = M.cpc[rng][s];
         cps[s] = ((((T * a[4] + a[3]) * T + a[2]) * T + a[1]) * T + a[0]) * M.RW[s];
-        cpm = cpm + Y[s] * cps[s];
+        dcps[s] = (((4.0 * a[4] * T + 3.0 * a[3]) * T + 2.0 * a[2]) * T + a[1]) * M.RW[s];
+        cpm += Y[s] * cps[s];
         const double *c = M.ec[rng][s];
-        const D hrt = ((((T * c[4] + c[3]) * T + c[2]) * T + c[1]) * T + c[0]) + invT * c[5];
-        hs[s] = hrt * T * M.RW[s];
+        const double Pe = (((T * c[4] + c[3]) * T + c[2]) * T + c[1]) * T + c[0];
+        const double dPe = ((4.0 * c[4] * T + 3.0 * c[3]) * T + 2.0 * c[2]) * T + c[1];
+        hs[s] = (Pe + invT * c[5]) * T * M.RW[s];            // = RW (T Pe(T) + c5)
+        dhs[s] = (Pe + T * dPe) * M.RW[s];
     }
-    const D cv = cpm - Rm;
-    const D p = rho * Rm * T;
-    const D c = dsqrt(cpm / cv * Rm * T);
-    Q[Q_U] = u;
-    Q[Q_V] = v;
-    Q[Q_W] = w;
-    Q[Q_P] = p;
-    Q[Q_C] = c;
-    Q[Q_T] = T;
-    D X[NS];
-    const D irm = recip(Rm);
+    const double cv = cpm - Rm;
+    const double p = rho * Rm * T;
+    const double r = cpm / cv;
+    const double c = sqrt(r * Rm * T);
+    const double irm = 1.0 / Rm;
+    double X[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) X[s] = Y[s] * M.RW[s] * irm;
+    const double lnTs = log(T * (1.0 / 300.0));
+    double mus[NS], sq[NS], isq[NS], den[NS], xr[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        X[s] = Y[s] * M.RW[s] * irm;
-        Q[QL<NS>::X + s] = X[s];
-        Q[QL<NS>::H + s] = hs[s];
+        mus[s] = exp(lnTs * M.mu_exp[s]) * M.mu_ref[s];
+        sq[s] = sqrt(mus[s]);
+        isq[s] = 1.0 / sq[s];
     }
-    // transport
-    const D lnTs = dlog(T * (1.0 / 300.0));
-    D mus[NS], sq[NS], isq[NS];
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-        mus[s] = dexp(lnTs * M.mu_exp[s]) * M.mu_ref[s];
-        sq[s] = dsqrt(mus[s]);
-        isq[s] = recip(sq[s]);
-    }
-    D mu = dconst<K>(0.0), lam = dconst<K>(0.0);
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
-        D den = dconst<K>(0.0);
+        double d = 0.0;
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-            const D a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
-            den = den + X[j] * (a * a) * M.wd[i][j];
+            const double a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
+            d += X[j] * (a * a) * M.wd[i][j];
         }
-        const D xr = X[i] / den;
-        mu = mu + xr * mus[i];
-        lam = lam + xr * mus[i] * (cps[i] + M.eucken[i]);
+        den[i] = d;
+        xr[i] = X[i] / d;
     }
-    Q[Q_MU] = mu;
-    Q[Q_LAM] = lam;
-    if (NS == 1) {
-        Q[QL<NS>::DC] = dconst<K>(0.0);
-    } else {
-        const D fT = dexp(lnTs * 1.75) * PATM / p;
-        D Xe[NS];
-        D Wbe = dconst<K>(0.0);
+    // ---------------------------------------------------------------- reverse
+    double Yb[NS], Xb[NS], hsb[NS], cpsb[NS];
 #pragma unroll
-        for (int j = 0; j < NS; ++j) {
-            Xe[j] = X[j] + EPS_D;
-            Wbe = Wbe + Xe[j] * M.W[j];
-        }
-        const D rhoW = rho * Rm * (1.0 / RU);          // rho / Wbar
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            D num = dconst<K>(0.0), den = dconst<K>(0.0);
-#pragma unroll
-            for (int j = 0; j < NS; ++j) {
-                if (j == s) continue;
-                num = num + Xe[j] * M.W[j];
-                den = den + Xe[j] * M.invDref[s][j];
-            }
-            const D Dm = num * fT / (Wbe * den);
-            Q[QL<NS>::DC + s] = rhoW * Dm * M.W[s];
-        }
+    for (int s = 0; s < NS; ++s) {
+        Yb[s] = 0.0;
+        Xb[s] = QB(QL<NS>::X + s);
+        hsb[s] = QB(QL<NS>::H + s);
+        cpsb[s] = 0.0;
     }
-    // chemistry
 #pragma unroll
-    for (int s = 0; s < NS; ++s) W[s] = dconst<K>(0.0);
-    hrr = dconst<K>(0.0);
+    for (int v2 = 0; v2 < NV; ++v2) Ub[v2] = 0.0;
+    double Tb = QB(Q_T), pb = QB(Q_P), cb = QB(Q_C), ub = QB(Q_U), vb = QB(Q_V), wb = QB(Q_W);
+    const double mub = QB(Q_MU), lamb = QB(Q_LAM);
+    double rhob = 0.0, Rmb = 0.0, irhob = 0.0, lnTsb = 0.0, invTb = 0.0;
+    // chemistry: omega_s = W_s sum_j nu_sj q_j, HRR = -sum_s h_s omega_s
     if (chem && M.nr > 0) {
-        const D lnT = dlog(T);
+        const double lnT = log(T);
+        double G[NS], C[NS], sP[NS], sR[NS], sCb[NS], sPb[NS], sRb[NS], wd[NS];
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const double *g = M.gc[rng][s];
-            const D lnGs = (((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6];
-            const D G = dexp(lnGs);
-            sC[s] = U[s] * M.invW[s];
-            sP[s] = sC[s] * G;
-            sR[s] = recip(G);
-            sWd[s] = dconst<K>(0.0);
+            G[s] = exp((((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6]);
+            C[s] = U[s] * M.invW[s];
+            sP[s] = C[s] * G[s];
+            sR[s] = 1.0 / G[s];
+            sCb[s] = sPb[s] = sRb[s] = 0.0;
+            wd[s] = 0.0;
         }
+        // forward rates (omega needed for the HRR adjoint)
         for (int j = 0; j < M.nr; ++j) {
-            const D kf = dexp(lnT * M.b[j] - invT * M.Theta[j] + M.lnA[j]);
-            D cf = kf;
-            for (int k = 0; k < M.n_reac[j]; ++k) cf = cf * sC[M.reac[j][k]];
-            D q = cf;
+            const double kf = exp(lnT * M.b[j] - invT * M.Theta[j] + M.lnA[j]);
+            double cf = kf;
+            for (int k = 0; k < M.n_reac[j]; ++k) cf *= C[M.reac[j][k]];
+            double q = cf;
             if (M.rev[j]) {
-                D pr = kf;
-                for (int k = 0; k < M.n_prod[j]; ++k) pr = pr * sP[M.prod[j][k]];
-                for (int k = 0; k < M.n_reac[j]; ++k) pr = pr * sR[M.reac[j][k]];
-                q = q - pr;
+                double pr = kf;
+                for (int k = 0; k < M.n_prod[j]; ++k) pr *= sP[M.prod[j][k]];
+                for (int k = 0; k < M.n_reac[j]; ++k) pr *= sR[M.reac[j][k]];
+                q -= pr;
             }
-            for (int k = 0; k < M.n_net[j]; ++k) {
-                const int s = M.net_sp[j][k];
-                sWd[s] = sWd[s] + q * (double)M.net_nu[j][k];
+            for (int k = 0; k < M.n_net[j]; ++k) wd[M.net_sp[j][k]] += q * (double)M.net_nu[j][k];
+        }
+        double sWdb[NS];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const double Ws = wd[s] * M.W[s];
+            hsb[s] -= hb * Ws;
+            sWdb[s] = (lam[(size_t)s * n + cell] - hb * hs[s]) * M.W[s];
+        }
+        double lnTb = 0.0;
+        for (int j = 0; j < M.nr; ++j) {
+            double qb = 0.0;
+            for (int k = 0; k < M.n_net[j]; ++k) qb += sWdb[M.net_sp[j][k]] * (double)M.net_nu[j][k];
+            if (qb == 0.0) continue;
+            const double kf = exp(lnT * M.b[j] - invT * M.Theta[j] + M.lnA[j]);
+            const int nrc = M.n_reac[j], npd = M.n_prod[j];
+            double prodC = 1.0;
+            for (int k = 0; k < nrc; ++k) prodC *= C[M.reac[j][k]];
+            double kfb = qb * prodC;
+            for (int k = 0; k < nrc; ++k) {
+                double part = qb * kf;
+                for (int k2 = 0; k2 < nrc; ++k2)
+                    if (k2 != k) part *= C[M.reac[j][k2]];
+                sCb[M.reac[j][k]] += part;
             }
+            if (M.rev[j]) {
+                double prodR = 1.0;
+                for (int k = 0; k < npd; ++k) prodR *= sP[M.prod[j][k]];
+                for (int k = 0; k < nrc; ++k) prodR *= sR[M.reac[j][k]];
+                kfb -= qb * prodR;
+                for (int k = 0; k < npd; ++k) {
+                    double part = -qb * kf;
+                    for (int k2 = 0; k2 < npd; ++k2)
+                        if (k2 != k) part *= sP[M.prod[j][k2]];
+                    for (int k2 = 0; k2 < nrc; ++k2) part *= sR[M.reac[j][k2]];
+                    sPb[M.prod[j][k]] += part;
+                }
+                for (int k = 0; k < nrc; ++k) {
+                    double part = -qb * kf;
+                    for (int k2 = 0; k2 < npd; ++k2) part *= sP[M.prod[j][k2]];
+                    for (int k2 = 0; k2 < nrc; ++k2)
+                        if (k2 != k) part *= sR[M.reac[j][k2]];
+                    sRb[M.reac[j][k]] += part;
+                }
+            }
+            const double zb = kfb * kf;
+            lnTb += zb * M.b[j];
+            invTb -= zb * M.Theta[j];
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            W[s] = sWd[s] * M.W[s];
-            hrr = hrr - hs[s] * W[s];
+            const double Gb = sPb[s] * C[s] - sRb[s] * sR[s] * sR[s];
+            Ub[s] += (sCb[s] + sPb[s] * G[s]) * M.invW[s];
+            const double lnGb = Gb * G[s];
+            const double *g = M.gc[rng][s];
+            Tb += lnGb * ((((4.0 * g[4] * T + 3.0 * g[3]) * T + 2.0 * g[2]) * T + g[1]));
+            invTb += lnGb * g[5];
+            lnTb += lnGb * g[6];
+        }
+        Tb += lnTb * invT;
+    }
+    // mixture-averaged diffusion: Dc_s = (rho / Wbar) D_s W_s
+    if (NS > 1) {
+        const double fT = exp(1.75 * lnTs) * PATM / p;
+        double Xe[NS], Wbe = 0.0;
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            Xe[j] = X[j] + EPS_D;
+            Wbe += Xe[j] * M.W[j];
+        }
+        const double rhoW = rho * Rm * (1.0 / RU);
+        double rhoWb = 0.0, fTb = 0.0, Wbeb = 0.0, Xeb[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) Xeb[j] = 0.0;
+#pragma unroll
+        for (int s2 = 0; s2 < NS; ++s2) {
+            double num = 0.0, dd = 0.0;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                if (j == s2) continue;
+                num += Xe[j] * M.W[j];
+                dd += Xe[j] * M.invDref[s2][j];
+            }
+            const double Dm = num * fT / (Wbe * dd);
+            const double QDb = QB(QL<NS>::DC + s2);
+            rhoWb += QDb * Dm * M.W[s2];
+            const double t = QDb * rhoW * M.W[s2] * Dm;          // Dm_bar * Dm
+            const double numb = t / num, ddb = -t / dd;
+            fTb += t / fT;
+            Wbeb -= t / Wbe;
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                if (j == s2) continue;
+                Xeb[j] += numb * M.W[j] + ddb * M.invDref[s2][j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NS; ++j) Xb[j] += Xeb[j] + Wbeb * M.W[j];
+        rhob += rhoWb * Rm * (1.0 / RU);
+        Rmb += rhoWb * rho * (1.0 / RU);
+        lnTsb += fTb * fT * 1.75;
+        pb -= fTb * fT / p;
+    }
+    // Wilke viscosity and conductivity
+    double sqb[NS], isqb[NS], musb[NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sqb[s] = isqb[s] = 0.0;
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        const double fac = cps[i] + M.eucken[i];
+        const double xrb = mub * mus[i] + lamb * mus[i] * fac;
+        musb[i] = mub * xr[i] + lamb * xr[i] * fac;
+        cpsb[i] += lamb * xr[i] * mus[i];
+        Xb[i] += xrb / den[i];
+        const double denb = -xrb * xr[i] / den[i];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const double a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
+            Xb[j] += denb * (a * a) * M.wd[i][j];
+            const double ab = denb * X[j] * 2.0 * a * M.wd[i][j];
+            sqb[i] += ab * isq[j] * M.wc[i][j];
+            isqb[j] += ab * sq[i] * M.wc[i][j];
         }
     }
-    (void)NQ;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        sqb[s] -= isqb[s] * isq[s] * isq[s];
+        musb[s] += sqb[s] * 0.5 / sq[s];
+        lnTsb += musb[s] * mus[s] * M.mu_exp[s];
+    }
+    Tb += lnTsb / T;
+    // X_s = Y_s RW_s / Rm
+    double irmb = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        Yb[s] += Xb[s] * M.RW[s] * irm;
+        irmb += Xb[s] * Y[s] * M.RW[s];
+    }
+    Rmb -= irmb * irm * irm;
+    // c = sqrt(cpm / cv Rm T), p = rho Rm T, cv = cpm - Rm
+    const double zb = cb * 0.5 / c;
+    const double rb = zb * Rm * T;
+    Rmb += zb * r * T;
+    Tb += zb * r * Rm;
+    double cpmb = rb / cv;
+    const double cvb = -rb * r / cv;
+    rhob += pb * Rm * T;
+    Rmb += pb * rho * T;
+    Tb += pb * rho * Rm;
+    cpmb += cvb;
+    Rmb -= cvb;
+    // h_s(T), cp_s(T), cpm
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        Tb += hsb[s] * dhs[s];
+        Yb[s] += cpmb * cps[s];
+        cpsb[s] += cpmb * Y[s];
+        Tb += cpsb[s] * dcps[s];
+    }
+    Tb -= invTb * invT * invT;
+    // T = Tc - (em - e) / cvm
+    const double emb = -Tb * icv, eb = Tb * icv, cvmb = Tb * res * icv * icv;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Yb[s] += emb * es[s] + cvmb * cvs[s] + Rmb * M.RW[s];
+    // e = E / rho - |u|^2 / 2
+    Ub[NS + 3] += eb * irho;
+    irhob += eb * U[NS + 3];
+    ub -= eb * u;
+    vb -= eb * v;
+    wb -= eb * w;
+    // Y, u, v, w, rho
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        Ub[s] += Yb[s] * irho;
+        irhob += Yb[s] * U[s];
+    }
+    Ub[NS] += ub * irho;
+    Ub[NS + 1] += vb * irho;
+    Ub[NS + 2] += wb * irho;
+    irhob += ub * U[NS] + vb * U[NS + 1] + wb * U[NS + 2];
+    rhob -= irhob * irho * irho;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Ub[s] += rhob;
 }
 
 // Rate of progress q_j of every reaction at a cell (FP64 values), for the
@@ -297,8 +360,7 @@ __global__ void __launch_bounds__(64) adjoint_cell_kernel(int mslot, const __gri
                                                           double *__restrict__ Ubar, double *__restrict__ grads,
                                                           double wH) {
     const MechDev &M = c_mech[mslot];
-    constexpr int NV = NS + 4, NQ = QL<NS>::NQ, K = 4;
-    using D = Dual<K>;
+    constexpr int NV = NS + 4;
     const long long n = m.n;
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     __shared__ double red[5 + NRMAX][64];
@@ -311,27 +373,10 @@ __global__ void __launch_bounds__(64) adjoint_cell_kernel(int mslot, const __gri
 #pragma unroll
         for (int v = 0; v < NV; ++v) Uv[v] = m.U[v * n + cell];
         const double Tc = m.T[cell];
-        D Uin[NV], Qo[NQ], Wo[NS], hrr, sC[NS], sP[NS], sR[NS], sWd[NS];
-        for (int k0 = 0; k0 < NV; k0 += K) {
+        double Ub[NV];
+        cell_map_reverse<NS>(M, Uv, Tc, chem, Qbar, n, cell, lam, wH * dV, Ub);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                Uin[v] = dconst<K>(Uv[v]);
-#pragma unroll
-                for (int k = 0; k < K; ++k)
-                    if (v == k0 + k) Uin[v].d[k] = 1.0;
-            }
-            cell_map<K, NS>(M, Uin, Tc, chem, Qo, Wo, hrr, sC, sP, sR, sWd);
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                if (k0 + k >= NV) break;
-                double acc = 0.0;
-                for (int q = 0; q < NQ; ++q) acc = fma(Qbar[(size_t)q * n + cell], Qo[q].d[k], acc);
-#pragma unroll
-                for (int s = 0; s < NS; ++s) acc = fma(lam[(size_t)s * n + cell], Wo[s].d[k], acc);
-                acc = fma(wH * dV, hrr.d[k], acc);
-                Ubar[(size_t)(k0 + k) * n + cell] += acc;
-            }
-        }
+        for (int v = 0; v < NV; ++v) Ubar[(size_t)v * n + cell] += Ub[v];
         // parameter gradients
         if (chem && M.nr > 0) {
             double rs[NS], qj[NRMAX], sG[NS];

@@ -1263,15 +1263,22 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
     }
 }
 
+// One warp per value: lane l folds partials l, l + 32, ... in order, then a fixed
+// shuffle tree combines the lanes (the last value is a maximum).  Deterministic.
 __global__ void diag_fold_kernel(const double *partial, int nblocks, int nvals, double *out) {
-    const int v = threadIdx.x;
+    const int v = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (v >= nvals) return;
+    const bool is_max = v == nvals - 1;
     double acc = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
+    for (int b = lane; b < nblocks; b += 32) {
         const double x = partial[(size_t)b * nvals + v];
-        acc = (v == nvals - 1) ? fmax(acc, x) : acc + x;
+        acc = is_max ? fmax(acc, x) : acc + x;
     }
-    out[v] = acc;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_xor_sync(0xffffffffu, acc, o);
+        acc = is_max ? fmax(acc, y) : acc + y;
+    }
+    if (lane == 0) out[v] = acc;
 }
 
 }  // namespace rf

@@ -308,12 +308,13 @@ def adjoint_rhs(ctx: Context, U, T, t: float, laser, lam_dUdt, w_hrr: float, lam
                                _ptr(grad_params), _stream(stream)), "rf_adjoint_rhs")
 
 
-def rk_step_objective(ctx: Context, U, T, t: float, dt: float, laser=None, stream=None) -> float:
-    """Advances U, T by one RK3 step; returns this step's dt sum_k b_k H(U^(k))."""
+def rk_step_objective(ctx: Context, U, T, t: float, dt: float, laser=None, stream=None, want_J: bool = True) -> float:
+    """Advances U, T by one RK3 step; returns this step's dt sum_k b_k H(U^(k))
+    (0.0 without evaluating H when want_J is False)."""
     L = _laser(laser)
     J = ctypes.c_double(0.0)
     _check(_lib.rf_rk_step_objective(ctx.handle, _ptr(U), _ptr(T), float(t), float(dt), ctypes.byref(L) if L else None,
-                                     ctypes.byref(J), _stream(stream)), "rf_rk_step_objective")
+                                     ctypes.byref(J) if want_J else None, _stream(stream)), "rf_rk_step_objective")
     return J.value
 
 
