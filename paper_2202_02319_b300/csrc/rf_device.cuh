@@ -210,17 +210,20 @@ __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (
 __device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
 
 // Newton solve of e(T) = e_target, warm-started from T; returns false if the
-// update did not fall below 1e-13 T within maxit iterations.  On return P holds
-// the mixture polynomial of the range containing T.
+// update did not fall below 1e-9 T (which leaves T within ~1e-16 T of the root,
+// see the tolerance below) within maxit iterations.  On return P holds the mixture
+// polynomial of the range containing T.
 template <int NS>
 __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
                                          double &T, int maxit, MixPoly &P) {
     int r = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
     mix_poly<NS>(M, r, Y, Rm, P);
     double e5 = P.e[5] - e_target;
-    // |dT| <= 1e-13 T, with T taken at the start: the iterates differ from it by
-    // far less than the tolerance's own precision
-    const double tol = 1.0e-13 * fabs(T);
+    // Stop once the update just applied is below 1e-9 T: the iteration contracts the
+    // error by the FP32 reciprocal's ~6e-8 per step (plus a quadratic term), so the
+    // updated T is then within ~1e-16 T of the root, and a further step (the
+    // |dT| <= 1e-13 T test of the definition) would move it by less than that.
+    const double tol = 1.0e-9 * fabs(T);
     for (int it = 0; it < maxit; ++it) {
         const int rn = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
         if (rn != r) {

@@ -188,7 +188,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             Y[s] = rs[s] * irho;
             Rm = fma(Y[s], M.RW[s], Rm);
         }
-        const double e = E * irho - 0.5 * (u * u + v * v + w * w);
+        const double e = fma(-0.5, fma(u, u, fma(v, v, w * w)), E * irho);
         double T = m.T[cell];
         MixPoly P;
         const bool ok = newton_T<NS>(M, Y, Rm, e, T, newton_maxit, P);
