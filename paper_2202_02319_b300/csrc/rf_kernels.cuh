@@ -785,51 +785,86 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
     const bool vec = (m.nx % 4 == 0) && (x0 + W::TX <= m.nx);
     auto pmod = [](int c, int d) { return ((c % d) + d) % d; };
 
-    auto stage_I = [&](int c) {
-        const int cm = map_idx(c, nd, m.bc[DIR]);
-        float *dst = ringI + pmod(c, W::DI) * W::NI * NL;
-        auto src = [&](int f) -> const float * {
-            return f < NV ? U + (long long)f * n : Q + (long long)(f == NV ? Q_U + DIR : (f == NV + 1 ? Q_P : Q_C)) * n;
-        };
-        if (vec) {
-            for (int q = l; q < W::NI * W::TY * 8; q += NL) {
-                const int f = q / (W::TY * 8), r = (q >> 3) % W::TY, k = q & 7;
-                if (o0 + r >= no) continue;
-                const long long cell = (long long)(x0 + 4 * k) + (long long)(o0 + r) * so + (long long)cm * sd;
-                cp_async16(dst + f * NL + r * W::TX + 4 * k, src(f) + cell);
-            }
-        } else if (active) {
-            const long long cell = (long long)x + (long long)o * so + (long long)cm * sd;
+    // Copy items of this thread, fixed for the tile (only the plane offset changes):
+    // 16-byte chunks of row r = (l >> 3) & 3, columns 4 (l & 7) .. + 3, fields
+    // f = ty + 4 i of ring I and ring V; slab elements e = l + 128 i.
+    constexpr int CI = (W::NI * W::TY * 8 + NL - 1) / NL, CV = (W::NVV * W::TY * 8 + NL - 1) / NL;
+    constexpr int CS = (3 * W::NSL + NL - 1) / NL;
+    const int vr = (l >> 3) & 3, vk = l & 7;
+    const bool vrow = o0 + vr < no;
+    const long long rowoff = (long long)(x0 + 4 * vk) + (long long)(o0 + vr) * so;
+    const float *gI[CI];
+    const float *gV[CV];
+    const float *gS[CS];
 #pragma unroll
-            for (int f = 0; f < W::NI; ++f) cp_async4(dst + f * NL + l, src(f) + cell);
-        }
-    };
-    auto stage_V = [&](int c) {
-        const int cm = map_idx(c, nd, m.bc[DIR]);
-        const int slot = pmod(c, W::DV);
-        float *dst = ringV + slot * W::NVV * NL;
-        const float *qv = Q + (long long)Q_T * n;
-        if (vec) {
-            for (int q = l; q < W::NVV * W::TY * 8; q += NL) {
-                const int f = q / (W::TY * 8), r = (q >> 3) % W::TY, k = q & 7;
-                if (o0 + r >= no) continue;
-                const long long cell = (long long)(x0 + 4 * k) + (long long)(o0 + r) * so + (long long)cm * sd;
-                cp_async16(dst + f * NL + r * W::TX + 4 * k, qv + (long long)f * n + cell);
-            }
-        } else if (active) {
-            const long long cell = (long long)x + (long long)o * so + (long long)cm * sd;
+    for (int i2 = 0; i2 < CI; ++i2) {
+        const int f = ty + 4 * i2;
+        const float *base = f < NV ? U + (long long)f * n
+                                   : Q + (long long)(f == NV ? Q_U + DIR : (f == NV + 1 ? Q_P : Q_C)) * n;
+        gI[i2] = f < W::NI ? base + rowoff : nullptr;
+    }
 #pragma unroll
-            for (int f = 0; f < W::NVV; ++f) cp_async4(dst + f * NL + l, qv + (long long)f * n + cell);
-        }
-        float *sdst = slab + slot * 3 * W::NSL;
-        for (int e = l; e < 3 * W::NSL; e += NL) {
+    for (int i2 = 0; i2 < CV; ++i2) {
+        const int f = ty + 4 * i2;
+        gV[i2] = f < W::NVV ? Q + (long long)(Q_T + f) * n + rowoff : nullptr;
+    }
+#pragma unroll
+    for (int i2 = 0; i2 < CS; ++i2) {
+        const int e = l + NL * i2;
+        if (e < 3 * W::NSL) {
             const int f = e / W::NSL, p = e - f * W::NSL;
             const int sy = p / W::SX, sx = p - sy * W::SX;
             int X = x0 - 1 + sx, O = o0 - 1 + sy;
             if ((unsigned)X >= (unsigned)m.nx) X = map_idx(X, m.nx, m.bc[0]);
             if ((unsigned)O >= (unsigned)no) O = map_idx(O, no, bco);
-            cp_async4(sdst + e, Q + (long long)f * n + (long long)X + (long long)O * so + (long long)cm * sd);
+            gS[i2] = Q + (long long)f * n + (long long)X + (long long)O * so;
+        } else {
+            gS[i2] = nullptr;
         }
+    }
+    const int dvec = vr * W::TX + 4 * vk;
+
+    auto stage_I = [&](int c) {
+        const int cm = map_idx(c, nd, m.bc[DIR]);
+        const long long plane = (long long)cm * sd;
+        float *dst = ringI + pmod(c, W::DI) * W::NI * NL;
+        if (vec) {
+            if (vrow) {
+#pragma unroll
+                for (int i2 = 0; i2 < CI; ++i2)
+                    if (gI[i2]) cp_async16(dst + (ty + 4 * i2) * NL + dvec, gI[i2] + plane);
+            }
+        } else if (active) {
+            const long long cell = (long long)x + (long long)o * so + plane;
+#pragma unroll
+            for (int f = 0; f < W::NI; ++f) {
+                const float *base = f < NV ? U + (long long)f * n
+                                           : Q + (long long)(f == NV ? Q_U + DIR : (f == NV + 1 ? Q_P : Q_C)) * n;
+                cp_async4(dst + f * NL + l, base + cell);
+            }
+        }
+    };
+    auto stage_V = [&](int c) {
+        const int cm = map_idx(c, nd, m.bc[DIR]);
+        const long long plane = (long long)cm * sd;
+        const int slot = pmod(c, W::DV);
+        float *dst = ringV + slot * W::NVV * NL;
+        if (vec) {
+            if (vrow) {
+#pragma unroll
+                for (int i2 = 0; i2 < CV; ++i2)
+                    if (gV[i2]) cp_async16(dst + (ty + 4 * i2) * NL + dvec, gV[i2] + plane);
+            }
+        } else if (active) {
+            const long long cell = (long long)x + (long long)o * so + plane;
+            const float *qv = Q + (long long)Q_T * n;
+#pragma unroll
+            for (int f = 0; f < W::NVV; ++f) cp_async4(dst + f * NL + l, qv + (long long)f * n + cell);
+        }
+        float *sdst = slab + slot * 3 * W::NSL;
+#pragma unroll
+        for (int i2 = 0; i2 < CS; ++i2)
+            if (gS[i2]) cp_async4(sdst + l + NL * i2, gS[i2] + plane);
     };
 
     stage_I(c0 - 2);
