@@ -1028,18 +1028,23 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     const float **tab = (const float **)(stash + 16) ;
     for (int fr = lane; fr < X::NFR; fr += 32) tab[fr] = src_of(fr);
     __syncwarp();
+    // lanes 0..29 copy the window's 4-cell column chunk lane % 10 of field-rows
+    // lane / 10, + 3, + 6, ...: the range test and any wrap are per lane, not per item
+    const int sq4 = lane % (WIN / 4), sfr0 = lane / (WIN / 4);
     auto stage = [&](int c, float *dst) {
-        const int A = 32 * c - 4;
-        for (int e = lane; e < X::NFR * (WIN / 4); e += 32) {
-            const int fr = e / (WIN / 4), q4 = e - fr * (WIN / 4);
-            const int x4 = A + 4 * q4;
-            const float *sp = tab[fr];
-            float *dp = dst + fr * WIN + 4 * q4;
-            if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
-                cp_async16(dp, sp + x4);
-            } else {
+        if (lane >= 3 * (WIN / 4)) return;
+        const int x4 = 32 * c - 4 + 4 * sq4;
+        float *dp = dst + sfr0 * WIN + 4 * sq4;
+        if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
+            for (int fr = sfr0; fr < X::NFR; fr += 3, dp += 3 * WIN) cp_async16(dp, tab[fr] + x4);
+        } else {
+            int xi[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) cp_async4(dp + i, sp + map_idx(x4 + i, nx, m.bc[0]));
+            for (int i = 0; i < 4; ++i) xi[i] = map_idx(x4 + i, nx, m.bc[0]);
+            for (int fr = sfr0; fr < X::NFR; fr += 3, dp += 3 * WIN) {
+                const float *sp = tab[fr];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cp_async4(dp + i, sp + xi[i]);
             }
         }
     };
