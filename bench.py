@@ -259,18 +259,25 @@ def run_ours(args):
     tot = {k: v[0] for k, v in prof.items()}
     dom = max(("cell_state", "sweep_x", "sweep_y", "sweep_z"), key=lambda k: tot[k])
     kernels = {}
-    for k in ("cell_state", "sweep_x", "sweep_y", "sweep_z"):
+    prof["stage_update"] = prof["other"]
+    tot["stage_update"] = tot["other"]
+    for k in ("cell_state", "sweep_x", "sweep_y", "sweep_z", "stage_update"):
         ms_k, nl = prof[k]
         if nl == 0:
             continue
         avg = ms_k / nl
         if k == "cell_state":
             b = cell_state_bytes(ns, 4)
+        elif k == "stage_update":
+            # RHS (FP32) and U^(k) read, U^(k+1) written; U^n read in stages 2 and 3
+            nv = ns + 4
+            b = round(((nv * 4 + 2 * nv * 8) + 2 * (nv * 4 + 3 * nv * 8)) / 3, 1)
         else:
-            # per step: two accumulate launches per axis other than z, final z launches
-            b = sweep_bytes(ns, 4, "stage" if k == "sweep_z" else "accum")
+            # the mixed path's sweeps all accumulate; an elementwise kernel applies the stage
+            b = sweep_bytes(ns, 4, "accum")
         gbs = b * ncell / (avg * 1e-3) / 1e9
-        kernels[k] = {"ms_per_launch": round(avg, 4), "launches": nl, "share": round(ms_k / sum(tot.values()), 4),
+        kernels[k] = {"ms_per_launch": round(avg, 4), "launches": nl,
+                      "share": round(ms_k / sum(v for kk, v in tot.items() if kk != "stage_update"), 4),
                       "alg_bytes_per_cell": b, "achieved_gbs": round(gbs, 1),
                       "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
     k64 = {}

@@ -541,10 +541,19 @@ struct Path {
             LAUNCH_CHECK();
             return RF_OK;
         }
+        // FP32-bulk RK stages: every sweep accumulates, then an elementwise FP64
+        // Shu-Osher update (the same values as fusing it into the last sweep, whose
+        // FP64 operations would otherwise hold the sweep's few warps per SM)
+        const bool split = sizeof(R) == 4 && MODE == MODE_STAGE;
         for (int d = 0; d < 3; ++d) {
             if (n[d] <= 1) continue;
-            int rc = d == last ? sweep<MODE>(c, m, d, s) : sweep<MODE_ACCUM>(c, m, d, s);
+            int rc = (d == last && !split) ? sweep<MODE>(c, m, d, s) : sweep<MODE_ACCUM>(c, m, d, s);
             if (rc) return rc;
+        }
+        if (split) {
+            ProfScope ps(c, PROF_OTHER, s);
+            pointwise_final_kernel<R, NS, MODE><<<(unsigned)((c->n + 255) / 256), 256, 0, s>>>(m);
+            LAUNCH_CHECK();
         }
         return RF_OK;
     }

@@ -1148,7 +1148,9 @@ __global__ void __launch_bounds__(128) sweep_walk_staged_kernel(int mslot, const
     sweep_walk_staged_block<NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg, (float *)smem_raw);
 }
 
-// Grids with no axis longer than one cell: the RHS is the source alone.
+// The source term plus the accumulated fluxes in the RHS buffer applied as the
+// stage's output (MODE_RHS / MODE_STAGE) with no flux of its own: grids with no axis
+// longer than one cell, and the stage update after sweeps that all accumulate.
 template <typename R, int NS, int MODE>
 __global__ void pointwise_final_kernel(const __grid_constant__ Member m) {
     const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
