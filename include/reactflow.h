@@ -273,6 +273,12 @@ int rf_probe_peak(int kind, double *tflops, rf_stream s);
  * RF_EINVAL for n < 0 or a null array with n > 0. */
 int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s);
 
+/* Self-test of the FP64 logarithm the cell-state kernel uses for ln T (Arrhenius
+ * rates and Gibbs energies, Methods, chemistry): y[i] = ln x[i] for normal x > 0
+ * (Tang's table-driven method).  x, y: device arrays of n doubles (caller-owned).
+ * Asynchronous on s; RF_EINVAL for n < 0 or a null array with n > 0. */
+int rf_probe_log(const double *x, double *y, long long n, rf_stream s);
+
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Computes the same dU/dt as rf_rhs for a
  * mechanism and grid without a context, for callers that cannot allocate device

@@ -78,6 +78,16 @@ static int upload_exp_table(int dev) {
         tab[64 + j] = (double)std::exp2l(-(long double)j / 64.0L);
     }
     CUDA_TRY(cudaMemcpyToSymbol(g_exp_tab, tab, sizeof(tab)));
+    // logarithm table: 1/F, ln F split into high and low parts, F = 1 + j/64
+    double ltab[65 * 3];
+    for (int j = 0; j <= 64; ++j) {
+        const long double F = 1.0L + (long double)j / 64.0L;
+        const long double lf = std::log(F);
+        ltab[3 * j] = (double)(1.0L / F);
+        ltab[3 * j + 1] = (double)lf;
+        ltab[3 * j + 2] = (double)(lf - (long double)ltab[3 * j + 1]);
+    }
+    CUDA_TRY(cudaMemcpyToSymbol(g_log_tab, ltab, sizeof(ltab)));
     g_exp_tab_done[dev] = true;
     return RF_OK;
 }
@@ -1451,6 +1461,26 @@ extern "C" int rf_probe_peak(int kind, double *tflops, rf_stream s) {
 __global__ void exp_pair_probe_kernel(const double *x, double *ep, double *em, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) exp_pair(x[i], ep[i], em[i]);
+}
+
+__global__ void log_probe_kernel(const double *x, double *y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = log64(x[i]);
+}
+
+extern "C" int rf_probe_log(const double *x, double *y, long long n, rf_stream s) {
+    if (n < 0 || (n > 0 && (!x || !y))) return fail(RF_EINVAL, "rf_probe_log: bad argument");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
+    {
+        std::lock_guard<std::mutex> lock(g_slot_mutex);
+        if (int rc = upload_exp_table(dev)) return rc;
+    }
+    if (n == 0) return RF_OK;
+    log_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)s>>>(x, y, n);
+    LAUNCH_CHECK();
+    return RF_OK;
 }
 
 extern "C" int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s) {

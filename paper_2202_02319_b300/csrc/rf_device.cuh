@@ -174,6 +174,37 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     em = sm * (E - O);
 }
 
+// ----------------------------------------------------------------------------- logarithm
+
+// ln x in FP64 for normal x > 0, after Tang's table-driven logarithm (P. T. P. Tang,
+// ACM TOMS 16 (1990) 378-400): x = 2^m y with y in [1, 2), F = 1 + j/64 the nearest
+// table point (from the leading mantissa bits, exact), f = y - F (exact),
+// r = f / F (|r| <= 1/128) and
+//   ln x = m ln2 + ln F + ln(1 + r),  ln(1 + r) = r - r^2/2 + ... - r^6/6
+// (first omitted term r^7/7 < 4e-17).  ln 2 and ln F are carried as high and low
+// parts; 1/F and ln F are tabulated from extended precision.
+constexpr double LN2_HI = 0.6931471805599453094;           // double(ln 2)
+constexpr double LN2_LO = 2.3190468138462996e-17;          // ln 2 - double(ln 2)
+__device__ double g_log_tab[65 * 3];                        // per j = 0..64: 1/F, ln F (high), ln F (low)
+
+__device__ __forceinline__ double log64(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int m = ((hi >> 20) & 0x7ff) - 1023;
+    const int mant = hi & 0xfffff;
+    const int j = (mant + (1 << 13)) >> 14;                 // nearest of 64 points (0..64)
+    const double y = __hiloint2double(0x3ff00000 | mant, lo);
+    const double F = __hiloint2double(0x3ff00000 + (j << 14), 0);   // 1 + j/64 (j = 64: 2)
+    const double f = y - F;
+    const double r = f * __ldg(&g_log_tab[3 * j]);
+    const double r2 = r * r;
+    const double q = fma(r, fma(r, fma(r, fma(r, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
+    const double p = fma(r2, q, r);
+    const double md = (double)m;
+    const double head = fma(md, LN2_HI, __ldg(&g_log_tab[3 * j + 1]));
+    const double tail = fma(md, LN2_LO, __ldg(&g_log_tab[3 * j + 2])) + p;
+    return head + tail;
+}
+
 // ----------------------------------------------------------------------------- thermo
 
 // Mixture polynomial of the specific internal energy for one NASA range:

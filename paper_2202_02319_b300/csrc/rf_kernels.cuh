@@ -202,7 +202,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 
         const int rng = nasa_range(M, T);
         const double invT = rcp64(T);
-        const double lnT = log(T);
+        const double lnT = log64(T);
         const double cv = mix_cv(P, T);
         const double cp = cv + Rm;
         double p;

@@ -64,6 +64,7 @@ _sigs = {
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
     "rf_probe_exp_pair": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, _vp]),
+    "rf_probe_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _vp]),
     "rf_adjoint_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Laser), _vp, ctypes.c_double, _vp,
                                       _vp, _vp]),
     "rf_rk_step_objective": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _dp,
@@ -219,6 +220,11 @@ def probe_peak(kind: int, stream=None) -> float:
 def probe_exp_pair(x, ep, em, stream=None):
     """ep = exp(x), em = exp(-x) by the kernels' FP64 exponential pair (device tensors)."""
     _check(_lib.rf_probe_exp_pair(_ptr(x), _ptr(ep), _ptr(em), int(x.numel()), _stream(stream)), "rf_probe_exp_pair")
+
+
+def probe_log(x, y, stream=None):
+    """y = ln x by the kernels' FP64 logarithm (device tensors)."""
+    _check(_lib.rf_probe_log(_ptr(x), _ptr(y), int(x.numel()), _stream(stream)), "rf_probe_log")
 
 
 PROF_CLASSES = ("cell_state", "sweep_x", "sweep_y", "sweep_z", "other")

@@ -42,3 +42,20 @@ def test_exp_pair_saturates_beyond_707_and_handles_empty():
     assert ep[0] >= big and em[1] >= big and ep[2] >= big and em[3] >= big
     assert em[0] <= 1.0 / big and ep[1] <= 1.0 / big
     _pair(np.zeros(0))
+
+
+def test_log64_within_a_few_ulp():
+    from paper_2202_02319_b300 import native as nv
+    g = np.random.default_rng(12)
+    x = np.concatenate([g.uniform(50.0, 1.0e5, 400_000), np.exp(g.uniform(-700.0, 700.0, 200_000)),
+                        g.uniform(0.99, 1.01, 100_000), [1.0, 2.0, 0.5, 1.0 + 1.0 / 128.0, 1.0 - 1e-16, 1e-300, 1e300]])
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    y = torch.empty_like(xd)
+    nv.probe_log(xd, y)
+    torch.cuda.synchronize()
+    got = y.cpu().numpy()
+    ref = np.log(x)
+    # absolute error against |ln x| + 1: a few ulp of the result, and of 1 near x = 1
+    assert float(np.max(np.abs(got - ref) / (np.abs(ref) + 1.0))) < 1e-15
+    assert float(((y - torch.log(xd)).abs() / (torch.log(xd).abs() + 1.0)).max()) < 1e-15
+    assert got[x == 1.0][0] == 0.0
