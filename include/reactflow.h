@@ -265,19 +265,16 @@ int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_
  * Synchronous.  The FP64 figure is the ALU roofline of the cell-state kernel. */
 int rf_probe_peak(int kind, double *tflops, rf_stream s);
 
-/* Self-test of the FP64 exponential pair the cell-state kernel uses for the
- * Gibbs factors G_s = exp(g_s/RT) RT/p_atm and 1/G_s (equilibrium constants,
- * Methods, chemistry): ep[i] = exp(x[i]) and em[i] = exp(-x[i]) from one
- * argument reduction (Tang's table-driven method), |x| clamped to 707.
- * x, ep, em: device arrays of n doubles (caller-owned).  Asynchronous on s;
- * RF_EINVAL for n < 0 or a null array with n > 0. */
-int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s);
-
-/* Self-test of the FP64 logarithm the cell-state kernel uses for ln T (Arrhenius
- * rates and Gibbs energies, Methods, chemistry): y[i] = ln x[i] for normal x > 0
- * (Tang's table-driven method).  x, y: device arrays of n doubles (caller-owned).
- * Asynchronous on s; RF_EINVAL for n < 0 or a null array with n > 0. */
-int rf_probe_log(const double *x, double *y, long long n, rf_stream s);
+/* Self-test of the FP64 elementary functions of the kernels (table-driven, after
+ * Tang's methods): fn 0, the exponential pair of the Gibbs factors G_s =
+ * exp(g_s/RT) RT/p_atm and 1/G_s (equilibrium constants, Methods, chemistry):
+ * y[i] = exp(x[i]), y2[i] = exp(-x[i]) from one argument reduction; fn 1: y[i] =
+ * ln x[i] for normal x > 0 (ln T of the rates and Gibbs energies); fn 2: y[i] =
+ * exp(x[i]) (FP64 Arrhenius rates and transport powers).  Exponentials saturate at
+ * 2^(+-1020) beyond |x| ~ 707.  x, y, y2 (fn 0 only; may be NULL otherwise): device
+ * arrays of n doubles (caller-owned).  Asynchronous on s; RF_EINVAL for an unknown
+ * fn, n < 0 or a missing array with n > 0. */
+int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s);
 
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Computes the same dU/dt as rf_rhs for a

@@ -1463,13 +1463,17 @@ __global__ void exp_pair_probe_kernel(const double *x, double *ep, double *em, l
     if (i < n) exp_pair(x[i], ep[i], em[i]);
 }
 
-__global__ void log_probe_kernel(const double *x, double *y, long long n) {
+__global__ void math_probe_kernel(int fn, const double *x, double *y, double *y2, long long n) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = log64(x[i]);
+    if (i >= n) return;
+    if (fn == 0) exp_pair(x[i], y[i], y2[i]);
+    else if (fn == 1) y[i] = log64(x[i]);
+    else y[i] = exp64(x[i]);
 }
 
-extern "C" int rf_probe_log(const double *x, double *y, long long n, rf_stream s) {
-    if (n < 0 || (n > 0 && (!x || !y))) return fail(RF_EINVAL, "rf_probe_log: bad argument");
+extern "C" int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s) {
+    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y || (fn == 0 && !y2))))
+        return fail(RF_EINVAL, "rf_probe_math: bad argument");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
@@ -1478,23 +1482,7 @@ extern "C" int rf_probe_log(const double *x, double *y, long long n, rf_stream s
         if (int rc = upload_exp_table(dev)) return rc;
     }
     if (n == 0) return RF_OK;
-    log_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)s>>>(x, y, n);
-    LAUNCH_CHECK();
-    return RF_OK;
-}
-
-extern "C" int rf_probe_exp_pair(const double *x, double *ep, double *em, long long n, rf_stream s) {
-    if (n < 0 || (n > 0 && (!x || !ep || !em))) return fail(RF_EINVAL, "rf_probe_exp_pair: bad argument");
-    int dev = 0;
-    CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= RF_MAX_DEVICES) return fail(RF_EINVAL, "device %d out of range", dev);
-    {
-        std::lock_guard<std::mutex> lock(g_slot_mutex);
-        if (int rc = upload_exp_table(dev)) return rc;
-    }
-    if (n == 0) return RF_OK;
-    const int threads = 256;
-    exp_pair_probe_kernel<<<(unsigned)((n + threads - 1) / threads), threads, 0, (cudaStream_t)s>>>(x, ep, em, n);
+    math_probe_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)s>>>(fn, x, y, y2, n);
     LAUNCH_CHECK();
     return RF_OK;
 }

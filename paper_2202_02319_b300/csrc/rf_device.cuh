@@ -89,7 +89,6 @@ template <int NS> struct QL {
     static constexpr int X = Q_X0, DC = Q_X0 + NS, H = Q_X0 + 2 * NS, NQ = Q_X0 + 3 * NS;
 };
 
-__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
 
 // 1/x in FP64 by Newton-Raphson iteration r <- r + r (1 - x r) from an FP32 seed:
 // two steps take the seed's ~2^-23 relative error to rounding level.  For x whose
@@ -104,9 +103,7 @@ __device__ __forceinline__ double rcp64(double x) {
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
 __device__ __forceinline__ float exp_(float x) { return expf(x); }
-__device__ __forceinline__ double log_(double x) { return log(x); }
 __device__ __forceinline__ float log_(float x) { return logf(x); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
 __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
@@ -174,6 +171,21 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     em = sm * (E - O);
 }
 
+// exp(x) alone from the same reduction and table: exp(r) by its Taylor polynomial
+// through r^5 (first omitted term r^6/720 < 4e-17 relative), one table factor.
+__device__ __forceinline__ double exp64(double x) {
+    const double shifter = 6755399441055744.0;
+    const double t = fma(x, 92.33248261689366 /* 64 / ln 2 */, shifter);
+    const int k = __double2loint(t);
+    const double kd = t - shifter;
+    double r = fma(-kd, LN2_64_HI, x);
+    r = fma(-kd, LN2_64_LO, r);
+    const double p = fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0), 1.0);
+    const int j = k & 63, m = min(max(k >> 6, -1020), 1020);
+    const double tp = __ldg(&g_exp_tab[j]);
+    return __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp)) * p;
+}
+
 // ----------------------------------------------------------------------------- logarithm
 
 // ln x in FP64 for normal x > 0, after Tang's table-driven logarithm (P. T. P. Tang,
@@ -204,6 +216,14 @@ __device__ __forceinline__ double log64(double x) {
     const double tail = fma(md, LN2_LO, __ldg(&g_log_tab[3 * j + 2])) + p;
     return head + tail;
 }
+
+// FP64 instances of the bulk-type helpers (transport and chemistry of the FP64
+// path): table-driven exponential and logarithm, Newton-Raphson reciprocal (the
+// arguments -- viscosities, mixture sums, pressures, molar masses -- lie in the FP32
+// normal range).
+__device__ __forceinline__ double rcp(double x) { return rcp64(x); }
+__device__ __forceinline__ double exp_(double x) { return exp64(x); }
+__device__ __forceinline__ double log_(double x) { return log64(x); }
 
 // ----------------------------------------------------------------------------- thermo
 

@@ -51,7 +51,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
     const R lnTb = (R)lnT, invTb = (R)invT;
     for (int j = 0; j < M.nr; ++j) {
         R kf;
-        if (sizeof(R) == 8) kf = (R)exp(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
+        if (sizeof(R) == 8) kf = (R)exp64(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
         else kf = (R)expf(M.lnAf[j] + M.bf[j] * (float)lnTb - M.Thetaf[j] * (float)invTb);
         const int nrc = M.n_reac[j], npd = M.n_prod[j];
         R cf = kf;
@@ -269,7 +269,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                 const double dz = fma((double)k, m.h[2], fma(0.5, m.h[2], -m.las[3]));
                 r2 = fma(dz, dz, r2);
             }
-            if (sizeof(R) == 8) qL = s_laser[0] * exp(s_laser[1] * r2);
+            if (sizeof(R) == 8) qL = s_laser[0] * exp64(s_laser[1] * r2);
             else qL = s_laser[0] * (double)expf((float)(s_laser[1] * r2));
         }
         rhs[(NS + 3) * n + cell] = (R)qL;

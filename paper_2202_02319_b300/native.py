@@ -63,8 +63,7 @@ _sigs = {
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
-    "rf_probe_exp_pair": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_longlong, _vp]),
-    "rf_probe_log": (ctypes.c_int, [_vp, _vp, ctypes.c_longlong, _vp]),
+    "rf_probe_math": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong, _vp]),
     "rf_adjoint_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Laser), _vp, ctypes.c_double, _vp,
                                       _vp, _vp]),
     "rf_rk_step_objective": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _dp,
@@ -219,12 +218,17 @@ def probe_peak(kind: int, stream=None) -> float:
 
 def probe_exp_pair(x, ep, em, stream=None):
     """ep = exp(x), em = exp(-x) by the kernels' FP64 exponential pair (device tensors)."""
-    _check(_lib.rf_probe_exp_pair(_ptr(x), _ptr(ep), _ptr(em), int(x.numel()), _stream(stream)), "rf_probe_exp_pair")
+    _check(_lib.rf_probe_math(0, _ptr(x), _ptr(ep), _ptr(em), int(x.numel()), _stream(stream)), "rf_probe_math")
 
 
 def probe_log(x, y, stream=None):
     """y = ln x by the kernels' FP64 logarithm (device tensors)."""
-    _check(_lib.rf_probe_log(_ptr(x), _ptr(y), int(x.numel()), _stream(stream)), "rf_probe_log")
+    _check(_lib.rf_probe_math(1, _ptr(x), _ptr(y), None, int(x.numel()), _stream(stream)), "rf_probe_math")
+
+
+def probe_exp(x, y, stream=None):
+    """y = exp(x) by the kernels' single FP64 exponential (device tensors)."""
+    _check(_lib.rf_probe_math(2, _ptr(x), _ptr(y), None, int(x.numel()), _stream(stream)), "rf_probe_math")
 
 
 PROF_CLASSES = ("cell_state", "sweep_x", "sweep_y", "sweep_z", "other")

@@ -1,5 +1,6 @@
-"""The FP64 exponential pair of the cell-state kernel (G_s and 1/G_s of the
-equilibrium constants) against CUDA's exp (through torch) and numpy's exp."""
+"""The FP64 elementary functions of the kernels (the exponential pair of G_s and
+1/G_s, the single exponential, the logarithm) against CUDA's functions (through
+torch) and numpy's."""
 import numpy as np
 import pytest
 import torch
@@ -59,3 +60,16 @@ def test_log64_within_a_few_ulp():
     assert float(np.max(np.abs(got - ref) / (np.abs(ref) + 1.0))) < 1e-15
     assert float(((y - torch.log(xd)).abs() / (torch.log(xd).abs() + 1.0)).max()) < 1e-15
     assert got[x == 1.0][0] == 0.0
+
+
+def test_single_exp64_within_a_few_ulp():
+    from paper_2202_02319_b300 import native as nv
+    g = np.random.default_rng(13)
+    x = np.concatenate([g.uniform(-700.0, 700.0, 400_000), g.uniform(-1.0, 1.0, 200_000),
+                        np.arange(-200, 201) * np.log(2.0) / 128.0, [0.0, -0.0, 706.9, -706.9]])
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    y = torch.empty_like(xd)
+    nv.probe_exp(xd, y)
+    torch.cuda.synchronize()
+    assert float(np.max(np.abs(y.cpu().numpy() - np.exp(x)) / np.exp(x))) < 1e-15
+    assert float(((y - torch.exp(xd)).abs() / torch.exp(xd)).max()) < 1e-15
