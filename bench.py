@@ -118,7 +118,7 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
 # captured for the current kernel.
 CELL_STATE_MIXED_FP64_INST = (252.7, 142.3, 46.2)        # DFMA, DMUL, DADD per cell
 CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 2 * CELL_STATE_MIXED_FP64_INST[0] + sum(CELL_STATE_MIXED_FP64_INST[1:])
-CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 308.8              # (100.55 + 172.67) MB / 884,736 cells
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 309.2              # (100.49 + 173.03) MB / 884,736 cells
 
 
 def cell_state_bytes(ns: int, rsize: int) -> int:
