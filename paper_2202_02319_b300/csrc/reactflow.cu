@@ -68,14 +68,15 @@ static const rf_mech *g_slot_owner[RF_MAX_DEVICES][MECH_SLOTS];
 
 static bool g_exp_tab_done[RF_MAX_DEVICES];
 
-// Table of the FP64 exponential pair (2^(j/64) and 2^(-j/64), j = 0..63, rounded
-// from extended precision) on device dev; the caller holds g_slot_mutex.
+// Tables of the FP64 exponential (2^(j/256) and 2^(-j/256), j = 0..255) and
+// logarithm, rounded from extended precision, on device dev; the caller holds
+// g_slot_mutex.
 static int upload_exp_table(int dev) {
     if (g_exp_tab_done[dev]) return RF_OK;
-    double tab[128];
-    for (int j = 0; j < 64; ++j) {
-        tab[j] = (double)std::exp2l((long double)j / 64.0L);
-        tab[64 + j] = (double)std::exp2l(-(long double)j / 64.0L);
+    double tab[512];
+    for (int j = 0; j < 256; ++j) {
+        tab[j] = (double)std::exp2l((long double)j / 256.0L);
+        tab[256 + j] = (double)std::exp2l(-(long double)j / 256.0L);
     }
     CUDA_TRY(cudaMemcpyToSymbol(g_exp_tab, tab, sizeof(tab)));
     // logarithm table: 1/F, ln F split into high and low parts, F = 1 + j/64

@@ -140,31 +140,31 @@ template <> __device__ __forceinline__ float mech_cpc<float>(const MechDev &M, i
 
 // exp(x) and exp(-x) in FP64 from one argument reduction, after Tang's
 // table-driven exponential (P. T. P. Tang, ACM TOMS 15 (1989) 144-157):
-// x = k ln2/64 + r with k = 64 m + j, 0 <= j < 64, |r| <= ln2/128, and
-//   exp(+-x) = 2^(+-m) 2^(+-j/64) (E(r) +- O(r)),
-// E = 1 + r^2/2 + r^4/24 and O = r + r^3/6 + r^5/120 the even and odd parts of the
-// Taylor series of exp(r) (first omitted terms r^6/720 < 4e-17 and r^7/7! < 3e-20
-// relative).  ln2/64 is split into its double value and the remainder so that r
-// keeps full precision for every k; 2^(+-m) is added to the exponent fields of
-// the correctly rounded table entries.  A few ulp from exp itself for |x| <= 707;
-// beyond that (up to |x| ~ 2e7) the power of two is clamped to 2^(+-1020) and the
+// x = k ln2/256 + r with k = 256 m + j, 0 <= j < 256, |r| <= ln2/512, and
+//   exp(+-x) = 2^(+-m) 2^(+-j/256) (E(r) +- O(r)),
+// E = 1 + r^2/2 + r^4/24 and O = r + r^3/6 the even and odd parts of the Taylor
+// series of exp(r) (first omitted terms r^6/720 < 1e-20 and r^5/120 < 4e-17
+// relative).  ln2/256 is split into its double value and the remainder so that r
+// keeps full precision for every k; 2^(+-m) is added to the exponent fields of the
+// correctly rounded table entries.  A few ulp from exp itself for |x| <= 707;
+// beyond that (up to |x| ~ 5e6) the power of two is clamped to 2^(+-1020) and the
 // results saturate.
-constexpr double LN2_64_HI = 0.6931471805599453094 / 64.0;   // double(ln 2) / 64, exact
-constexpr double LN2_64_LO = 2.3190468138462996e-17 / 64.0;  // (ln 2 - double(ln 2)) / 64
-__device__ double g_exp_tab[128];                            // 2^(j/64), then 2^(-j/64), j = 0..63
+constexpr double LN2_256_HI = 0.6931471805599453094 / 256.0;   // double(ln 2) / 256, exact
+constexpr double LN2_256_LO = 2.3190468138462996e-17 / 256.0;  // (ln 2 - double(ln 2)) / 256
+__device__ double g_exp_tab[512];                              // 2^(j/256), then 2^(-j/256), j = 0..255
 
 __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     const double shifter = 6755399441055744.0;               // 1.5 * 2^52: rounds to an integer in the low bits
-    const double t = fma(x, 92.33248261689366 /* 64 / ln 2 */, shifter);
+    const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
     const int k = __double2loint(t);
     const double kd = t - shifter;
-    double r = fma(-kd, LN2_64_HI, x);
-    r = fma(-kd, LN2_64_LO, r);
+    double r = fma(-kd, LN2_256_HI, x);
+    r = fma(-kd, LN2_256_LO, r);
     const double r2 = r * r;
     const double E = fma(r2, fma(r2, 1.0 / 24.0, 0.5), 1.0);
-    const double O = fma(r * r2, fma(r2, 1.0 / 120.0, 1.0 / 6.0), r);
-    const int j = k & 63, m = min(max(k >> 6, -1020), 1020);
-    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[64 + j]);
+    const double O = fma(r * r2, 1.0 / 6.0, r);
+    const int j = k & 255, m = min(max(k >> 8, -1020), 1020);
+    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[256 + j]);
     const double sp = __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp));
     const double sm = __hiloint2double(__double2hiint(tm) - (m << 20), __double2loint(tm));
     ep = sp * (E + O);
@@ -172,16 +172,16 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
 }
 
 // exp(x) alone from the same reduction and table: exp(r) by its Taylor polynomial
-// through r^5 (first omitted term r^6/720 < 4e-17 relative), one table factor.
+// through r^4 (first omitted term r^5/120 < 4e-17 relative), one table factor.
 __device__ __forceinline__ double exp64(double x) {
     const double shifter = 6755399441055744.0;
-    const double t = fma(x, 92.33248261689366 /* 64 / ln 2 */, shifter);
+    const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
     const int k = __double2loint(t);
     const double kd = t - shifter;
-    double r = fma(-kd, LN2_64_HI, x);
-    r = fma(-kd, LN2_64_LO, r);
-    const double p = fma(r, fma(r, fma(r, fma(r, fma(r, 1.0 / 120.0, 1.0 / 24.0), 1.0 / 6.0), 0.5), 1.0), 1.0);
-    const int j = k & 63, m = min(max(k >> 6, -1020), 1020);
+    double r = fma(-kd, LN2_256_HI, x);
+    r = fma(-kd, LN2_256_LO, r);
+    const double p = fma(r, fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0), 1.0);
+    const int j = k & 255, m = min(max(k >> 8, -1020), 1020);
     const double tp = __ldg(&g_exp_tab[j]);
     return __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp)) * p;
 }
