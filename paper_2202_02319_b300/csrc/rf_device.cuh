@@ -29,7 +29,7 @@ struct MechDev {
     double W[NSMAX], invW[NSMAX], RW[NSMAX];   // R/W_s
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
     double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
-    double sc[2][NSMAX][6];                    // a1 (x lnT), a2, a3/2, a4/3, a5/4, a7
+    double ecR[2][NSMAX][6];                   // ec times R/W_s (mixture energy polynomial of the Newton solve)
     double gc[2][NSMAX][7];                    // ln G = g/RT + ln(RT/p_atm) = gc0 + T(gc1 + ... T gc4) + gc5/T + gc6 lnT
     float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
@@ -239,9 +239,8 @@ __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (
     double c[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const double yr = Y[s] * M.RW[s];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) c[k] = fma(yr, M.ec[r][s][k], c[k]);
+        for (int k = 0; k < 6; ++k) c[k] = fma(Y[s], M.ecR[r][s][k], c[k]);
     }
     // sum_s Y_s (R/W_s) [a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6] - Rm T
     P.e[0] = c[0] - Rm;
@@ -308,12 +307,6 @@ __device__ __forceinline__ int nasa_range(const MechDev &M, double T) { return (
 __device__ __forceinline__ double h_RT(const MechDev &M, int r, int s, double T, double invT) {
     const double *c = M.ec[r][s];
     return fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[0]) + c[5] * invT;
-}
-
-// s_s/R of species s.
-__device__ __forceinline__ double s_R(const MechDev &M, int r, int s, double T, double lnT) {
-    const double *c = M.sc[r][s];
-    return fma(c[0], lnT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[5]));
 }
 
 // ln G_s = g_s/RT + ln(R T / p_atm), g_s/RT = h_s/RT - s_s/R, of species s in one Horner pass.

@@ -195,4 +195,5 @@ def test_diagnostics_parity():
     w = oracle.chemistry.production_rates(mt, st["rho_s"], st["T"])
     hrr = float(oracle.chemistry.heat_release_rate(mt, w, st["T"]).sum()) * dV
     assert abs(d["heat_release"] - hrr) <= 1e-12 * abs(hrr)
-    assert d["max_T"] == float(st["T"].max())
+    # the maximum is exact, the temperatures themselves are Newton results (rounding level)
+    assert abs(d["max_T"] - float(st["T"].max())) <= 1e-13 * float(st["T"].max())
