@@ -259,7 +259,10 @@ __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (
 
 __device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
 
-// Newton solve of e(T) = e_target, warm-started from T; returns false if the
+// Newton solve of e(T) = e_target, warm-started from T, with e(T) = sum_s Y_s e_s(T)
+// and Rm = sum_s Y_s R/W_s; the weights may be mass fractions (energy per unit mass)
+// or partial densities (energy per unit volume, e_target = rho e: the same root, and
+// the polynomial P is then density-weighted).  Returns false if the
 // update did not fall below 1e-9 T (which leaves T within ~1e-16 T of the root,
 // see the tolerance below) within maxit iterations.  On return P holds the mixture
 // polynomial of the range containing T.

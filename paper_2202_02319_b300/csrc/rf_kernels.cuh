@@ -181,29 +181,43 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const double mx = U[(NS + 0) * n + cell], my = U[(NS + 1) * n + cell], mz = U[(NS + 2) * n + cell];
         const double E = U[(NS + 3) * n + cell];
         const double irho = rcp64(rho);
-        const double u = mx * irho, v = my * irho, w = mz * irho;
-        double Rm = 0.0;
+        // Newton on the density-weighted energy rho e(T) = sum_s rho_s e_s(T) = E - |rho u|^2 / (2 rho):
+        // the same root as e(T) = e without forming the mass fractions in FP64
+        double rhoRm = 0.0;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            Y[s] = rs[s] * irho;
-            Rm = fma(Y[s], M.RW[s], Rm);
-        }
-        const double e = fma(-0.5, fma(u, u, fma(v, v, w * w)), E * irho);
+        for (int s = 0; s < NS; ++s) rhoRm = fma(rs[s], M.RW[s], rhoRm);
+        const double Rm = rhoRm * irho;
+        const double rho_e = fma(-0.5 * irho, fma(mx, mx, fma(my, my, mz * mz)), E);
         double T = m.T[cell];
         MixPoly P;
-        const bool ok = newton_T<NS>(M, Y, Rm, e, T, newton_maxit, P);
+        const bool ok = newton_T<NS>(M, rs, rhoRm, rho_e, T, newton_maxit, P);
         if (!ok) flag_error(m, ST_NEWTON, cell);
         if (!(rho > 0.0) || !(T > 0.0) || !(T < T_MAX_ADMISSIBLE)) {
             if (isfinite(rho) && isfinite(T)) flag_error(m, ST_RANGE, cell);
             else flag_error(m, ST_NONFINITE, cell);
         }
-        if (!isfinite(E) || !isfinite(u) || !isfinite(v) || !isfinite(w)) flag_error(m, ST_NONFINITE, cell);
+        if (!isfinite(E) || !isfinite(mx) || !isfinite(my) || !isfinite(mz)) flag_error(m, ST_NONFINITE, cell);
+        const R irhob = (R)irho;
+        R ub, vb, wb;
+        if constexpr (sizeof(R) == 4) {
+            ub = (R)mx * irhob;
+            vb = (R)my * irhob;
+            wb = (R)mz * irhob;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) Y[s] = 0.0;
+        } else {
+            ub = mx * irho;
+            vb = my * irho;
+            wb = mz * irho;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) Y[s] = rs[s] * irho;
+        }
         m.T[cell] = T;
 
         const int rng = nasa_range(M, T);
         const double invT = rcp64(T);
         const double lnT = log64(T);
-        const double cv = mix_cv(P, T);
+        const double cv = mix_cv(P, T) * irho;           // P is density-weighted
         const double cp = cv + Rm;
         double p;
         R c;
@@ -219,9 +233,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const double irm = rcp64(Rm);
         const double Wbar = RU * irm;
         R *Q = (R *)m.Q;
-        Q[Q_U * n + cell] = (R)u;
-        Q[Q_V * n + cell] = (R)v;
-        Q[Q_W * n + cell] = (R)w;
+        Q[Q_U * n + cell] = ub;
+        Q[Q_V * n + cell] = vb;
+        Q[Q_W * n + cell] = wb;
         Q[Q_P * n + cell] = (R)p;
         Q[Q_C * n + cell] = (R)c;
         Q[Q_T * n + cell] = (R)T;
@@ -229,7 +243,8 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const R Tb = (R)T, invTb = (R)invT, irmb = (R)irm;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            X[s] = (R)Y[s] * (mech_RW<R>(M, s) * irmb);
+            const R Ys = sizeof(R) == 4 ? (R)rs[s] * irhob : (R)Y[s];
+            X[s] = Ys * (mech_RW<R>(M, s) * irmb);
             Q[(QL<NS>::X + s) * n + cell] = X[s];
             Q[(QL<NS>::H + s) * n + cell] = h_RT_bulk(M, rng, s, Tb, invTb) * mech_RW<R>(M, s) * Tb;
         }
@@ -279,9 +294,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         }
         if (m.want_rates) {
             R ac = 0;
-            if (m.nx > 1) ac += (fabs((R)u) + c) * (R)m.invh[0];
-            if (m.ny > 1) ac += (fabs((R)v) + c) * (R)m.invh[1];
-            if (m.nz > 1) ac += (fabs((R)w) + c) * (R)m.invh[2];
+            if (m.nx > 1) ac += (fabs(ub) + c) * (R)m.invh[0];
+            if (m.ny > 1) ac += (fabs(vb) + c) * (R)m.invh[1];
+            if (m.nz > 1) ac += (fabs(wb) + c) * (R)m.invh[2];
             r_ac = ac;
             if (!(m.flags & F_NO_VISCOUS)) {
                 const R nu = mu / (R)rho;
