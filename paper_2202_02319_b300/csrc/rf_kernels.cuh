@@ -542,21 +542,21 @@ __device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (
             else tau[q] = mu * (dtd[q] + dn[q]);
         }
         // species diffusion with correction velocity, enthalpy flux
+        R jd[NS];                   // Dc_s,face dX_s / dn
         R corr = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             const R dX = (st.q(QL<NS>::X + s, 2) - st.q(QL<NS>::X + s, 1)) * ih;
             const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
-            corr = fma(Dcf, dX, corr);
+            jd[s] = Dcf * dX;
+            corr += jd[s];
         }
         const R irL = rcp_face(rhoL), irR = rcp_face(rhoR);
         R qh = 0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R dX = (st.q(QL<NS>::X + s, 2) - st.q(QL<NS>::X + s, 1)) * ih;
-            const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
             const R Yf = R(0.5) * (st.u(s, 1) * irL + st.u(s, 2) * irR);
-            const R J = fma(Yf, corr, -Dcf * dX);
+            const R J = fma(Yf, corr, -jd[s]);
             const R hf = R(0.5) * (st.q(QL<NS>::H + s, 1) + st.q(QL<NS>::H + s, 2));
             qh = fma(J, hf, qh);
             G[s] -= J;
