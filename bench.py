@@ -209,7 +209,8 @@ def run_ours(args):
     nv.set_option(ctx, "profile", 0)
     launches_per_step = sum(v[1] for v in prof.values()) // nsteps_prof + 3     # + dt, prologue, epilogue kernels
 
-    # --- e2e through the public API with host buffers: H2D U,T, one step, D2H U
+    # --- e2e through the public host-buffer call: each step copies U, T in from pinned
+    # host memory (by chunks overlapping the first stage) and U, T back out
     Uh = torch.empty_like(U, device="cpu").pin_memory()
     Th = torch.empty_like(T, device="cpu").pin_memory()
     Uh.copy_(U)
@@ -217,21 +218,19 @@ def run_ours(args):
     s = torch.cuda.current_stream()
     te = torch.zeros(1, dtype=torch.float64, device=dev)
     e2e_steps = max(1, min(3, args.steps))
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nv.rk_step_host(ctx, Uh, Th, Uh, Th, te, 0.0, case.cfl, las, None)      # allocates the context's copies
     torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(s)
     for _ in range(e2e_steps):
-        U.copy_(Uh, non_blocking=True)
-        T.copy_(Th, non_blocking=True)
-        nv.rk_step(ctx, U, T, te, 0.0, case.cfl, las, None)
-        Uh.copy_(U, non_blocking=True)
+        nv.rk_step_host(ctx, Uh, Th, Uh, Th, te, 0.0, case.cfl, las, None)
     f1.record(s)
     torch.cuda.synchronize()
     nv.check(ctx)
     e2e_ms = f0.elapsed_time(f1)
     e2e_value = world * ncell * 3 * e2e_steps / (e2e_ms * 1e-3)
     h2d = (U.numel() + T.numel()) * 8
-    d2h = U.numel() * 8
+    d2h = (U.numel() + T.numel()) * 8
     del ctx, U, T, Uh, Th
     torch.cuda.empty_cache()
 

@@ -161,6 +161,20 @@ int rf_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *lase
 int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, double cfl,
                const rf_laser *laser, double *dt_dev, rf_stream s);
 
+/* rf_rk_step on host buffers: U_in (host, FP64, [Ns+4][N]) and T_in (host, [N]) are
+ * copied to device buffers owned by the context (allocated on the first call,
+ * N (Ns+5) doubles, counted by rf_ctx_workspace_bytes), the step runs there, and the
+ * new state is copied to U_out (host, may equal U_in) and, if not NULL, the
+ * temperature to T_out (host, may equal T_in).  The state is copied in by eight
+ * chunks of cells on a copy stream of the context, and the first stage's
+ * cell-state kernel of each chunk starts once that chunk has arrived, so that the
+ * transfer overlaps computation (with pinned host memory; pageable memory works
+ * but copies synchronously).  t_dev, dt_fixed, cfl, laser, dt_dev as rf_rk_step.
+ * Asynchronous on s: the host buffers must stay valid, and U_out unread, until s
+ * has completed.  Errors: RF_EINVAL, RF_ENOMEM, RF_ECUDA. */
+int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U_out, double *T_out, double *t_dev,
+                    double dt_fixed, double cfl, const rf_laser *laser, double *dt_dev, rf_stream s);
+
 /* Tuning and test options of a context (host-side, take effect on the next call):
  *   "newton_maxit" Newton iteration cap (default 30; 0 forces RF_ENEWTON, for tests)
  *   "x_block"      threads per block of the x sweep (multiple of 32, <= 256; default 256)

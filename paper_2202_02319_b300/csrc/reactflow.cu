@@ -144,6 +144,10 @@ struct rf_ctx {
     size_t bytes = 0;
     // adjoint workspace (FP64 contexts), allocated on first use
     double *adj = nullptr;                   // Qbar [nq n], zero [nv n], R [nv n], lamS [nv n], Ub1, Ub2, Ln [nv n], T0, T1, T2 [n]
+    // host-buffer step: device copies of U and T, a copy stream and its chunk events
+    double *hU = nullptr, *hT = nullptr;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t hev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
@@ -309,9 +313,13 @@ extern "C" void rf_free_mechanism(rf_mech *m) {
 }
 
 static void free_ctx_buffers(rf_ctx *c) {
-    void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag, c->adj};
+    void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag, c->adj,
+                    c->hU, c->hT};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    for (cudaEvent_t e : c->hev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy) cudaStreamDestroy(c->copy);
 }
 
 static void clear_profile(rf_ctx *c) {
@@ -431,6 +439,8 @@ static Member base_member(rf_ctx *c) {
     m.status = c->status;
     m.bad_cell = c->bad_cell;
     m.flags = (int)c->flags;
+    m.c_lo = 0;
+    m.c_hi = c->n;
     return m;
 }
 
@@ -473,7 +483,8 @@ struct Path {
 
     static int cell_state(rf_ctx *c, const Member &m, cudaStream_t s) {
         const int B = 128;
-        const long long nb = (c->n + B - 1) / B;
+        const long long nb = (m.c_hi - m.c_lo + B - 1) / B;
+        if (nb <= 0) return RF_OK;
         const size_t smem = cell_state_smem<R, NS>(B);
         ProfScope ps(c, PROF_CELL, s);
         cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mslot, m, c->newton_maxit);
@@ -577,8 +588,10 @@ struct Path {
         return sweeps<MODE_RHS>(c, m, s);
     }
 
+    // chunks > 0: the first stage's cell state runs on cells [q n / chunks, (q + 1) n / chunks)
+    // once chunk_ev[q] has completed (the host-buffer step streams the state in by chunks)
     static int rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, double cfl, const rf_laser *L,
-                       double *dt_dev, cudaStream_t s) {
+                       double *dt_dev, cudaStream_t s, int chunks = 0, const cudaEvent_t *chunk_ev = nullptr) {
         // clock = (t, dt, cfl, dt_fixed)
         double hostclk[2] = {cfl, dt_fixed};
         CUDA_TRY(cudaMemcpyAsync(c->clock, t_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -600,8 +613,18 @@ struct Path {
             m.stage_b = b[k];
             m.stage_c = cc[k];
             m.want_rates = (k == 0 && !(dt_fixed > 0.0)) ? 1 : 0;
-            int rc = cell_state(c, m, s);
-            if (rc) return rc;
+            int rc;
+            if (k == 0 && chunks > 0) {
+                for (int q = 0; q < chunks; ++q) {
+                    Member mq = m;
+                    mq.c_lo = c->n * q / chunks;
+                    mq.c_hi = c->n * (q + 1) / chunks;
+                    CUDA_TRY(cudaStreamWaitEvent(s, chunk_ev[q], 0));
+                    if ((rc = cell_state(c, mq, s))) return rc;
+                }
+            } else if ((rc = cell_state(c, m, s))) {
+                return rc;
+            }
             if (k == 0) {
                 dt_kernel<<<1, 1, 0, s>>>(c->clock, c->rates, hmin, !(c->flags & RF_NO_VISCOUS),
                                           !(c->flags & RF_NO_CHEMISTRY) && c->mech->nr > 0, m.laser_on && !(c->flags & RF_NO_LASER),
@@ -685,6 +708,46 @@ extern "C" int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double
     if (!c || !U || !T || !t_dev) return fail(RF_EINVAL, "rf_rk_step: null argument");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_rk_step: need dt_fixed > 0 or cfl > 0");
     DISPATCH(c, rk_step(c, U, T, t_dev, dt_fixed, cfl, L, dt_dev, (cudaStream_t)s));
+}
+
+static int rk_step_chunked(rf_ctx *c, double *t_dev, double dt_fixed, double cfl, const rf_laser *L, double *dt_dev,
+                           cudaStream_t s, int chunks) {
+    DISPATCH(c, rk_step(c, c->hU, c->hT, t_dev, dt_fixed, cfl, L, dt_dev, s, chunks, c->hev));
+}
+
+extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U_out, double *T_out,
+                               double *t_dev, double dt_fixed, double cfl, const rf_laser *L, double *dt_dev,
+                               rf_stream s) {
+    if (!c || !U_in || !T_in || !U_out || !t_dev) return fail(RF_EINVAL, "rf_rk_step_host: null argument");
+    if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_rk_step_host: need dt_fixed > 0 or cfl > 0");
+    const long long n = c->n;
+    const int nv = c->nv;
+    if (!c->hU) {
+        CUDA_TRY(cudaMalloc((void **)&c->hU, (size_t)n * nv * sizeof(double)));
+        CUDA_TRY(cudaMalloc((void **)&c->hT, (size_t)n * sizeof(double)));
+        c->bytes += (size_t)n * (nv + 1) * sizeof(double);
+    }
+    if (!c->copy) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : c->hev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    cudaStream_t st = (cudaStream_t)s;
+    const int chunks = (int)std::min<long long>(8, n);
+    // the copy stream follows the work already queued on s (an earlier read of hU / hT)
+    CUDA_TRY(cudaEventRecord(c->hev[8], st));
+    CUDA_TRY(cudaStreamWaitEvent(c->copy, c->hev[8], 0));
+    for (int q = 0; q < chunks; ++q) {
+        const long long lo = n * q / chunks, hi = n * (q + 1) / chunks;
+        for (int v = 0; v < nv; ++v)
+            CUDA_TRY(cudaMemcpyAsync(c->hU + (size_t)v * n + lo, U_in + (size_t)v * n + lo, (size_t)(hi - lo) * sizeof(double),
+                                     cudaMemcpyHostToDevice, c->copy));
+        CUDA_TRY(cudaMemcpyAsync(c->hT + lo, T_in + lo, (size_t)(hi - lo) * sizeof(double), cudaMemcpyHostToDevice, c->copy));
+        CUDA_TRY(cudaEventRecord(c->hev[q], c->copy));
+    }
+    if (int rc = rk_step_chunked(c, t_dev, dt_fixed, cfl, L, dt_dev, st, chunks)) return rc;
+    CUDA_TRY(cudaMemcpyAsync(U_out, c->hU, (size_t)n * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (T_out) CUDA_TRY(cudaMemcpyAsync(T_out, c->hT, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    return RF_OK;
 }
 
 extern "C" int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s) {

@@ -81,6 +81,7 @@ struct Member {
     int t_from_host;             // 1: stage time is t_host (rf_rhs), 0: clock[0] + stage_c clock[1]
     double t_host;
     int xW, xrpb;                // x sweep row chunk width and rows per block (ensemble launches)
+    long long c_lo, c_hi;        // cells [c_lo, c_hi) of a cell-state launch
 };
 
 // Q field order (each field n values of type R).

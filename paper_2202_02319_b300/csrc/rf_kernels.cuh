@@ -153,7 +153,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 
     const int tid = threadIdx.x;
     const long long n = m.n;
-    const long long cell = blk * B + tid;
+    const long long cell = m.c_lo + blk * B + tid;
     const bool chem_on = !(m.flags & F_NO_CHEM) && M.nr > 0;
     const bool laser_on = m.laser_on && !(m.flags & F_NO_LASER);
     if (tid == 0 && laser_on) {
@@ -169,7 +169,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
     __syncthreads();
 
     R r_ac = 0, r_df = 0, r_ch = 0;
-    if (cell < n) {
+    if (cell < m.c_hi) {
         const double *U = m.U;
         double rs[NS], Y[NS];
         double rho = 0.0;

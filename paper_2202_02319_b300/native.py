@@ -60,6 +60,8 @@ _sigs = {
     "rf_init_state": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "rf_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.POINTER(Laser), _vp, _vp]),
     "rf_rk_step": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _vp, _vp]),
+    "rf_rk_step_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(Laser), _vp, _vp]),
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
@@ -203,6 +205,26 @@ def rk_step(ctx: Context, U, T, t_dev, dt_fixed: float = 0.0, cfl: float = 0.5, 
     L = _laser(laser)
     _check(_lib.rf_rk_step(ctx.handle, _ptr(U), _ptr(T), _ptr(t_dev), float(dt_fixed), float(cfl),
                            ctypes.byref(L) if L else None, _ptr(dt_dev), _stream(stream)), "rf_rk_step")
+
+
+def _hptr(t) -> int:
+    if t is None:
+        return None
+    import torch
+    if not (t.device.type == "cpu" and t.dtype == torch.float64 and t.is_contiguous()):
+        raise ValueError("expected a contiguous float64 CPU tensor")
+    return t.data_ptr()
+
+
+def rk_step_host(ctx: Context, U_in, T_in, U_out, T_out, t_dev, dt_fixed: float = 0.0, cfl: float = 0.5, laser=None,
+                 dt_dev=None, stream=None):
+    """One SSP-RK3 step on host tensors (pinned for overlap): U_in, T_in copied in by chunks
+    overlapping the first stage, the new state written to U_out (and T_out if given).
+    Asynchronous on the stream, like the device-buffer step."""
+    L = _laser(laser)
+    _check(_lib.rf_rk_step_host(ctx.handle, _hptr(U_in), _hptr(T_in), _hptr(U_out), _hptr(T_out), _ptr(t_dev),
+                                float(dt_fixed), float(cfl), ctypes.byref(L) if L else None, _ptr(dt_dev),
+                                _stream(stream)), "rf_rk_step_host")
 
 
 def set_option(ctx: Context, key: str, value: float):
