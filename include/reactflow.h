@@ -177,8 +177,9 @@ int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U
 
 /* Tuning and test options of a context (host-side, take effect on the next call):
  *   "newton_maxit" Newton iteration cap (default 30; 0 forces RF_ENEWTON, for tests)
- *   "x_block"      threads per block of the x sweep (multiple of 32, <= 256; default 256)
- *   "walk_block"   threads per block of the y / z sweeps (multiple of 32, <= 128; default 128)
+ *   "x_block"      threads per block of the FP64 x sweep (multiple of 32, <= 256; default 256)
+ *   "walk_block"   threads per block of the FP64 y / z sweeps (multiple of 32, <= 128; default 128)
+ *                  (the mixed-precision sweeps use fixed 128-thread tiles staged in shared memory)
  *   "walk_seg"     cells walked per thread in the y / z sweeps (default 16 in FP64, 32 in mixed precision)
  *   "profile"      1: record a CUDA event pair on the launching stream around every
  *                  kernel launch of this context (read with rf_profile_read); 0: off
@@ -302,7 +303,9 @@ int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, r
  * the FP32 state copy in mixed precision and a 256-byte header; e.g. at most
  * 43,000 cells for 9 species in FP64) are rejected with RF_EINVAL before any
  * device work.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and the first call per precision and species count sets
+ * kernel attributes (shared-memory limits), so make those calls before any
+ * stream capture.
  * Calls share the array and its last contents (the status word is cleared at
  * each call); calls that overlap on the GPU race, so issue them on one stream.
  * Arguments as rf_rhs; m, g, precision and flags as rf_create_ctx.  The call
