@@ -447,61 +447,29 @@ struct GlobalStencil {
 
 // Flux G = -Fhat^a + F^d at the face between cells L = f-1 and R = f along DIR, from
 // the stencil accessor st (u: conserved variables, q: Q fields, qt: tangential
-// neighbours of L / R).  Every sweep variant computes its faces with this code.
-template <typename R, int NS, int DIR, class S>
-__device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (&G)[NS + 4]) {
+// neighbours of L / R).  Every sweep variant computes its faces with this code, in
+// two parts: face_visc (viscous stress, heat conduction, species diffusion: the
+// only part that reads T, mu, lambda, X, Dc, h and the tangential neighbours) and
+// face_invisc (the LLF-split WENO3-Z flux: conserved variables, u_n, p, c), joined
+// by face_join.
+
+// Viscous part.  ACC = false: D[s] = J_s (diffusive mass flux, subtracted),
+// D[NS + k] = tau_{DIR k}, D[NS + 3] = tau . u_face - q, for face_join.  ACC = true:
+// the same terms applied to the flux in D directly, as face_join would.  rho_L, rho_R
+// are the sums of the partial densities of L and R when have_rho, else formed here
+// (in the same order).
+template <typename R, int NS, int DIR, bool ACC, class S>
+__device__ __forceinline__ void face_visc(const Member &m, const S &st, R (&D)[NS + 4], R rhoL = 0, R rhoR = 0,
+                                          bool have_rho = false) {
     constexpr int NV = NS + 4;
+    if (!ACC) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) G[v] = 0;
-    R rhoL = 0, rhoR = 0;
-    if (!(m.flags & F_NO_INVISCID)) {
-        R un[4], pp[4];
-        R alpha = 0;
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            un[o] = st.q(Q_U + DIR, o);
-            pp[o] = st.q(Q_P, o);
-            const R lam = fabs(un[o]) + st.q(Q_C, o);
-            alpha = lam > alpha ? lam : alpha;
-        }
-        // f+- = (F(U) +- alpha U) / 2 = (u_n/2 +- alpha/2) U + (p/2 or p u_n/2 for the
-        // momentum along DIR and the energy)
-        const R ha = R(0.5) * alpha;
-        R lp[4], lm[4], hp[4], hpu[4];
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-            const R h = R(0.5) * un[o];
-            lp[o] = h + ha;
-            lm[o] = h - ha;
-            hp[o] = R(0.5) * pp[o];
-            hpu[o] = hp[o] * un[o];
-        }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            R fp[4], fm[4];
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const R Uv = st.u(v, o);
-                if (v < NS) {
-                    if (o == 1) rhoL += Uv;
-                    if (o == 2) rhoR += Uv;
-                }
-                fp[o] = lp[o] * Uv;
-                fm[o] = lm[o] * Uv;
-                if (v == NS + DIR) {
-                    fp[o] += hp[o];
-                    fm[o] += hp[o];
-                }
-                if (v == NS + 3) {
-                    fp[o] += hpu[o];
-                    fm[o] += hpu[o];
-                }
-            }
-            G[v] = -(weno3z<R>(fp[0], fp[1], fp[2]) + weno3z<R>(fm[3], fm[2], fm[1]));
-        }
+        for (int v = 0; v < NV; ++v) D[v] = 0;
     }
     if (!(m.flags & F_NO_VISCOUS)) {
-        if (m.flags & F_NO_INVISCID) {
+        if (!have_rho) {
+            rhoL = 0;
+            rhoR = 0;
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 rhoL += st.u(s, 1);
@@ -559,17 +527,95 @@ __device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (
             const R J = fma(Yf, corr, -jd[s]);
             const R hf = R(0.5) * (st.q(QL<NS>::H + s, 1) + st.q(QL<NS>::H + s, 2));
             qh = fma(J, hf, qh);
-            G[s] -= J;
+            if (ACC) D[s] -= J;
+            else D[s] = J;
         }
         const R q = fma(-lam, (st.q(Q_T, 2) - st.q(Q_T, 1)) * ih, qh);
         R work = 0;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            G[NS + k] += tau[k];
+            if (ACC) D[NS + k] += tau[k];
+            else D[NS + k] = tau[k];
             work = fma(tau[k], R(0.5) * (velL[k] + velR[k]), work);
         }
-        G[NS + 3] += work - q;
+        if (ACC) D[NS + 3] += work - q;
+        else D[NS + 3] = work - q;
     }
+}
+
+// Inviscid part: G = -(f+ reconstructed from the left + f- from the right); rho_L,
+// rho_R the sums of the partial densities of L and R met on the way (0 when the
+// inviscid flux is off).
+template <typename R, int NS, int DIR, class S>
+__device__ __forceinline__ void face_invisc(const Member &m, const S &st, R (&G)[NS + 4], R &rhoL, R &rhoR) {
+    constexpr int NV = NS + 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    rhoL = 0;
+    rhoR = 0;
+    if (!(m.flags & F_NO_INVISCID)) {
+        R un[4], pp[4];
+        R alpha = 0;
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            un[o] = st.q(Q_U + DIR, o);
+            pp[o] = st.q(Q_P, o);
+            const R lam = fabs(un[o]) + st.q(Q_C, o);
+            alpha = lam > alpha ? lam : alpha;
+        }
+        // f+- = (F(U) +- alpha U) / 2 = (u_n/2 +- alpha/2) U + (p/2 or p u_n/2 for the
+        // momentum along DIR and the energy)
+        const R ha = R(0.5) * alpha;
+        R lp[4], lm[4], hp[4], hpu[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const R h = R(0.5) * un[o];
+            lp[o] = h + ha;
+            lm[o] = h - ha;
+            hp[o] = R(0.5) * pp[o];
+            hpu[o] = hp[o] * un[o];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R fp[4], fm[4];
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const R Uv = st.u(v, o);
+                if (v < NS) {
+                    if (o == 1) rhoL += Uv;
+                    if (o == 2) rhoR += Uv;
+                }
+                fp[o] = lp[o] * Uv;
+                fm[o] = lm[o] * Uv;
+                if (v == NS + DIR) {
+                    fp[o] += hp[o];
+                    fm[o] += hp[o];
+                }
+                if (v == NS + 3) {
+                    fp[o] += hpu[o];
+                    fm[o] += hpu[o];
+                }
+            }
+            G[v] = -(weno3z<R>(fp[0], fp[1], fp[2]) + weno3z<R>(fm[3], fm[2], fm[1]));
+        }
+    }
+}
+
+template <typename R, int NS>
+__device__ __forceinline__ void face_join(const Member &m, const R (&D)[NS + 4], R (&G)[NS + 4]) {
+    if (m.flags & F_NO_VISCOUS) return;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) G[s] -= D[s];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) G[NS + k] += D[NS + k];
+    G[NS + 3] += D[NS + 3];
+}
+
+template <typename R, int NS, int DIR, class S>
+__device__ __forceinline__ void face_flux_core(const Member &m, const S &st, R (&G)[NS + 4]) {
+    R rhoL, rhoR;
+    face_invisc<R, NS, DIR>(m, st, G, rhoL, rhoR);
+    face_visc<R, NS, DIR, true>(m, st, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
 }
 
 // Face flux from global memory; `cc` holds the cell's coordinates (i, j, k) with
@@ -742,7 +788,7 @@ struct WalkTile {
     static constexpr int TX = 32, TY = 4, NL = TX * TY;
     static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS;
     static constexpr int SX = TX + 2, SY = TY + 2, NSL = SX * SY;
-    static constexpr int DI = 5, DV = 3;
+    static constexpr int DI = 5, DV = 2;
     static constexpr int I_FLOATS = DI * NI * NL, V_FLOATS = DV * NVV * NL, S_FLOATS = DV * 3 * NSL;
     static constexpr size_t SMEM = sizeof(float) * (size_t)(I_FLOATS + V_FLOATS + S_FLOATS);
 };
@@ -769,9 +815,12 @@ struct WalkStencil {
 };
 
 // One tile line group walking faces c0 .. c1 of its segment [c0, c1) along DIR:
-// face f needs planes f-2 .. f+1 (ring I) and f-1, f (ring V, slab); while face f is
-// computed the planes f+2 / f+1 are in flight.  Faces are computed by
-// face_flux_core from shared memory, cells updated one face behind.
+// face f needs planes f-2 .. f+1 (ring I) and f-1, f (ring V, slab).  Per face: wait
+// for its planes; start plane f+2 of ring I (into the slot of plane f-3); the
+// viscous part (the only reader of ring V and the slab); barrier; start plane f+1
+// of ring V and the slab (into the slots of plane f-1); the inviscid part and the
+// update of cell f-1.  Two V slots instead of three keep a block at 74.8 KB, three
+// per SM.
 template <int NS, int DIR, int MODE>
 __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const Member &m, int tile, int sblk, int seg,
                                                         float *smem) {
@@ -895,9 +944,6 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
     const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
     float Gp[NV];
     for (int f = c0; f <= c1; ++f) {
-        if (f + 2 <= c1 + 1) stage_I(f + 2);
-        if (f + 1 <= c1) stage_V(f + 1);
-        cp_async_commit();
         // the update's inputs of cell f-1, loaded before the wait so their latency overlaps it
         const bool upd = active && f > c0;
         const long long cell = lbase + (long long)(f - 1) * sd;
@@ -917,20 +963,28 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
                 }
             }
         }
-        cp_async_wait_all_but_one();
+        cp_async_wait_all();
         __syncthreads();
-        if (active) {
-            WalkStencil<NS, DIR> st;
+        if (f + 2 <= c1 + 1) stage_I(f + 2);
+        cp_async_commit();
+        WalkStencil<NS, DIR> st;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) st.I[q] = ringI + pmod(f - 2 + q, W::DI) * W::NI * NL;
-            st.V[0] = ringV + pmod(f - 1, W::DV) * W::NVV * NL;
-            st.V[1] = ringV + pmod(f, W::DV) * W::NVV * NL;
-            st.S[0] = slab + pmod(f - 1, W::DV) * 3 * W::NSL;
-            st.S[1] = slab + pmod(f, W::DV) * 3 * W::NSL;
-            st.l = l;
-            st.sl = (ty + 1) * W::SX + tx + 1;
-            float Gn[NV];
-            face_flux_core<float, NS, DIR>(m, st, Gn);
+        for (int q = 0; q < 4; ++q) st.I[q] = ringI + pmod(f - 2 + q, W::DI) * W::NI * NL;
+        st.V[0] = ringV + pmod(f - 1, W::DV) * W::NVV * NL;
+        st.V[1] = ringV + pmod(f, W::DV) * W::NVV * NL;
+        st.S[0] = slab + pmod(f - 1, W::DV) * 3 * W::NSL;
+        st.S[1] = slab + pmod(f, W::DV) * 3 * W::NSL;
+        st.l = l;
+        st.sl = (ty + 1) * W::SX + tx + 1;
+        float D[NV];
+        if (active) face_visc<float, NS, DIR, false>(m, st, D);
+        __syncthreads();
+        if (f + 1 <= c1) stage_V(f + 1);
+        cp_async_commit();
+        if (active) {
+            float Gn[NV], rl, rr;
+            face_invisc<float, NS, DIR>(m, st, Gn, rl, rr);
+            face_join<float, NS>(m, D, Gn);
             if (upd) {
                 // as cell_update, from the preloaded inputs
 #pragma unroll
@@ -945,20 +999,23 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
 #pragma unroll
             for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
         }
-        __syncthreads();
     }
     cp_async_wait_all();
+    __syncthreads();            // the rings are free for the block's next tile
 }
 
 // ----------------------------------------------------------------------------- staged x sweep (FP32 bulk)
 
 // Each warp of a 128-thread block takes one row (fixed y, z) and walks it in chunks
 // of 32 faces, lane l computing face F = F0 + l.  A chunk's window of 40 cells,
-// starting at the 4-aligned cell 32 k - 4, is copied by cp.async into one of two
-// per-warp buffers while the previous chunk is computed:
+// starting at the 4-aligned cell 32 k - 4, is copied by cp.async, in field-rows:
 //   I   fields: the NS + 4 conserved variables (FP32 copy), u, p, c;
 //   V   fields: T, mu, lambda, X_s, Dc_s, h_s;
 //   vel rows:   v, w of the row and (u, v) of rows y -+ 1, (u, w) of rows z -+ 1.
+// The I rows are double-buffered per warp; the V and vel rows, read only by the
+// viscous part of the face, have one buffer per warp, refilled for the next chunk
+// between the viscous and the inviscid part (warp-level synchronisation only):
+// 47 KB per block of 4 warps, four blocks per SM.
 // Periodic rows compute faces 1 .. nx (face nx has the stencil of face 0) and
 // update cell 0 last; other rows compute faces 0 .. nx.
 template <int NS>
@@ -966,17 +1023,20 @@ struct XTile {
     static constexpr int WARPS = 4, WIN = 40;
     static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS, NVEL = 10;
     static constexpr int NFR = NI + NVV + NVEL;                // field-rows of a window
-    static constexpr int BUF = NFR * WIN;                     // floats of one window
+    static constexpr int BUF_I = NI * WIN, BUF_V = (NFR - NI) * WIN;
+    static constexpr int WBUF = 2 * BUF_I + BUF_V;             // floats of one warp's buffers
     static constexpr int AUX = 16 + 2 * ((NFR + 1) / 2 * 2);    // floats per warp: G(1) stash, then NFR pointers
-    static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * 2 * BUF + (size_t)WARPS * AUX);
+    static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * WBUF + (size_t)WARPS * AUX);
 };
 
 template <int NS>
 struct XStencil {
     using X = XTile<NS>;
-    const float *b;          // window buffer
+    const float *bi, *bv;    // window buffers of the I rows and of the V / vel rows
     int po;                  // window position of the face's cell f-2
-    __device__ __forceinline__ float at(int fr, int o) const { return b[fr * X::WIN + po + o]; }
+    __device__ __forceinline__ float at(int fr, int o) const {
+        return fr < X::NI ? bi[fr * X::WIN + po + o] : bv[(fr - X::NI) * X::WIN + po + o];
+    }
     __device__ __forceinline__ float u(int v, int o) const { return at(v, o); }
     __device__ __forceinline__ float q(int f, int o) const {
         if (f == Q_U) return at(X::NV + 0, o);
@@ -1006,8 +1066,9 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     const long long n = m.n;
     const float *__restrict__ U = m.U32;
     const float *__restrict__ Q = (const float *)m.Q;
-    float *buf0 = smem + (size_t)warp * 2 * X::BUF;
-    float *stash = smem + (size_t)X::WARPS * 2 * X::BUF + warp * X::AUX;
+    float *bufI = smem + (size_t)warp * X::WBUF;           // two I buffers, then the V buffer
+    float *bufV = bufI + 2 * X::BUF_I;
+    float *stash = smem + (size_t)X::WARPS * X::WBUF + warp * X::AUX;
     const bool periodic = m.bc[0] == 0;
     const int fs = periodic ? 1 : 0;                       // first face computed
     const int nf = periodic ? nx : nx + 1;                 // faces fs .. fs + nf - 1
@@ -1046,33 +1107,36 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     // lanes 0..29 copy the window's 4-cell column chunk lane % 10 of field-rows
     // lane / 10, + 3, + 6, ...: the range test and any wrap are per lane, not per item
     const int sq4 = lane % (WIN / 4), sfr0 = lane / (WIN / 4);
-    auto stage = [&](int c, float *dst) {
+    int sfrv = sfr0;                                       // the lane's first V / vel row
+    while (sfrv < X::NI) sfrv += 3;
+    // field-rows fr0, fr0 + 3, .. < fr1 of chunk c's window into dst (row fr at dst + (fr - base) WIN)
+    auto stage = [&](int c, float *dst, int fr0, int fr1, int base) {
         if (lane >= 3 * (WIN / 4)) return;
         const int x4 = 32 * c - 4 + 4 * sq4;
-        float *dp = dst + sfr0 * WIN + 4 * sq4;
+        float *dp = dst + (fr0 - base) * WIN + 4 * sq4;
         if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
-            for (int fr = sfr0; fr < X::NFR; fr += 3, dp += 3 * WIN) cp_async16(dp, tab[fr] + x4);
+            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * WIN) cp_async16(dp, tab[fr] + x4);
         } else {
             int xi[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) xi[i] = map_idx(x4 + i, nx, m.bc[0]);
-            for (int fr = sfr0; fr < X::NFR; fr += 3, dp += 3 * WIN) {
+            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * WIN) {
                 const float *sp = tab[fr];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) cp_async4(dp + i, sp + xi[i]);
             }
         }
     };
+    auto stage_I = [&](int c) { stage(c, bufI + (c & 1) * X::BUF_I, sfr0, X::NI, 0); };
+    auto stage_V = [&](int c) { stage(c, bufV, sfrv, X::NFR, X::NI); };
 
     const float ih = (float)m.invh[0];
     const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
     float Gc[NV];                      // lane 31's flux of the previous chunk
-    stage(0, buf0);
+    stage_I(0);
+    stage_V(0);
     cp_async_commit();
     for (int c = 0; c < nchunks; ++c) {
-        float *cur = buf0 + (c & 1) * X::BUF;
-        if (c + 1 < nchunks) stage(c + 1, buf0 + ((c + 1) & 1) * X::BUF);
-        cp_async_commit();
         const int F = fs + 32 * c + lane;
         const bool has_face = F < fs + nf;
         // this lane updates cell F - 1 (cell 0 of a periodic row comes last)
@@ -1094,14 +1158,25 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
                 }
             }
         }
-        cp_async_wait_all_but_one();
+        cp_async_wait_all();
         __syncwarp();
+        // the I buffer of chunk c + 1 is the one chunk c - 1 read
+        if (c + 1 < nchunks) stage_I(c + 1);
+        cp_async_commit();
+        XStencil<NS> st;
+        st.bi = bufI + (c & 1) * X::BUF_I;
+        st.bv = bufV;
+        st.po = F - 2 - (32 * c - 4);
+        float D[NV];
+        if (has_face) face_visc<float, NS, 0, false>(m, st, D);
+        __syncwarp();
+        if (c + 1 < nchunks) stage_V(c + 1);
+        cp_async_commit();
         float G[NV];
         if (has_face) {
-            XStencil<NS> st;
-            st.b = cur;
-            st.po = F - 2 - (32 * c - 4);
-            face_flux_core<float, NS, 0>(m, st, G);
+            float rl, rr;
+            face_invisc<float, NS, 0>(m, st, G, rl, rr);
+            face_join<float, NS>(m, D, G);
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) G[v] = 0.f;
