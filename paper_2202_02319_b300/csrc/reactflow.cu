@@ -905,8 +905,7 @@ static int ens_build(rf_ensemble *e) {
         const int nv = c->nv;
         const bool staged = c->precision == RF_MIXED;
         // staged x sweep (FP32 bulk): four rows per block, window buffers as XTile
-        const int nfr = 4 * c->ns + 20;
-        const size_t x_staged = sizeof(float) * ((size_t)4 * 2 * nfr * 40 + (size_t)4 * (16 + 2 * ((nfr + 1) / 2 * 2)));
+        const size_t x_staged = x_staged_smem(c->ns);
         smx = std::max(smx, staged ? x_staged : (size_t)nv * rpb * (W + 2) * c->rsize);
         const long long ncb = (c->n + 127) / 128;
         for (long long q = 0; q < ncb; ++q) items[0].push_back({mi, (int)q, 0, 0});

@@ -1013,29 +1013,37 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
 //   V   fields: T, mu, lambda, X_s, Dc_s, h_s;
 //   vel rows:   v, w of the row and (u, v) of rows y -+ 1, (u, w) of rows z -+ 1.
 // The I rows are double-buffered per warp; the V and vel rows, read only by the
-// viscous part of the face, have one buffer per warp, refilled for the next chunk
-// between the viscous and the inviscid part (warp-level synchronisation only):
-// 47 KB per block of 4 warps, four blocks per SM.
+// viscous part of the face (at cells f-1 and f), have one 36-cell window per warp
+// (starting 4 cells later in periodic rows, whose faces are shifted by one),
+// refilled for the next chunk between the viscous and the inviscid part
+// (warp-level synchronisation only): 44.5 KB per block of 4 warps, five blocks per SM.
 // Periodic rows compute faces 1 .. nx (face nx has the stencil of face 0) and
 // update cell 0 last; other rows compute faces 0 .. nx.
+// Dynamic shared memory of a staged x-sweep block for ns species (as XTile<ns>::SMEM).
+__host__ __device__ constexpr size_t x_staged_smem(int ns) {
+    return sizeof(float) * (size_t)4 *
+           ((size_t)2 * (ns + 7) * 40 + (size_t)(3 * ns + 13) * 36 + 16 + 2 * ((4 * ns + 21) / 2 * 2));
+}
+
 template <int NS>
 struct XTile {
-    static constexpr int WARPS = 4, WIN = 40;
+    static constexpr int WARPS = 4, WIN = 40, WINV = 36;
     static constexpr int NV = NS + 4, NI = NV + 3, NVV = 3 + 3 * NS, NVEL = 10;
     static constexpr int NFR = NI + NVV + NVEL;                // field-rows of a window
-    static constexpr int BUF_I = NI * WIN, BUF_V = (NFR - NI) * WIN;
+    static constexpr int BUF_I = NI * WIN, BUF_V = (NFR - NI) * WINV;
     static constexpr int WBUF = 2 * BUF_I + BUF_V;             // floats of one warp's buffers
     static constexpr int AUX = 16 + 2 * ((NFR + 1) / 2 * 2);    // floats per warp: G(1) stash, then NFR pointers
     static constexpr size_t SMEM = sizeof(float) * ((size_t)WARPS * WBUF + (size_t)WARPS * AUX);
+    static_assert(SMEM == x_staged_smem(NS), "x_staged_smem out of step with XTile");
 };
 
 template <int NS>
 struct XStencil {
     using X = XTile<NS>;
-    const float *bi, *bv;    // window buffers of the I rows and of the V / vel rows
-    int po;                  // window position of the face's cell f-2
+    const float *bi, *bv;    // I window; V / vel window less the offset of its start from the I window's
+    int po;                  // I window position of the face's cell f-2
     __device__ __forceinline__ float at(int fr, int o) const {
-        return fr < X::NI ? bi[fr * X::WIN + po + o] : bv[(fr - X::NI) * X::WIN + po + o];
+        return fr < X::NI ? bi[fr * X::WIN + po + o] : bv[(fr - X::NI) * X::WINV + po + o];
     }
     __device__ __forceinline__ float u(int v, int o) const { return at(v, o); }
     __device__ __forceinline__ float q(int f, int o) const {
@@ -1106,29 +1114,36 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
     __syncwarp();
     // lanes 0..29 copy the window's 4-cell column chunk lane % 10 of field-rows
     // lane / 10, + 3, + 6, ...: the range test and any wrap are per lane, not per item
-    const int sq4 = lane % (WIN / 4), sfr0 = lane / (WIN / 4);
-    int sfrv = sfr0;                                       // the lane's first V / vel row
-    while (sfrv < X::NI) sfrv += 3;
-    // field-rows fr0, fr0 + 3, .. < fr1 of chunk c's window into dst (row fr at dst + (fr - base) WIN)
-    auto stage = [&](int c, float *dst, int fr0, int fr1, int base) {
-        if (lane >= 3 * (WIN / 4)) return;
-        const int x4 = 32 * c - 4 + 4 * sq4;
-        float *dp = dst + (fr0 - base) * WIN + 4 * sq4;
+    // Window of chunk c: I rows from cell 32 c - 4 (40 cells), V / vel rows from
+    // 32 c - 4 + vsh (36 cells).  Lane q + nq r copies the 4-cell column chunk q of
+    // field-rows r, r + 3, r + 6, ... (nq = 10 chunks for I, 9 for V).
+    const int vsh = periodic ? 4 : 0;
+    const int sqI = lane % (WIN / 4), srI = lane / (WIN / 4);
+    const int sqV = lane % (X::WINV / 4), srV = lane / (X::WINV / 4);
+    const int sfrv = X::NI + srV;                          // the lane's first V / vel row
+    // field-rows fr0, fr0 + 3, .. < fr1 into dst (row fr at dst + (fr - base) win), cells x0 + 4 q ..
+    auto stage = [&](int x0, int q, int win, float *dst, int fr0, int fr1, int base) {
+        const int x4 = x0 + 4 * q;
+        float *dp = dst + (fr0 - base) * win + 4 * q;
         if (vec_ok && x4 >= 0 && x4 + 3 < nx) {
-            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * WIN) cp_async16(dp, tab[fr] + x4);
+            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * win) cp_async16(dp, tab[fr] + x4);
         } else {
             int xi[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) xi[i] = map_idx(x4 + i, nx, m.bc[0]);
-            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * WIN) {
+            for (int fr = fr0; fr < fr1; fr += 3, dp += 3 * win) {
                 const float *sp = tab[fr];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) cp_async4(dp + i, sp + xi[i]);
             }
         }
     };
-    auto stage_I = [&](int c) { stage(c, bufI + (c & 1) * X::BUF_I, sfr0, X::NI, 0); };
-    auto stage_V = [&](int c) { stage(c, bufV, sfrv, X::NFR, X::NI); };
+    auto stage_I = [&](int c) {
+        if (lane < 3 * (WIN / 4)) stage(32 * c - 4, sqI, WIN, bufI + (c & 1) * X::BUF_I, srI, X::NI, 0);
+    };
+    auto stage_V = [&](int c) {
+        if (lane < 3 * (X::WINV / 4)) stage(32 * c - 4 + vsh, sqV, X::WINV, bufV, sfrv, X::NFR, X::NI);
+    };
 
     const float ih = (float)m.invh[0];
     const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
@@ -1165,7 +1180,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
         cp_async_commit();
         XStencil<NS> st;
         st.bi = bufI + (c & 1) * X::BUF_I;
-        st.bv = bufV;
+        st.bv = bufV - vsh;
         st.po = F - 2 - (32 * c - 4);
         float D[NV];
         if (has_face) face_visc<float, NS, 0, false>(m, st, D);
@@ -1232,7 +1247,7 @@ template <typename R, int NS>
 __host__ __device__ constexpr size_t walk_smem() { return sizeof(R) == 4 ? WalkTile<NS>::SMEM : 0; }
 
 template <int NS, int DIR, int MODE>
-__global__ void __launch_bounds__(128) sweep_walk_staged_kernel(int mslot, const __grid_constant__ Member m, int seg) {
+__global__ void __launch_bounds__(128, MODE == MODE_STAGE ? 2 : 3) sweep_walk_staged_kernel(int mslot, const __grid_constant__ Member m, int seg) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     sweep_walk_staged_block<NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg, (float *)smem_raw);
