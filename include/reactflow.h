@@ -286,9 +286,14 @@ int rf_probe_peak(int kind, double *tflops, rf_stream s);
  * y[i] = exp(x[i]), y2[i] = exp(-x[i]) from one argument reduction; fn 1: y[i] =
  * ln x[i] for normal x > 0 (ln T of the rates and Gibbs energies); fn 2: y[i] =
  * exp(x[i]) (FP64 Arrhenius rates and transport powers).  Exponentials saturate at
- * 2^(+-1020) beyond |x| ~ 707.  x, y, y2 (fn 0 only; may be NULL otherwise): device
- * arrays of n doubles (caller-owned).  Asynchronous on s; RF_EINVAL for an unknown
- * fn, n < 0 or a missing array with n > 0. */
+ * 2^(+-1020) beyond |x| ~ 707.  And of the binary32 <-> binary64 conversions the
+ * mixed-precision kernels build from integer operations: fn 3: y[i] = the
+ * kernels' binary32 rounding of x[i], y2[i] = the hardware's (both widened
+ * exactly to double); fn 4: the low 32 bits of each x[i] are a binary32 pattern
+ * f, y[i] = the kernels' widening of f, y2[i] = the hardware's.  x, y, y2 (fn 0,
+ * 3, 4; may be NULL otherwise): device arrays of n doubles (caller-owned).
+ * Asynchronous on s; RF_EINVAL for an unknown fn, n < 0 or a missing array with
+ * n > 0. */
 int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s);
 
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the

@@ -1526,11 +1526,19 @@ __global__ void math_probe_kernel(int fn, const double *x, double *y, double *y2
     if (i >= n) return;
     if (fn == 0) exp_pair(x[i], y[i], y2[i]);
     else if (fn == 1) y[i] = log64(x[i]);
-    else y[i] = exp64(x[i]);
+    else if (fn == 2) y[i] = exp64(x[i]);
+    else if (fn == 3) {
+        y[i] = (double)d2f(x[i]);
+        y2[i] = (double)(float)x[i];
+    } else {
+        const float f = __uint_as_float((unsigned)__double2loint(x[i]));
+        y[i] = f2d(f);
+        y2[i] = (double)f;
+    }
 }
 
 extern "C" int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s) {
-    if (fn < 0 || fn > 2 || n < 0 || (n > 0 && (!x || !y || (fn == 0 && !y2))))
+    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y || ((fn == 0 || fn >= 3) && !y2))))
         return fail(RF_EINVAL, "rf_probe_math: bad argument");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));

@@ -91,11 +91,58 @@ template <int NS> struct QL {
 };
 
 
+// ----------------------------------------------------------------------------- binary32 <-> binary64
+
+// Conversions between IEEE 754 binary32 and binary64 from integer operations on the
+// bit fields.  The hardware conversions execute on the FP64 unit at its rate, and
+// the FP64 unit is what bounds the mixed-precision cell state; these run on the
+// integer pipes.  Both return what the hardware conversion (round to nearest even)
+// returns, for every input: values outside the ranges handled below take the
+// hardware conversion.
+
+// binary32 -> binary64 (exact).  Normal numbers: the 8-bit exponent is rebiased
+// (127 -> 1023) and the 23 mantissa bits become the top of the 52; zeros keep their sign.
+__device__ __forceinline__ double f2d(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned a = u & 0x7fffffffu;
+    if (a - 0x00800000u >= 0x7f000000u) {           // zero, subnormal, infinity or NaN
+        if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+        return (double)x;
+    }
+    return __hiloint2double((int)(((a >> 3) + (896u << 20)) | (u & 0x80000000u)), (int)(a << 29));
+}
+
+// binary64 -> binary32, round to nearest even.  For 2^-126 <= |x| < 2^128 the exponent
+// is rebiased (1023 -> 127), the top 23 of the 52 mantissa bits are kept and the 29
+// below them rounded; a carry out of the mantissa is the next binade (or infinity),
+// as in IEEE rounding.  |x| < 2^-150 rounds to a signed zero.
+__device__ __forceinline__ float d2f(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u >= 254u) {                          // outside [2^-126, 2^128)
+        if (e <= 872u) return __uint_as_float(hi & 0x80000000u);
+        return (float)x;
+    }
+    // (hi:lo) << 3: the low nine exponent bits and the top 23 mantissa bits; the
+    // rebias 1023 -> 127 is -896 = -384 (mod 512) in the nine-bit exponent field
+    unsigned t = __funnelshift_l(lo, hi, 3) - (384u << 23);
+    const unsigned rem = lo & 0x1fffffffu;           // the 29 bits rounded away
+    t += (rem + (t & 1u)) > 0x10000000u ? 1u : 0u;   // above half, or half and odd
+    return __uint_as_float(t | (hi & 0x80000000u));
+}
+
+// FP64 value of a bulk-type number and bulk-type value of an FP64 number.
+__device__ __forceinline__ double wide(float x) { return f2d(x); }
+__device__ __forceinline__ double wide(double x) { return x; }
+template <typename R> __device__ __forceinline__ R narrow(double x);
+template <> __device__ __forceinline__ float narrow<float>(double x) { return d2f(x); }
+template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
+
 // 1/x in FP64 by Newton-Raphson iteration r <- r + r (1 - x r) from an FP32 seed:
 // two steps take the seed's ~2^-23 relative error to rounding level.  For x whose
 // magnitude lies in the FP32 normal range (densities, temperatures, gas constants).
 __device__ __forceinline__ double rcp64(double x) {
-    double r = (double)__frcp_rn((float)x);
+    double r = f2d(__frcp_rn(d2f(x)));
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
@@ -290,7 +337,7 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
         const double cv = fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
         // The root is fixed by e(T) = e_target alone; an FP32 reciprocal of cv only
         // perturbs the convergence rate (by ~1e-7 per step), not the converged T.
-        const double dT = res * (double)__frcp_rn((float)cv);
+        const double dT = res * f2d(__frcp_rn(d2f(cv)));
         T = T - dT;
         if (fabs(dT) <= tol) {
             if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS>(M, nasa_range_of(M, T), Y, Rm, P);

@@ -48,7 +48,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
                                        const R *__restrict__ sCb, const double *__restrict__ sP,
                                        const double *__restrict__ sRr, R *__restrict__ sW, R *__restrict__ sD,
                                        int stride, bool want_rate) {
-    const R lnTb = (R)lnT, invTb = (R)invT;
+    const R lnTb = narrow<R>(lnT), invTb = narrow<R>(invT);
     for (int j = 0; j < M.nr; ++j) {
         R kf;
         if (sizeof(R) == 8) kf = (R)exp64(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
@@ -62,7 +62,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             double pr = npd > 0 ? sP[M.prod[j][0] * stride] : 1.0;
             for (int k = 1; k < npd; ++k) pr *= sP[M.prod[j][k] * stride];
             for (int k = 0; k < nrc; ++k) pr *= sRr[M.reac[j][k] * stride];
-            q = (R)fma(-(double)kf, pr, (double)cf);
+            q = narrow<R>(fma(-wide(kf), pr, wide(cf)));
         }
         for (int k = 0; k < M.n_net[j]; ++k) {
             const int s = M.net_sp[j][k];
@@ -83,14 +83,14 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             if (M.rev[j]) {
                 for (int k = 0; k < npd; ++k) {
                     const int s = M.prod[j][k];
-                    double part = sizeof(R) == 4 ? (double)kf * sC[s * stride] : (double)kf / sRr[s * stride];
+                    double part = sizeof(R) == 4 ? wide(kf) * sC[s * stride] : wide(kf) / sRr[s * stride];
                     for (int k2 = 0; k2 < npd; ++k2)
                         if (k2 != k) part *= sP[M.prod[j][k2] * stride];
                     for (int k2 = 0; k2 < nrc; ++k2) part *= sRr[M.reac[j][k2] * stride];
                     R dn = 0;
                     for (int k3 = 0; k3 < M.n_net[j]; ++k3)
                         if (M.net_sp[j][k3] == s) dn = (R)M.net_nu[j][k3];
-                    sD[s * stride] = fma(-dn, (R)part, sD[s * stride]);
+                    sD[s * stride] = fma(-dn, narrow<R>(part), sD[s * stride]);
                 }
             }
         }
@@ -118,7 +118,7 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
         exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
         if (sizeof(R) == 4) {
             sC[s * stride] = G;
-            sCb[s * stride] = (R)C;
+            sCb[s * stride] = narrow<R>(C);
         } else {
             sC[s * stride] = C;
         }
@@ -197,12 +197,12 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             else flag_error(m, ST_NONFINITE, cell);
         }
         if (!isfinite(E) || !isfinite(mx) || !isfinite(my) || !isfinite(mz)) flag_error(m, ST_NONFINITE, cell);
-        const R irhob = (R)irho;
+        const R irhob = narrow<R>(irho);
         R ub, vb, wb;
         if constexpr (sizeof(R) == 4) {
-            ub = (R)mx * irhob;
-            vb = (R)my * irhob;
-            wb = (R)mz * irhob;
+            ub = narrow<R>(mx) * irhob;
+            vb = narrow<R>(my) * irhob;
+            wb = narrow<R>(mz) * irhob;
 #pragma unroll
             for (int s = 0; s < NS; ++s) Y[s] = 0.0;
         } else {
@@ -219,15 +219,14 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const double lnT = log64(T);
         const double cv = mix_cv(P, T) * irho;           // P is density-weighted
         const double cp = cv + Rm;
-        double p;
-        R c;
+        R pb, c;
         if constexpr (sizeof(R) == 4) {
             // bulk quantities of the mixed path: gamma, c and p from FP32 factors
-            const float Tf = (float)T, Rmf = (float)Rm;
-            p = (double)((float)rho * (Rmf * Tf));
-            c = sqrtf((float)cp * rcp((float)cv) * (Rmf * Tf));
+            const float Tf = d2f(T), Rmf = d2f(Rm);
+            pb = d2f(rho) * (Rmf * Tf);
+            c = sqrtf(d2f(cp) * rcp(d2f(cv)) * (Rmf * Tf));
         } else {
-            p = rho * Rm * T;
+            pb = rho * Rm * T;
             c = sqrt_((R)(cp / cv) * (R)(Rm * T));
         }
         const double irm = rcp64(Rm);
@@ -236,14 +235,14 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         Q[Q_U * n + cell] = ub;
         Q[Q_V * n + cell] = vb;
         Q[Q_W * n + cell] = wb;
-        Q[Q_P * n + cell] = (R)p;
-        Q[Q_C * n + cell] = (R)c;
-        Q[Q_T * n + cell] = (R)T;
+        const R Tb = narrow<R>(T), invTb = narrow<R>(invT), irmb = narrow<R>(irm);
+        Q[Q_P * n + cell] = pb;
+        Q[Q_C * n + cell] = c;
+        Q[Q_T * n + cell] = Tb;
         R X[NS];
-        const R Tb = (R)T, invTb = (R)invT, irmb = (R)irm;
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            const R Ys = sizeof(R) == 4 ? (R)rs[s] * irhob : (R)Y[s];
+            const R Ys = sizeof(R) == 4 ? narrow<R>(rs[s]) * irhob : (R)Y[s];
             X[s] = Ys * (mech_RW<R>(M, s) * irmb);
             Q[(QL<NS>::X + s) * n + cell] = X[s];
             Q[(QL<NS>::H + s) * n + cell] = h_RT_bulk(M, rng, s, Tb, invTb) * mech_RW<R>(M, s) * Tb;
@@ -252,7 +251,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
                                     sD + tid, B);
         R mu, lam, Dc[NS], Dmax;
-        transport<R, NS>(M, rng, (R)T, (R)p, (R)rho, (R)Wbar, X, mu, lam, Dc, Dmax);
+        transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), narrow<R>(Wbar), X, mu, lam, Dc, Dmax);
         Q[Q_MU * n + cell] = mu;
         Q[Q_LAM * n + cell] = lam;
 #pragma unroll
@@ -285,12 +284,12 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                 r2 = fma(dz, dz, r2);
             }
             if (sizeof(R) == 8) qL = s_laser[0] * exp64(s_laser[1] * r2);
-            else qL = s_laser[0] * (double)expf((float)(s_laser[1] * r2));
+            else qL = s_laser[0] * f2d(expf(d2f(s_laser[1] * r2)));
         }
-        rhs[(NS + 3) * n + cell] = (R)qL;
+        rhs[(NS + 3) * n + cell] = narrow<R>(qL);
         if (sizeof(R) == 4) {
 #pragma unroll
-            for (int v2 = 0; v2 < NV; ++v2) m.U32[v2 * n + cell] = (float)U[v2 * n + cell];
+            for (int v2 = 0; v2 < NV; ++v2) m.U32[v2 * n + cell] = d2f(U[v2 * n + cell]);
         }
         if (m.want_rates) {
             R ac = 0;
@@ -637,7 +636,7 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
         for (int v = 0; v < NV; ++v) rhs[v * n + cell] = fma(dG[v], ih, rhs[v * n + cell]);
     } else if (MODE == MODE_RHS) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) m.dUdt[v * n + cell] = (double)fma(dG[v], ih, rhs[v * n + cell]);
+        for (int v = 0; v < NV; ++v) m.dUdt[v * n + cell] = wide(fma(dG[v], ih, rhs[v * n + cell]));
     } else {
         const double dt = m.clock[1];
         const double *__restrict__ Uk = m.U;
@@ -647,7 +646,7 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
         const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const double L = (double)fma(dG[v], ih, rhs[v * n + cell]);
+            const double L = wide(fma(dG[v], ih, rhs[v * n + cell]));
             Uo[v * n + cell] = euler ? fma(dt, L, Uk[v * n + cell])
                                      : fma(m.stage_a, Un[v * n + cell], m.stage_b * fma(dt, L, Uk[v * n + cell]));
         }
@@ -991,9 +990,9 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
                 for (int v = 0; v < NV; ++v) {
                     const float L = fma(Gn[v] - Gp[v], ih, racc[v]);
                     if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
-                    else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
-                    else m.Uout[v * n + cell] = euler ? fma(dt, (double)L, uk[v])
-                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+                    else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = wide(L);
+                    else m.Uout[v * n + cell] = euler ? fma(dt, wide(L), uk[v])
+                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, wide(L), uk[v]));
                 }
             }
 #pragma unroll
@@ -1212,9 +1211,9 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
             for (int v = 0; v < NV; ++v) {
                 const float L = fma(G[v] - Gl[v], ih, racc[v]);
                 if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
-                else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = (double)L;
-                else m.Uout[v * n + cell] = euler ? fma(dt, (double)L, uk[v])
-                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, (double)L, uk[v]));
+                else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = wide(L);
+                else m.Uout[v * n + cell] = euler ? fma(dt, wide(L), uk[v])
+                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, wide(L), uk[v]));
             }
         }
         __syncwarp();

@@ -253,6 +253,17 @@ def probe_exp(x, y, stream=None):
     _check(_lib.rf_probe_math(2, _ptr(x), _ptr(y), None, int(x.numel()), _stream(stream)), "rf_probe_math")
 
 
+def probe_d2f(x, y, y2, stream=None):
+    """y = the kernels' binary32 rounding of x, y2 = the hardware's (float64 device tensors)."""
+    _check(_lib.rf_probe_math(3, _ptr(x), _ptr(y), _ptr(y2), int(x.numel()), _stream(stream)), "rf_probe_math")
+
+
+def probe_f2d(x, y, y2, stream=None):
+    """Low 32 bits of each x hold a binary32 pattern f: y = the kernels' widening of f,
+    y2 = the hardware's (float64 device tensors)."""
+    _check(_lib.rf_probe_math(4, _ptr(x), _ptr(y), _ptr(y2), int(x.numel()), _stream(stream)), "rf_probe_math")
+
+
 PROF_CLASSES = ("cell_state", "sweep_x", "sweep_y", "sweep_z", "other")
 
 
