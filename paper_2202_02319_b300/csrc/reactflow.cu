@@ -297,6 +297,10 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
         M.n_prod[j] = (int8_t)npd;
         M.n_net[j] = (int8_t)nnet;
         M.dnu_sum[j] = (int8_t)dsum;
+        int nf = 0;
+        for (int k = 0; k < npd; ++k) M.revf[j][nf++] = M.prod[j][k];
+        for (int k = 0; k < nrc; ++k) M.revf[j][nf++] = (int8_t)(M.reac[j][k] + 16);
+        M.n_revf[j] = (int8_t)nf;
     }
     *out = m;
     return RF_OK;

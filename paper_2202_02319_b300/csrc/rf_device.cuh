@@ -47,6 +47,9 @@ struct MechDev {
     int8_t n_reac[NRMAX], n_prod[NRMAX], reac[NRMAX][3], prod[NRMAX][3];
     int8_t n_net[NRMAX], net_sp[NRMAX][6], net_nu[NRMAX][6];
     int8_t dnu_sum[NRMAX], rev[NRMAX];
+    // factors of the reverse term k_f prod_prod (C G)_s prod_reac (1/G)_s: products
+    // (species s) then reactants (s + 16), in that order
+    int8_t n_revf[NRMAX], revf[NRMAX][6];
 };
 
 // Mechanisms in use live in constant-memory slots; kernels receive the slot
@@ -93,21 +96,36 @@ template <int NS> struct QL {
 
 // ----------------------------------------------------------------------------- binary32 <-> binary64
 
-// Conversions between IEEE 754 binary32 and binary64 from integer operations on the
-// bit fields.  The hardware conversions execute on the FP64 unit at its rate, and
-// the FP64 unit is what bounds the mixed-precision cell state; these run on the
-// integer pipes.  Both return what the hardware conversion (round to nearest even)
-// returns, for every input: values outside the ranges handled below take the
-// hardware conversion.
+// Conversions between IEEE 754 binary32 and binary64 from integer operations on the bit
+// fields.  The hardware conversions execute on the FP64 unit at its rate, and the FP64
+// unit is what bounds the mixed-precision cell state; these run on the integer pipes,
+// every input class included (a hardware conversion kept for the rare classes was
+// still issued, predicated off, on the common path).  The rare classes sit in
+// functions of their own, so the common path is a test and a branch (zeros, common
+// in the species fields, are handled inline).  Both return what
+// the hardware conversion (round to nearest even, subnormals kept) returns for every
+// non-NaN input; a NaN converts to a quiet NaN with the same sign and the leading
+// payload bits.
 
 // binary32 -> binary64 (exact).  Normal numbers: the 8-bit exponent is rebiased
-// (127 -> 1023) and the 23 mantissa bits become the top of the 52; zeros keep their sign.
+// (127 -> 1023) and the 23 mantissa bits become the top of the 52; zeros keep their
+// sign; a subnormal a 2^-149 is normalised at its leading bit.
+__device__ __noinline__ double f2d_rare(unsigned u) {
+    const unsigned a = u & 0x7fffffffu, sg = u & 0x80000000u;
+    if (a == 0u) return __hiloint2double((int)sg, 0);
+    if (a >= 0x7f800000u)                            // infinity, or NaN (quieted)
+        return __hiloint2double((int)(sg | 0x7ff00000u | (a == 0x7f800000u ? 0u : 0x00080000u) | ((a & 0x7fffffu) >> 3)),
+                                (int)(a << 29));
+    const int lz = __clz(a);                         // 9 .. 31: leading bit at 31 - lz, value 2^(-118 - lz) (1.f)
+    const unsigned f = (a << lz) << 1;               // fraction bits below it, left-aligned
+    return __hiloint2double((int)(sg | ((unsigned)(905 - lz) << 20) | (f >> 12)), (int)(f << 20));
+}
 __device__ __forceinline__ double f2d(float x) {
     const unsigned u = __float_as_uint(x);
     const unsigned a = u & 0x7fffffffu;
-    if (a - 0x00800000u >= 0x7f000000u) {           // zero, subnormal, infinity or NaN
-        if (a == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
-        return (double)x;
+    if (a - 0x00800000u >= 0x7f000000u) {            // zero, subnormal, infinity or NaN
+        if (a == 0u) return __hiloint2double((int)u, 0);
+        return f2d_rare(u);
     }
     return __hiloint2double((int)(((a >> 3) + (896u << 20)) | (u & 0x80000000u)), (int)(a << 29));
 }
@@ -115,13 +133,28 @@ __device__ __forceinline__ double f2d(float x) {
 // binary64 -> binary32, round to nearest even.  For 2^-126 <= |x| < 2^128 the exponent
 // is rebiased (1023 -> 127), the top 23 of the 52 mantissa bits are kept and the 29
 // below them rounded; a carry out of the mantissa is the next binade (or infinity),
-// as in IEEE rounding.  |x| < 2^-150 rounds to a signed zero.
+// as in IEEE rounding.  Below 2^-126 the 53-bit significand is shifted onto the
+// subnormal grid (2^-149) and rounded the same way (|x| <= 2^-150 gives a signed
+// zero); from 2^128 on the result is infinity.
+__device__ __noinline__ float d2f_rare(unsigned hi, unsigned lo) {
+    const unsigned e = (hi >> 20) & 0x7ffu, sg = hi & 0x80000000u;
+    if (e >= 1151u) {                                // |x| >= 2^128, infinity or NaN
+        const bool nan = e == 2047u && ((hi & 0xfffffu) | lo) != 0u;
+        return __uint_as_float(sg | 0x7f800000u | (nan ? 0x00400000u | ((hi & 0xfffffu) << 3) | (lo >> 29) : 0u));
+    }
+    if (e < 873u) return __uint_as_float(sg);        // |x| < 2^-150
+    const unsigned long long M = ((unsigned long long)((hi & 0xfffffu) | 0x100000u) << 32) | lo;
+    const unsigned sh = 926u - e;                    // 30 .. 53: M 2^(e - 1075) = (M >> sh) 2^-149
+    const unsigned long long q = M >> sh, rem = M & ((1ull << sh) - 1ull), half = 1ull << (sh - 1u);
+    const unsigned r = (unsigned)q + ((rem > half || (rem == half && (q & 1ull))) ? 1u : 0u);
+    return __uint_as_float(sg | r);
+}
 __device__ __forceinline__ float d2f(double x) {
     const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
     const unsigned e = (hi >> 20) & 0x7ffu;
     if (e - 897u >= 254u) {                          // outside [2^-126, 2^128)
-        if (e <= 872u) return __uint_as_float(hi & 0x80000000u);
-        return (float)x;
+        if (e < 873u) return __uint_as_float(hi & 0x80000000u);   // |x| < 2^-150 (zero included)
+        return d2f_rare(hi, lo);
     }
     // (hi:lo) << 3: the low nine exponent bits and the top 23 mantissa bits; the
     // rebias 1023 -> 127 is -896 = -384 (mod 512) in the nine-bit exponent field
@@ -130,6 +163,21 @@ __device__ __forceinline__ float d2f(double x) {
     t += (rem + (t & 1u)) > 0x10000000u ? 1u : 0u;   // above half, or half and odd
     return __uint_as_float(t | (hi & 0x80000000u));
 }
+
+// Comparisons of doubles on their bit patterns (integer pipes): non-negative doubles
+// order like their patterns, and an exponent field of all ones is an infinity or a NaN.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool finite64(double x) { return ((unsigned)__double2hiint(x) & 0x7ff00000u) != 0x7ff00000u; }
+// 0 < x < b, for a positive finite bound b (false for zero, negative, infinite and NaN x)
+__device__ __forceinline__ bool in_open_pos(double x, double b) {
+    return (unsigned long long)(dbits(x) - 1) < (unsigned long long)(dbits(b) - 1);
+}
+// |x| <= b, for b >= 0 (false for NaN x)
+__device__ __forceinline__ bool abs_le(double x, double b) {
+    return (unsigned long long)(dbits(x) & 0x7fffffffffffffffll) <= (unsigned long long)dbits(b);
+}
+// x >= b, for b > 0 and x not NaN
+__device__ __forceinline__ bool ge_pos(double x, double b) { return dbits(x) >= dbits(b); }
 
 // FP64 value of a bulk-type number and bulk-type value of an FP64 number.
 __device__ __forceinline__ double wide(float x) { return f2d(x); }
@@ -259,7 +307,7 @@ __device__ __forceinline__ double log64(double x) {
     const double r2 = r * r;
     const double q = fma(r, fma(r, fma(r, fma(r, -1.0 / 6.0, 0.2), -0.25), 1.0 / 3.0), -0.5);
     const double p = fma(r2, q, r);
-    const double md = (double)m;
+    const double md = f2d((float)m);                        // exact: |m| < 2^24
     const double head = fma(md, LN2_HI, __ldg(&g_log_tab[3 * j + 1]));
     const double tail = fma(md, LN2_LO, __ldg(&g_log_tab[3 * j + 2])) + p;
     return head + tail;
@@ -276,13 +324,16 @@ __device__ __forceinline__ double log_(double x) { return log64(x); }
 // ----------------------------------------------------------------------------- thermo
 
 // Mixture polynomial of the specific internal energy for one NASA range:
-// e(T) = e5 + T (e0 + T (e1 + T (e2 + T (e3 + T e4)))), cv(T) = de/dT.
+// e(T) = e5 + T (e0 + T (e1 + T (e2 + T (e3 + T e4)))), cv(T) = de/dT.  The cv
+// coefficients come in FP32 (cvf: the Newton update's derivative, and the mixed
+// path's cv) and, if CV64, in FP64 (cv: the FP64 path's cv, gamma and c).
 struct MixPoly {
     double e[6];
     double cv[5];
+    float cvf[5];
 };
 
-template <int NS>
+template <int NS, bool CV64>
 __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double Rm, MixPoly &P) {
     double c[6] = {0, 0, 0, 0, 0, 0};
 #pragma unroll
@@ -298,61 +349,71 @@ __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (
     P.e[4] = c[4];
     P.e[5] = c[5];
     // cv = (c0 - Rm) + 2 c1 T + 3 c2 T^2 + 4 c3 T^3 + 5 c4 T^4
-    P.cv[0] = c[0] - Rm;
-    P.cv[1] = 2.0 * c[1];
-    P.cv[2] = 3.0 * c[2];
-    P.cv[3] = 4.0 * c[3];
-    P.cv[4] = 5.0 * c[4];
+    if (CV64) {
+        P.cv[0] = P.e[0];
+        P.cv[1] = 2.0 * c[1];
+        P.cv[2] = 3.0 * c[2];
+        P.cv[3] = 4.0 * c[3];
+        P.cv[4] = 5.0 * c[4];
+    }
+    P.cvf[0] = d2f(P.e[0]);
+    P.cvf[1] = 2.0f * d2f(c[1]);
+    P.cvf[2] = 3.0f * d2f(c[2]);
+    P.cvf[3] = 4.0f * d2f(c[3]);
+    P.cvf[4] = 5.0f * d2f(c[4]);
 }
 
-__device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
+// cv(T) of the mixture polynomial P in FP32 (relative error a few 1e-7).
+__device__ __forceinline__ float mix_cvf(const MixPoly &P, float T) {
+    return fmaf(T, fmaf(T, fmaf(T, fmaf(T, P.cvf[4], P.cvf[3]), P.cvf[2]), P.cvf[1]), P.cvf[0]);
+}
+
+__device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && ge_pos(T, M.Tmid)) ? 1 : 0; }
 
 // Newton solve of e(T) = e_target, warm-started from T, with e(T) = sum_s Y_s e_s(T)
 // and Rm = sum_s Y_s R/W_s; the weights may be mass fractions (energy per unit mass)
 // or partial densities (energy per unit volume, e_target = rho e: the same root, and
-// the polynomial P is then density-weighted).  Returns false if the
-// update did not fall below 1e-9 T (which leaves T within ~1e-16 T of the root,
-// see the tolerance below) within maxit iterations.  On return P holds the mixture
-// polynomial of the range containing T.
-template <int NS>
+// the polynomial P is then density-weighted).  The residual is FP64; the derivative
+// cv is the FP32 polynomial, whose relative error (a few 1e-7) only sets the
+// convergence rate, not the root.  Returns false if the update did not fall below
+// 1e-9 T (which leaves T within ~1e-16 T of the root, see the tolerance below) within
+// maxit iterations.  On return P holds the mixture polynomial of the range containing T.
+template <int NS, bool CV64>
 __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
                                          double &T, int maxit, MixPoly &P) {
-    int r = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
-    mix_poly<NS>(M, r, Y, Rm, P);
+    int r = nasa_range_of(M, T);
+    mix_poly<NS, CV64>(M, r, Y, Rm, P);
     double e5 = P.e[5] - e_target;
     // Stop once the update just applied is below 1e-9 T: the iteration contracts the
-    // error by the FP32 reciprocal's ~6e-8 per step (plus a quadratic term), so the
+    // error by the FP32 derivative's few 1e-7 per step (plus a quadratic term), so the
     // updated T is then within ~1e-16 T of the root, and a further step (the
     // |dT| <= 1e-13 T test of the definition) would move it by less than that.
     const double tol = 1.0e-9 * fabs(T);
     for (int it = 0; it < maxit; ++it) {
-        const int rn = (M.two_ranges && T >= M.Tmid) ? 1 : 0;
+        const int rn = nasa_range_of(M, T);
         if (rn != r) {
             r = rn;
-            mix_poly<NS>(M, r, Y, Rm, P);
+            mix_poly<NS, CV64>(M, r, Y, Rm, P);
             e5 = P.e[5] - e_target;
         }
         // residual e(T) - e_target with the target folded into the constant term
         const double res = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), e5);
-        const double cv = fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
-        // The root is fixed by e(T) = e_target alone; an FP32 reciprocal of cv only
-        // perturbs the convergence rate (by ~1e-7 per step), not the converged T.
-        const double dT = res * f2d(__frcp_rn(d2f(cv)));
+        const double dT = res * f2d(__frcp_rn(mix_cvf(P, d2f(T))));
         T = T - dT;
-        if (fabs(dT) <= tol) {
-            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS>(M, nasa_range_of(M, T), Y, Rm, P);
+        if (abs_le(dT, tol)) {
+            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS, CV64>(M, nasa_range_of(M, T), Y, Rm, P);
             return true;
         }
     }
     return false;
 }
 
-// cv(T) of the mixture polynomial P (J/kg/K).
+// cv(T) of the mixture polynomial P in FP64 (needs CV64).
 __device__ __forceinline__ double mix_cv(const MixPoly &P, double T) {
     return fma(T, fma(T, fma(T, fma(T, P.cv[4], P.cv[3]), P.cv[2]), P.cv[1]), P.cv[0]);
 }
 
-__device__ __forceinline__ int nasa_range(const MechDev &M, double T) { return (M.two_ranges && T >= M.Tmid) ? 1 : 0; }
+__device__ __forceinline__ int nasa_range(const MechDev &M, double T) { return nasa_range_of(M, T); }
 
 // h_s/RT of species s.
 __device__ __forceinline__ double h_RT(const MechDev &M, int r, int s, double T, double invT) {

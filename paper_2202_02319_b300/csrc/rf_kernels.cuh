@@ -58,10 +58,16 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
         for (int k = 0; k < nrc; ++k) cf *= sCb[M.reac[j][k] * stride];
         R q = cf;
         if (M.rev[j]) {
-            // k_f (cf / k_f - prod_prod (C G) prod_reac (1/G)) with the reverse term in FP64
-            double pr = npd > 0 ? sP[M.prod[j][0] * stride] : 1.0;
-            for (int k = 1; k < npd; ++k) pr *= sP[M.prod[j][k] * stride];
-            for (int k = 0; k < nrc; ++k) pr *= sRr[M.reac[j][k] * stride];
+            // k_f (cf / k_f - prod_prod (C G) prod_reac (1/G)) with the reverse term in FP64;
+            // a loop (not unrolled), so that no multiplication is issued for absent factors
+            const int nf = M.n_revf[j];
+            auto fac = [&](int k) {
+                const int e = M.revf[j][k];
+                return e < 16 ? sP[e * stride] : sRr[(e - 16) * stride];
+            };
+            double pr = nf > 0 ? fac(0) : 1.0;
+#pragma unroll 1
+            for (int k = 1; k < nf; ++k) pr *= fac(k);
             q = narrow<R>(fma(-wide(kf), pr, wide(cf)));
         }
         for (int k = 0; k < M.n_net[j]; ++k) {
@@ -148,8 +154,8 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
     R *sW = (R *)(sRr + NS * B);
     R *sD = sW + NS * B;
     R *sCb = sizeof(R) == 8 ? (R *)sC : sD + NS * B;
-    __shared__ double s_laser[2];
-    __shared__ double s_red[3][32];
+    __shared__ double s_laser[5];
+    __shared__ R s_red[3][32];
 
     const int tid = threadIdx.x;
     const long long n = m.n;
@@ -165,6 +171,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         else norm = m.las[0] / (two_pi * two_pi * m.las[4] * m.las[4] * m.las[4] * m.las[6]);
         s_laser[0] = norm * exp(-0.5 * tt * tt);
         s_laser[1] = -0.5 / (m.las[4] * m.las[4]);
+        for (int d = 0; d < 3; ++d) s_laser[2 + d] = fma(0.5, m.h[d], -m.las[1 + d]);   // centre of cell 0 - x0
     }
     __syncthreads();
 
@@ -186,17 +193,18 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         double rhoRm = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) rhoRm = fma(rs[s], M.RW[s], rhoRm);
-        const double Rm = rhoRm * irho;
         const double rho_e = fma(-0.5 * irho, fma(mx, mx, fma(my, my, mz * mz)), E);
         double T = m.T[cell];
         MixPoly P;
-        const bool ok = newton_T<NS>(M, rs, rhoRm, rho_e, T, newton_maxit, P);
+        const bool ok = newton_T<NS, sizeof(R) == 8>(M, rs, rhoRm, rho_e, T, newton_maxit, P);
         if (!ok) flag_error(m, ST_NEWTON, cell);
-        if (!(rho > 0.0) || !(T > 0.0) || !(T < T_MAX_ADMISSIBLE)) {
-            if (isfinite(rho) && isfinite(T)) flag_error(m, ST_RANGE, cell);
+        // rho > 0 and 0 < T < T_MAX, compared on the bit patterns
+        const bool rho_pos = (unsigned long long)(dbits(rho) - 1) < 0x7ff0000000000000ull;
+        if (!rho_pos || !in_open_pos(T, T_MAX_ADMISSIBLE)) {
+            if (finite64(rho) && finite64(T)) flag_error(m, ST_RANGE, cell);
             else flag_error(m, ST_NONFINITE, cell);
         }
-        if (!isfinite(E) || !isfinite(mx) || !isfinite(my) || !isfinite(mz)) flag_error(m, ST_NONFINITE, cell);
+        if (!finite64(E) || !finite64(mx) || !finite64(my) || !finite64(mz)) flag_error(m, ST_NONFINITE, cell);
         const R irhob = narrow<R>(irho);
         R ub, vb, wb;
         if constexpr (sizeof(R) == 4) {
@@ -217,25 +225,33 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const int rng = nasa_range(M, T);
         const double invT = rcp64(T);
         const double lnT = log64(T);
-        const double cv = mix_cv(P, T) * irho;           // P is density-weighted
-        const double cp = cv + Rm;
-        R pb, c;
+        R pb, c, cpb, irmb, Wbarb;                        // P is density-weighted
         if constexpr (sizeof(R) == 4) {
-            // bulk quantities of the mixed path: gamma, c and p from FP32 factors
-            const float Tf = d2f(T), Rmf = d2f(Rm);
+            // bulk quantities of the mixed path in FP32: R_m, cv from the FP32 mixture
+            // polynomial, cp, p, gamma and c, 1 / R_m and the mean molar mass
+            const float Tf = d2f(T);
+            const float Rmf = d2f(rhoRm) * irhob;
+            const float cvf = mix_cvf(P, Tf) * irhob;
+            cpb = cvf + Rmf;
             pb = d2f(rho) * (Rmf * Tf);
-            c = sqrtf(d2f(cp) * rcp(d2f(cv)) * (Rmf * Tf));
+            c = sqrtf(cpb * rcp(cvf) * (Rmf * Tf));
+            irmb = rcp(Rmf);
+            Wbarb = (float)RU * irmb;
         } else {
+            const double Rm = rhoRm * irho;
+            const double cv = mix_cv(P, T) * irho;
+            const double cp = cv + Rm;
             pb = rho * Rm * T;
-            c = sqrt_((R)(cp / cv) * (R)(Rm * T));
+            c = sqrt_((cp / cv) * (Rm * T));
+            cpb = cp;
+            irmb = rcp64(Rm);
+            Wbarb = RU * irmb;
         }
-        const double irm = rcp64(Rm);
-        const double Wbar = RU * irm;
         R *Q = (R *)m.Q;
         Q[Q_U * n + cell] = ub;
         Q[Q_V * n + cell] = vb;
         Q[Q_W * n + cell] = wb;
-        const R Tb = narrow<R>(T), invTb = narrow<R>(invT), irmb = narrow<R>(irm);
+        const R Tb = narrow<R>(T), invTb = narrow<R>(invT);
         Q[Q_P * n + cell] = pb;
         Q[Q_C * n + cell] = c;
         Q[Q_T * n + cell] = Tb;
@@ -251,7 +267,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
                                     sD + tid, B);
         R mu, lam, Dc[NS], Dmax;
-        transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), narrow<R>(Wbar), X, mu, lam, Dc, Dmax);
+        transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
         Q[Q_MU * n + cell] = mu;
         Q[Q_LAM * n + cell] = lam;
 #pragma unroll
@@ -276,15 +292,20 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             const int k = (int)(cell / nxy);
             const long long rem = cell - (long long)k * nxy;
             const int j = (int)(rem / m.nx), i = (int)(rem - (long long)j * m.nx);
-            const double dx = fma((double)i, m.h[0], fma(0.5, m.h[0], -m.las[1]));
-            const double dy = fma((double)j, m.h[1], fma(0.5, m.h[1], -m.las[2]));
-            double r2 = fma(dx, dx, dy * dy);
-            if (m.nz > 1) {
-                const double dz = fma((double)k, m.h[2], fma(0.5, m.h[2], -m.las[3]));
-                r2 = fma(dz, dz, r2);
+            // cell indices are below 2^24, so they convert exactly through FP32
+            const double dx = fma(f2d((float)i), m.h[0], s_laser[2]);
+            const double dy = fma(f2d((float)j), m.h[1], s_laser[3]);
+            const double dz = m.nz > 1 ? fma(f2d((float)k), m.h[2], s_laser[4]) : 0.0;
+            if (sizeof(R) == 8) {
+                double r2 = fma(dx, dx, dy * dy);
+                if (m.nz > 1) r2 = fma(dz, dz, r2);
+                qL = s_laser[0] * exp64(s_laser[1] * r2);
+            } else {
+                // mixed path: offsets from the cell centre in FP64, their squares in FP32
+                const float dxf = d2f(dx), dyf = d2f(dy), dzf = d2f(dz);
+                const float r2f = fmaf(dxf, dxf, fmaf(dyf, dyf, dzf * dzf));
+                qL = s_laser[0] * f2d(expf(d2f(s_laser[1]) * r2f));
             }
-            if (sizeof(R) == 8) qL = s_laser[0] * exp64(s_laser[1] * r2);
-            else qL = s_laser[0] * f2d(expf(d2f(s_laser[1] * r2)));
         }
         rhs[(NS + 3) * n + cell] = narrow<R>(qL);
         if (sizeof(R) == 4) {
@@ -293,21 +314,23 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         }
         if (m.want_rates) {
             R ac = 0;
-            if (m.nx > 1) ac += (fabs(ub) + c) * (R)m.invh[0];
-            if (m.ny > 1) ac += (fabs(vb) + c) * (R)m.invh[1];
-            if (m.nz > 1) ac += (fabs(wb) + c) * (R)m.invh[2];
+            if (m.nx > 1) ac += (fabs(ub) + c) * narrow<R>(m.invh[0]);
+            if (m.ny > 1) ac += (fabs(vb) + c) * narrow<R>(m.invh[1]);
+            if (m.nz > 1) ac += (fabs(wb) + c) * narrow<R>(m.invh[2]);
             r_ac = ac;
             if (!(m.flags & F_NO_VISCOUS)) {
-                const R nu = mu / (R)rho;
-                const R al = lam / ((R)rho * (R)cp);
+                const R rhob = narrow<R>(rho);
+                const R nu = mu / rhob;
+                const R al = lam / (rhob * cpb);
                 R d = nu > al ? nu : al;
                 r_df = Dmax > d ? Dmax : d;
             }
         }
     }
     if (m.want_rates) {
-        // block max (deterministic: max is exact), then one atomic per block
-        double a = r_ac, d = r_df, ch = r_ch;
+        // block max in the bulk type (deterministic: max is exact, and so is the
+        // widening to FP64), then one atomic per block
+        R a = r_ac, d = r_df, ch = r_ch;
         for (int o = 16; o > 0; o >>= 1) {
             a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
             d = fmax(d, __shfl_xor_sync(0xffffffffu, d, o));
@@ -326,9 +349,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                 d = fmax(d, s_red[1][q]);
                 ch = fmax(ch, s_red[2][q]);
             }
-            atomic_max_pos(&m.rates[0], a);
-            atomic_max_pos(&m.rates[1], d);
-            atomic_max_pos(&m.rates[2], ch);
+            atomic_max_pos(&m.rates[0], wide(a));
+            atomic_max_pos(&m.rates[1], wide(d));
+            atomic_max_pos(&m.rates[2], wide(ch));
         }
     }
 }
@@ -1375,7 +1398,7 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
         const double e = m.U[(NS + 3) * n + cell] * irho - 0.5 * (u * u + v * v + w * w);
         double T = m.T[cell];
         MixPoly P;
-        if (!newton_T<NS>(M, Y, Rm, e, T, newton_maxit, P)) flag_error(m, ST_NEWTON, cell);
+        if (!newton_T<NS, true>(M, Y, Rm, e, T, newton_maxit, P)) flag_error(m, ST_NEWTON, cell);
         m.T[cell] = T;
         const int rng = nasa_range(M, T);
         const double invT = 1.0 / T, lnT = log(T);
