@@ -458,6 +458,13 @@ static void set_laser(Member &m, const rf_laser *L) {
         m.las[4] = L->sigma_r;
         m.las[5] = L->t0;
         m.las[6] = L->sigma_t;
+        // the time-independent factors of the source, once on the host
+        const double two_pi = 6.283185307179586, sr = L->sigma_r, st = L->sigma_t;
+        m.las_k[0] = m.nz == 1 ? L->E / (two_pi * std::sqrt(two_pi) * sr * sr * st)
+                               : L->E / (two_pi * two_pi * sr * sr * sr * st);
+        m.las_k[1] = -0.5 / (sr * sr);
+        m.las_k[2] = 1.0 / st;
+        for (int d = 0; d < 3; ++d) m.las_c0[d] = std::fma(0.5, m.h[d], -m.las[1 + d]);
     }
 }
 
@@ -970,7 +977,7 @@ struct EnsPath {
         if constexpr (sizeof(R) == 4) {
             const int sw = (int)walk_smem<R, NS>();
             CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
-            CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 2, MODE_STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
+            CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 2, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
         }
         const size_t sm_stage = std::max(std::max(e->smem_cell, e->smem_x), walk_smem<R, NS>());
         CUDA_TRY(cudaFuncSetAttribute(ens_stage_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
@@ -998,7 +1005,14 @@ struct EnsPath {
             LAUNCH_CHECK();
             ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM><<<e->nitems[2], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[2]), k);
             LAUNCH_CHECK();
-            ens_walk_kernel<R, UT, NS, 2, MODE_STAGE><<<e->nitems[3], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[3]), k);
+            if constexpr (sizeof(R) == 4) {
+                // FP32 bulk: the z sweep accumulates, an elementwise FP64 kernel applies the stage
+                ens_walk_kernel<R, UT, NS, 2, MODE_ACCUM><<<e->nitems[3], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[3]), k);
+                LAUNCH_CHECK();
+                ens_final_kernel<R, NS><<<e->nitems[0], 128, 0, s>>>(ens_dev(e, e->nitems[0]), k);
+            } else {
+                ens_walk_kernel<R, UT, NS, 2, MODE_STAGE><<<e->nitems[3], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[3]), k);
+            }
             LAUNCH_CHECK();
         }
         ens_end_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(ens_dev(e, 1));

@@ -78,6 +78,9 @@ struct Member {
     long long *bad_cell;
     double stage_a, stage_b, stage_c;   // U_out = a Un + b (U + dt L), time t + c dt
     double las[7];               // E, x0, y0, z0, sigma_r, t0, sigma_t
+    double las_k[3];             // E / ((2 pi)^2 sigma_r^3 sigma_t) (nz = 1: E / ((2 pi)^(3/2) sigma_r^2 sigma_t)),
+                                 // -1 / (2 sigma_r^2), 1 / sigma_t
+    double las_c0[3];            // centre of cell 0 minus x0, y0, z0
     int laser_on;
     int flags;
     int want_rates;

@@ -90,6 +90,23 @@ __device__ __forceinline__ void ens_x_phase(const MechDev &M, const EnsDev &E, i
     }
 }
 
+// Elementwise FP64 stage update over the cell-state work list (FP32-bulk path: every
+// sweep accumulates, then U_out = a Un + b (U + dt L), as in a single-grid stage).
+template <typename R, int NS>
+__device__ __forceinline__ void ens_final_phase(const EnsDev &E, int stage, Member &sm, int &s_ok) {
+    for (int w = blockIdx.x; w < E.nitems[0]; w += gridDim.x) {
+        const EnsItem it = E.items[0][w];
+        if (!load_member(E.tab[stage], it.m, sm, s_ok)) continue;
+        const long long cell = sm.c_lo + (long long)it.a * blockDim.x + threadIdx.x;
+        if (cell < sm.c_hi) {
+            R z[NS + 4];
+#pragma unroll
+            for (int v = 0; v < NS + 4; ++v) z[v] = 0;
+            cell_update<R, NS, MODE_STAGE>(sm, cell, z, R(0));
+        }
+    }
+}
+
 // y / z work items: (tile, segment); a tile is a 32 x 4 line group of the staged
 // walk in the FP32-bulk path and a block of 128 lines otherwise.
 template <typename R, typename UT, int NS, int DIR, int MODE>
@@ -108,8 +125,9 @@ __device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E
 
 // ----------------------------------------------------------------------------- one launch per phase
 
+// the register budget of the single-grid cell state: five blocks per SM
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) ens_cell_kernel(int mslot, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128, 5) ens_cell_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                        int stage) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -136,6 +154,13 @@ __global__ void __launch_bounds__(128) ens_walk_kernel(int mslot, const __grid_c
     __shared__ Member sm;
     __shared__ int s_ok;
     ens_walk_phase<R, UT, NS, DIR, MODE>(M, E, stage, smem_raw, sm, s_ok);
+}
+
+template <typename R, int NS>
+__global__ void __launch_bounds__(128) ens_final_kernel(const __grid_constant__ EnsDev E, int stage) {
+    __shared__ Member sm;
+    __shared__ int s_ok;
+    ens_final_phase<R, NS>(E, stage, sm, s_ok);
 }
 
 // Step prologue (run start): t from the caller, CFL, fixed dt, cleared maxima.
@@ -211,7 +236,10 @@ __device__ __forceinline__ bool grid_barrier(const EnsDev &E, int &s_flag) {
 
 // One RK stage of every member in one cooperative launch: cell state, (stage 1:
 // time step), x, y and z sweeps, (stage 3: clock advance), separated by grid
-// barriers.  Members must have nx, ny, nz > 1 (the z sweep performs the update).
+// barriers.  Members must have nx, ny, nz > 1 (the z sweep performs the update:
+// a separate elementwise phase would add a grid barrier and a pass at this
+// launch's occupancy, which the staged walk's shared memory holds at two blocks
+// per SM).
 template <typename R, int NS>
 __global__ void __launch_bounds__(128) ens_stage_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                         int stage) {

@@ -163,15 +163,14 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
     const bool chem_on = !(m.flags & F_NO_CHEM) && M.nr > 0;
     const bool laser_on = m.laser_on && !(m.flags & F_NO_LASER);
     if (tid == 0 && laser_on) {
+        // temporal factor at the stage time (the rest was formed on the host); the
+        // exponent is bounded so that the table exponential stays in its range
         const double t = m.t_from_host ? m.t_host : m.clock[0] + m.stage_c * m.clock[1];
-        const double tt = (t - m.las[5]) / m.las[6];
-        const double two_pi = 6.283185307179586;
-        double norm;
-        if (m.nz == 1) norm = m.las[0] / (two_pi * sqrt(two_pi) * m.las[4] * m.las[4] * m.las[6]);
-        else norm = m.las[0] / (two_pi * two_pi * m.las[4] * m.las[4] * m.las[4] * m.las[6]);
-        s_laser[0] = norm * exp(-0.5 * tt * tt);
-        s_laser[1] = -0.5 / (m.las[4] * m.las[4]);
-        for (int d = 0; d < 3; ++d) s_laser[2 + d] = fma(0.5, m.h[d], -m.las[1 + d]);   // centre of cell 0 - x0
+        const double tt = (t - m.las[5]) * m.las_k[2];
+        const double a = -0.5 * tt * tt;
+        s_laser[0] = a > -740.0 ? m.las_k[0] * exp64(a) : 0.0;
+        s_laser[1] = m.las_k[1];
+        for (int d = 0; d < 3; ++d) s_laser[2 + d] = m.las_c0[d];
     }
     __syncthreads();
 
