@@ -116,7 +116,7 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
 # DRAM = dram__bytes_read.sum + dram__bytes_write.sum (traffic grows with the cell
 # count, so a full 256^3 launch is the per-cell figure times 256^3).  None until
 # captured for the current kernel.
-CELL_STATE_MIXED_FP64_INST = (222.1, 112.3, 45.3)        # DFMA, DMUL, DADD per cell
+CELL_STATE_MIXED_FP64_INST = (219.8, 112.2, 34.3)        # DFMA, DMUL, DADD per cell
 CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 2 * CELL_STATE_MIXED_FP64_INST[0] + sum(CELL_STATE_MIXED_FP64_INST[1:])
 CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 307.6              # (100.13 + 171.99) MB / 884,736 cells
 

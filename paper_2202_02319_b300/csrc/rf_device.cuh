@@ -189,15 +189,14 @@ template <typename R> __device__ __forceinline__ R narrow(double x);
 template <> __device__ __forceinline__ float narrow<float>(double x) { return d2f(x); }
 template <> __device__ __forceinline__ double narrow<double>(double x) { return x; }
 
-// 1/x in FP64 by Newton-Raphson iteration r <- r + r (1 - x r) from an FP32 seed:
-// two steps take the seed's ~2^-23 relative error to rounding level.  For x whose
+// 1/x in FP64 from an FP32 seed r (correctly rounded, |e| <= 2^-24 with e = 1 - x r,
+// which one FMA gives exactly): 1/x = r / (1 - e) = r (1 + e + e^2 + ...), and
+// r + r (e + e^2) leaves e^3 <= 2^-72 relative, below FP64 rounding.  For x whose
 // magnitude lies in the FP32 normal range (densities, temperatures, gas constants).
 __device__ __forceinline__ double rcp64(double x) {
-    double r = f2d(__frcp_rn(d2f(x)));
-    double e = fma(-x, r, 1.0);
-    r = fma(r, e, r);
-    e = fma(-x, r, 1.0);
-    return fma(r, e, r);
+    const double r = f2d(__frcp_rn(d2f(x)));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
 }
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
@@ -256,7 +255,7 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     const double shifter = 6755399441055744.0;               // 1.5 * 2^52: rounds to an integer in the low bits
     const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
     const int k = __double2loint(t);
-    const double kd = t - shifter;
+    const double kd = f2d((float)k);                          // = t - shifter, exactly (|k| < 2^24)
     double r = fma(-kd, LN2_256_HI, x);
     r = fma(-kd, LN2_256_LO, r);
     const double r2 = r * r;
@@ -276,7 +275,7 @@ __device__ __forceinline__ double exp64(double x) {
     const double shifter = 6755399441055744.0;
     const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
     const int k = __double2loint(t);
-    const double kd = t - shifter;
+    const double kd = f2d((float)k);                          // = t - shifter, exactly (|k| < 2^24)
     double r = fma(-kd, LN2_256_HI, x);
     r = fma(-kd, LN2_256_LO, r);
     const double p = fma(r, fma(r, fma(r, fma(r, 1.0 / 24.0, 1.0 / 6.0), 0.5), 1.0), 1.0);
@@ -336,16 +335,19 @@ struct MixPoly {
     float cvf[5];
 };
 
+// The sums start from -Rm (the linear term) and from e5, the constant term of the
+// caller (zero, or the Newton solve's -e_target).
 template <int NS, bool CV64>
-__device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double Rm, MixPoly &P) {
-    double c[6] = {0, 0, 0, 0, 0, 0};
+__device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double Rm, double e5,
+                                         MixPoly &P) {
+    double c[6] = {-Rm, 0, 0, 0, 0, e5};
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) c[k] = fma(Y[s], M.ecR[r][s][k], c[k]);
     }
-    // sum_s Y_s (R/W_s) [a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6] - Rm T
-    P.e[0] = c[0] - Rm;
+    // sum_s Y_s (R/W_s) [a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6] - Rm T + e5
+    P.e[0] = c[0];
     P.e[1] = c[1];
     P.e[2] = c[2];
     P.e[3] = c[3];
@@ -385,8 +387,7 @@ template <int NS, bool CV64>
 __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
                                          double &T, int maxit, MixPoly &P) {
     int r = nasa_range_of(M, T);
-    mix_poly<NS, CV64>(M, r, Y, Rm, P);
-    double e5 = P.e[5] - e_target;
+    mix_poly<NS, CV64>(M, r, Y, Rm, -e_target, P);      // P.e[5] holds e5 - e_target
     // Stop once the update just applied is below 1e-9 T: the iteration contracts the
     // error by the FP32 derivative's few 1e-7 per step (plus a quadratic term), so the
     // updated T is then within ~1e-16 T of the root, and a further step (the
@@ -396,15 +397,14 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
         const int rn = nasa_range_of(M, T);
         if (rn != r) {
             r = rn;
-            mix_poly<NS, CV64>(M, r, Y, Rm, P);
-            e5 = P.e[5] - e_target;
+            mix_poly<NS, CV64>(M, r, Y, Rm, -e_target, P);
         }
         // residual e(T) - e_target with the target folded into the constant term
-        const double res = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), e5);
+        const double res = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), P.e[5]);
         const double dT = res * f2d(__frcp_rn(mix_cvf(P, d2f(T))));
         T = T - dT;
         if (abs_le(dT, tol)) {
-            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS, CV64>(M, nasa_range_of(M, T), Y, Rm, P);
+            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS, CV64>(M, nasa_range_of(M, T), Y, Rm, -e_target, P);
             return true;
         }
     }

@@ -262,11 +262,16 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             Q[(QL<NS>::X + s) * n + cell] = X[s];
             Q[(QL<NS>::H + s) * n + cell] = h_RT_bulk(M, rng, s, Tb, invTb) * mech_RW<R>(M, s) * Tb;
         }
-        if (chem_on)
+        // the FP64 Gibbs factors and the FP32 transport in one basic block, so that the
+        // scheduler can interleave the two pipes' work
+        R mu, lam, Dc[NS], Dmax;
+        if (chem_on) {
             chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
                                     sD + tid, B);
-        R mu, lam, Dc[NS], Dmax;
-        transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
+            transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
+        } else {
+            transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
+        }
         Q[Q_MU * n + cell] = mu;
         Q[Q_LAM * n + cell] = lam;
 #pragma unroll
