@@ -118,7 +118,7 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
 # captured for the current kernel.
 CELL_STATE_MIXED_FP64_INST = (219.8, 112.2, 34.3)        # DFMA, DMUL, DADD per cell
 CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 2 * CELL_STATE_MIXED_FP64_INST[0] + sum(CELL_STATE_MIXED_FP64_INST[1:])
-CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 307.6              # (100.13 + 171.99) MB / 884,736 cells
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 309.0              # (100.75 + 172.59) MB / 884,736 cells
 
 
 def cell_state_bytes(ns: int, rsize: int) -> int:

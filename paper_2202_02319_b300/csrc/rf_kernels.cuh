@@ -653,6 +653,32 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
     face_flux_core<R, NS, DIR>(m, st, G);
 }
 
+// Stage value of one conserved variable, U_out = a U^n + b (U^(k) + dt L), in FP64.
+// FP64 bulk: as written.  FP32 bulk: L carries FP32 precision, so the increment
+// b dt L is formed in FP32 (and widened exactly) and joined to a U^n + b U^(k) by two
+// FP64 FMAs; the first stage (a = 0, b = 1) is U^(k) + dt L without reading U^n.
+struct StageK {
+    double a, b, dt;
+    float dtf, bdtf;
+    bool euler;
+};
+__device__ __forceinline__ StageK stage_k(const Member &m, double dt) {
+    StageK k;
+    k.a = m.stage_a;
+    k.b = m.stage_b;
+    k.dt = dt;
+    k.euler = m.stage_a == 0.0 && m.stage_b == 1.0;
+    k.dtf = d2f(dt);
+    k.bdtf = d2f(m.stage_b * dt);
+    return k;
+}
+__device__ __forceinline__ double stage_value(const StageK &k, double L, double uk, double un) {
+    return k.euler ? fma(k.dt, L, uk) : fma(k.a, un, k.b * fma(k.dt, L, uk));
+}
+__device__ __forceinline__ double stage_value(const StageK &k, float L, double uk, double un) {
+    return k.euler ? uk + f2d(k.dtf * L) : fma(k.a, un, fma(k.b, uk, f2d(k.bdtf * L)));
+}
+
 template <typename R, int NS, int MODE>
 __device__ __forceinline__ void cell_update(const Member &m, long long cell, const R (&dG)[NS + 4], R ih) {
     constexpr int NV = NS + 4;
@@ -665,17 +691,14 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
 #pragma unroll
         for (int v = 0; v < NV; ++v) m.dUdt[v * n + cell] = wide(fma(dG[v], ih, rhs[v * n + cell]));
     } else {
-        const double dt = m.clock[1];
+        const StageK k = stage_k(m, m.clock[1]);
         const double *__restrict__ Uk = m.U;
         const double *__restrict__ Un = m.Un;
         double *__restrict__ Uo = m.Uout;
-        // first stage (a = 0, b = 1): U + dt L, the same value without U^n
-        const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
-            const double L = wide(fma(dG[v], ih, rhs[v * n + cell]));
-            Uo[v * n + cell] = euler ? fma(dt, L, Uk[v * n + cell])
-                                     : fma(m.stage_a, Un[v * n + cell], m.stage_b * fma(dt, L, Uk[v * n + cell]));
+            const R L = fma(dG[v], ih, rhs[v * n + cell]);
+            Uo[v * n + cell] = stage_value(k, L, Uk[v * n + cell], k.euler ? 0.0 : Un[v * n + cell]);
         }
     }
 }
@@ -968,6 +991,8 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
     const float ih = (float)m.invh[DIR];
     const long long lbase = (long long)x + (long long)o * so;
     const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
+    StageK sk;
+    if (MODE == MODE_STAGE) sk = stage_k(m, m.clock[1]);
     float Gp[NV];
     for (int f = c0; f <= c1; ++f) {
         // the update's inputs of cell f-1, loaded before the wait so their latency overlaps it
@@ -975,9 +1000,7 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
         const long long cell = lbase + (long long)(f - 1) * sd;
         float racc[NV];
         double uk[MODE == MODE_STAGE ? NV : 1], un[MODE == MODE_STAGE ? NV : 1];
-        double dt = 0.0;
         if (upd) {
-            if (MODE == MODE_STAGE) dt = m.clock[1];
             const float *__restrict__ rhs = (const float *)m.rhs;
 #pragma unroll
             for (int v = 0; v < NV; ++v) racc[v] = rhs[v * n + cell];
@@ -1018,8 +1041,7 @@ __device__ __forceinline__ void sweep_walk_staged_block(const MechDev &M, const 
                     const float L = fma(Gn[v] - Gp[v], ih, racc[v]);
                     if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
                     else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = wide(L);
-                    else m.Uout[v * n + cell] = euler ? fma(dt, wide(L), uk[v])
-                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, wide(L), uk[v]));
+                    else m.Uout[v * n + cell] = stage_value(sk, L, uk[v], un[v]);
                 }
             }
 #pragma unroll
@@ -1173,6 +1195,8 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
 
     const float ih = (float)m.invh[0];
     const bool euler = m.stage_a == 0.0 && m.stage_b == 1.0;     // first RK stage: U^n not needed
+    StageK sk;
+    if (MODE == MODE_STAGE) sk = stage_k(m, m.clock[1]);
     float Gc[NV];                      // lane 31's flux of the previous chunk
     stage_I(0);
     stage_V(0);
@@ -1185,13 +1209,11 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
         const long long cell = rowc + (F - 1);
         float racc[NV];
         double uk[MODE == MODE_STAGE ? NV : 1], un[MODE == MODE_STAGE ? NV : 1];
-        double dt = 0.0;
         if (upd) {
             const float *__restrict__ rhs = (const float *)m.rhs;
 #pragma unroll
             for (int v = 0; v < NV; ++v) racc[v] = rhs[v * n + cell];
             if (MODE == MODE_STAGE) {
-                dt = m.clock[1];
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     uk[v] = m.U[v * n + cell];
@@ -1239,8 +1261,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
                 const float L = fma(G[v] - Gl[v], ih, racc[v]);
                 if (MODE == MODE_ACCUM) ((float *)m.rhs)[v * n + cell] = L;
                 else if (MODE == MODE_RHS) m.dUdt[v * n + cell] = wide(L);
-                else m.Uout[v * n + cell] = euler ? fma(dt, wide(L), uk[v])
-                                                    : fma(m.stage_a, un[v], m.stage_b * fma(dt, wide(L), uk[v]));
+                else m.Uout[v * n + cell] = stage_value(sk, L, uk[v], un[v]);
             }
         }
         __syncwarp();
