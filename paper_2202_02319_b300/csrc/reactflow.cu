@@ -301,6 +301,14 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
         for (int k = 0; k < npd; ++k) M.revf[j][nf++] = M.prod[j][k];
         for (int k = 0; k < nrc; ++k) M.revf[j][nf++] = (int8_t)(M.reac[j][k] + 16);
         M.n_revf[j] = (int8_t)nf;
+        for (int k = 0; k < nrc; ++k) {
+            const int sp = M.reac[j][k];
+            M.dnu_reac[j][k] = (int8_t)(d->nu_r[j * ns + sp] - d->nu_f[j * ns + sp]);
+        }
+        for (int k = 0; k < npd; ++k) {
+            const int sp = M.prod[j][k];
+            M.dnu_prod[j][k] = (int8_t)(d->nu_r[j * ns + sp] - d->nu_f[j * ns + sp]);
+        }
     }
     *out = m;
     return RF_OK;
@@ -496,7 +504,7 @@ struct Path {
         const int B = 128;
         const long long nb = (m.c_hi - m.c_lo + B - 1) / B;
         if (nb <= 0) return RF_OK;
-        const size_t smem = cell_state_smem<R, NS>(B);
+        const size_t smem = cell_state_smem<R, NS>(B, m.want_rates != 0);
         ProfScope ps(c, PROF_CELL, s);
         cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mslot, m, c->newton_maxit);
         LAUNCH_CHECK();
@@ -995,7 +1003,7 @@ struct EnsPath {
         const int M = e->mslot;
         for (int k = 0; k < 3; ++k) {
             EnsDev E0 = ens_dev(e, e->nitems[0]);
-            ens_cell_kernel<R, NS><<<e->nitems[0], 128, e->smem_cell, s>>>(M, E0, k);
+            ens_cell_kernel<R, NS><<<e->nitems[0], 128, cell_state_smem<R, NS>(128, k == 0), s>>>(M, E0, k);
             LAUNCH_CHECK();
             if (k == 0) {
                 ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);

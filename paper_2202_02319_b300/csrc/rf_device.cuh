@@ -50,6 +50,8 @@ struct MechDev {
     // factors of the reverse term k_f prod_prod (C G)_s prod_reac (1/G)_s: products
     // (species s) then reactants (s + 16), in that order
     int8_t n_revf[NRMAX], revf[NRMAX][6];
+    // net coefficient nu''_s - nu'_s of the species at each reactant / product position
+    int8_t dnu_reac[NRMAX][3], dnu_prod[NRMAX][3];
 };
 
 // Mechanisms in use live in constant-memory slots; kernels receive the slot

@@ -36,15 +36,15 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) 
 // Reversible mass-action rates.  Per-species inputs sit in per-thread
 // shared-memory columns (stride = block size) so the compact stoichiometry can
 // index species at run time:
-//   sC  = C_s (FP64 path; the mixed path keeps G_s there), sCb = C_s in the bulk type,
-//   sP  = C_s G_s and sRr = 1 / G_s (FP64), G_s = exp(g_s/RT) R T / p_atm,
+//   sCb = C_s in the bulk type, sP = C_s G_s and sRr = 1 / G_s (FP64),
+//   G_s = exp(g_s/RT) R T / p_atm, and (rates only) sG = G_s (FP64),
 // so that k_f / K_c,j * prod_s C_s^nu''_sj = k_f prod_prod (C G)_s prod_reac (1/G)_s,
 // i.e. the equilibrium constant costs one FP64 exponential per species rather than
 // per reaction, and the reverse rate stays in FP64.  sW accumulates
 // sum_j nu_sj q_j in the bulk type.  If want_rate, sD accumulates the diagonal of
 // d omega / d C and the function returns max_s |d omega_s / d rho_s|.
 template <typename R, int NS>
-__device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT, const double *__restrict__ sC,
+__device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT, const double *__restrict__ sG,
                                        const R *__restrict__ sCb, const double *__restrict__ sP,
                                        const double *__restrict__ sRr, R *__restrict__ sW, R *__restrict__ sD,
                                        int stride, bool want_rate) {
@@ -75,28 +75,32 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             sW[s * stride] = fma((R)M.net_nu[j][k], q, sW[s * stride]);
         }
         if (want_rate) {
-            // d q / d C_s: remove one factor at each position of the reactant / product lists
+            // d q / d C_s at each position of the reactant / product lists (a species
+            // repeated by its coefficient appears at as many positions): the forward term
+            // without that reactant factor, in the bulk type ...
+#pragma unroll 1
             for (int k = 0; k < nrc; ++k) {
                 R part = kf;
+#pragma unroll 1
                 for (int k2 = 0; k2 < nrc; ++k2)
                     if (k2 != k) part *= sCb[M.reac[j][k2] * stride];
                 const int s = M.reac[j][k];
-                R dn = 0;
-                for (int k3 = 0; k3 < M.n_net[j]; ++k3)
-                    if (M.net_sp[j][k3] == s) dn = (R)M.net_nu[j][k3];
-                sD[s * stride] = fma(dn, part, sD[s * stride]);
+                sD[s * stride] = fma((R)M.dnu_reac[j][k], part, sD[s * stride]);
             }
+            // ... and the reverse term k_f G_s prod_(other products) (C G) prod_reac (1/G)
+            // in FP64, the reactant factors shared by every product position
             if (M.rev[j]) {
+                double kr = wide(kf);
+#pragma unroll 1
+                for (int k2 = 0; k2 < nrc; ++k2) kr *= sRr[M.reac[j][k2] * stride];
+#pragma unroll 1
                 for (int k = 0; k < npd; ++k) {
                     const int s = M.prod[j][k];
-                    double part = sizeof(R) == 4 ? wide(kf) * sC[s * stride] : wide(kf) / sRr[s * stride];
+                    double part = kr * sG[s * stride];
+#pragma unroll 1
                     for (int k2 = 0; k2 < npd; ++k2)
                         if (k2 != k) part *= sP[M.prod[j][k2] * stride];
-                    for (int k2 = 0; k2 < nrc; ++k2) part *= sRr[M.reac[j][k2] * stride];
-                    R dn = 0;
-                    for (int k3 = 0; k3 < M.n_net[j]; ++k3)
-                        if (M.net_sp[j][k3] == s) dn = (R)M.net_nu[j][k3];
-                    sD[s * stride] = fma(-dn, narrow<R>(part), sD[s * stride]);
+                    sD[s * stride] = fma(-(R)M.dnu_prod[j][k], narrow<R>(part), sD[s * stride]);
                 }
             }
         }
@@ -115,32 +119,33 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
 // Per-species chemistry inputs of one cell (see chemistry()).
 template <typename R, int NS>
 __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, const double (&rs)[NS], double T, double invT,
-                                                 double lnT, double *sC, R *sCb, double *sP, double *sRr, R *sW, R *sD,
-                                                 int stride) {
+                                                 double lnT, double *sG, R *sCb, double *sP, double *sRr, R *sW, R *sD,
+                                                 int stride, bool rates) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const double C = rs[s] * M.invW[s];
         double G, iG;
         exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
-        if (sizeof(R) == 4) {
-            sC[s * stride] = G;
-            sCb[s * stride] = narrow<R>(C);
-        } else {
-            sC[s * stride] = C;
-        }
+        sCb[s * stride] = narrow<R>(C);
         sP[s * stride] = C * G;
         sRr[s * stride] = iG;
         sW[s * stride] = (R)0;
-        sD[s * stride] = (R)0;
+        if (rates) {
+            sG[s * stride] = G;
+            sD[s * stride] = (R)0;
+        }
     }
 }
 
 // ----------------------------------------------------------------------------- cell state
 
-// Dynamic shared memory of one cell-state block of B threads.
+// Dynamic shared memory of one cell-state block of B threads: per species and thread
+// C G and 1/G (FP64), the rate accumulator and C (bulk type); with rates (the time-step
+// evaluation) also G (FP64) and the rate-Jacobian diagonal (bulk type), placed last so
+// that launches without rates need less.
 template <typename R, int NS>
-__host__ __device__ constexpr size_t cell_state_smem(int B) {
-    return (size_t)B * NS * (3 * sizeof(double) + 2 * sizeof(R) + (sizeof(R) == 4 ? sizeof(R) : 0));
+__host__ __device__ constexpr size_t cell_state_smem(int B, bool rates = true) {
+    return (size_t)B * NS * (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(double) + sizeof(R) : 0));
 }
 
 template <typename R, int NS>
@@ -148,12 +153,13 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                                                  int newton_maxit) {
     constexpr int NV = NS + 4;
     const int B = blockDim.x;
-    double *sC = (double *)smem_raw;
-    double *sP = sC + NS * B;
+    // sP, sRr (FP64), sW, sCb (bulk type) | rates only: sG (FP64), sD (bulk type)
+    double *sP = (double *)smem_raw;
     double *sRr = sP + NS * B;
     R *sW = (R *)(sRr + NS * B);
-    R *sD = sW + NS * B;
-    R *sCb = sizeof(R) == 8 ? (R *)sC : sD + NS * B;
+    R *sCb = sW + NS * B;
+    double *sG = (double *)(sCb + NS * B);
+    R *sD = (R *)(sG + NS * B);
     __shared__ double s_laser[5];
     __shared__ R s_red[3][32];
 
@@ -266,8 +272,8 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         // scheduler can interleave the two pipes' work
         R mu, lam, Dc[NS], Dmax;
         if (chem_on) {
-            chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
-                                    sD + tid, B);
+            chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
+                                    sD + tid, B, m.want_rates != 0);
             transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
         } else {
             transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
@@ -279,7 +285,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 
         R *rhs = (R *)m.rhs;
         if (chem_on) {
-            r_ch = chemistry<R, NS>(M, lnT, invT, sC + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
+            r_ch = chemistry<R, NS>(M, lnT, invT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
                                     m.want_rates != 0);
 #pragma unroll
             for (int s = 0; s < NS; ++s) rhs[s * n + cell] = sW[s * B + tid] * mech_W<R>(M, s);
@@ -361,7 +367,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 }
 
 template <typename R, int NS>
-__global__ void __launch_bounds__(128, 5) cell_state_kernel(int mslot, const __grid_constant__ Member m,
+// mixed path: six blocks per SM in launches without rates (27.6 KB of shared memory
+// per block at 9 species); the FP64 path keeps five (more would spill heavily)
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 5) cell_state_kernel(int mslot, const __grid_constant__ Member m,
                                                          int newton_maxit) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1433,7 +1441,7 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
         double hrr = 0.0;
         if (M.nr > 0) {
             chemistry_inputs<double, NS>(M, rng, rs, T, invT, lnT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid,
-                                         sD + tid, B);
+                                         sD + tid, B, false);
             chemistry<double, NS>(M, lnT, invT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B, false);
 #pragma unroll
             for (int s = 0; s < NS; ++s) hrr -= hs[s] * sW[s * B + tid] * M.W[s];
