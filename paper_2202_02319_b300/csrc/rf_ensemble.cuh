@@ -125,9 +125,10 @@ __device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E
 
 // ----------------------------------------------------------------------------- one launch per phase
 
-// the register budget of the single-grid cell state: five blocks per SM
+// the register budgets of the single-grid kernels: cell state six blocks per SM (FP32
+// bulk; five in the FP64 path), staged x sweep five
 template <typename R, int NS>
-__global__ void __launch_bounds__(128, 5) ens_cell_kernel(int mslot, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 5) ens_cell_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                        int stage) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(128, 5) ens_cell_kernel(int mslot, const __gri
 }
 
 template <typename R, typename UT, int NS, int MODE>
-__global__ void __launch_bounds__(128) ens_x_kernel(int mslot, const __grid_constant__ EnsDev E,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 5 : 3) ens_x_kernel(int mslot, const __grid_constant__ EnsDev E,
                                                     int stage) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
