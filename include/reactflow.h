@@ -290,8 +290,12 @@ int rf_probe_peak(int kind, double *tflops, rf_stream s);
  * mixed-precision kernels build from integer operations: fn 3: y[i] = the
  * kernels' binary32 rounding of x[i], y2[i] = the hardware's (both widened
  * exactly to double); fn 4: the low 32 bits of each x[i] are a binary32 pattern
- * f, y[i] = the kernels' widening of f, y2[i] = the hardware's.  x, y, y2 (fn 0,
- * 3, 4; may be NULL otherwise): device arrays of n doubles (caller-owned).
+ * f, y[i] = the kernels' widening of f, y2[i] = the hardware's.  And of the
+ * mixed path's FP64 functions, whose results feed FP32 quantities: fn 5: the
+ * exponential pair y[i] = exp(x[i]), y2[i] = exp(-x[i]) to 2e-13 relative for
+ * |x| <= 700; fn 6: y[i] = ln x[i] to 5e-14 absolute for normal x > 0 with a
+ * binary exponent of magnitude at most 64.  x, y, y2 (fn 0, 3, 4, 5; may be NULL
+ * otherwise): device arrays of n doubles (caller-owned).
  * Asynchronous on s; RF_EINVAL for an unknown fn, n < 0 or a missing array with
  * n > 0. */
 int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s);

@@ -1553,6 +1553,8 @@ __global__ void math_probe_kernel(int fn, const double *x, double *y, double *y2
     if (fn == 0) exp_pair(x[i], y[i], y2[i]);
     else if (fn == 1) y[i] = log64(x[i]);
     else if (fn == 2) y[i] = exp64(x[i]);
+    else if (fn == 5) exp_pair_mixed(x[i], y[i], y2[i]);
+    else if (fn == 6) y[i] = log64_mixed(x[i]);
     else if (fn == 3) {
         y[i] = (double)d2f(x[i]);
         y2[i] = (double)(float)x[i];
@@ -1564,7 +1566,7 @@ __global__ void math_probe_kernel(int fn, const double *x, double *y, double *y2
 }
 
 extern "C" int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, rf_stream s) {
-    if (fn < 0 || fn > 4 || n < 0 || (n > 0 && (!x || !y || ((fn == 0 || fn >= 3) && !y2))))
+    if (fn < 0 || fn > 6 || n < 0 || (n > 0 && (!x || !y || ((fn == 0 || (fn >= 3 && fn <= 5)) && !y2))))
         return fail(RF_EINVAL, "rf_probe_math: bad argument");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));

@@ -271,6 +271,27 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
     em = sm * (E - O);
 }
 
+// The mixed path's exponential pair.  Its Gibbs factors feed a reverse term that is
+// subtracted from an FP32 forward term, so a relative error of 2e-13 loses nothing
+// there: the same reduction without the low part of ln2/256 (which moves r by at most
+// |x| 3.4e-17) and E = 1 + r^2/2 (the dropped r^4/24 is below 1.4e-13); still FP64.
+__device__ __forceinline__ void exp_pair_mixed(double x, double &ep, double &em) {
+    const double shifter = 6755399441055744.0;
+    const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
+    const int k = __double2loint(t);
+    const double kd = f2d((float)k);                          // = t - shifter, exactly (|k| < 2^24)
+    const double r = fma(-kd, LN2_256_HI, x);
+    const double r2 = r * r;
+    const double E = fma(r2, 0.5, 1.0);
+    const double O = fma(r * r2, 1.0 / 6.0, r);
+    const int j = k & 255, m = min(max(k >> 8, -1020), 1020);
+    const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[256 + j]);
+    const double sp = __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp));
+    const double sm = __hiloint2double(__double2hiint(tm) - (m << 20), __double2loint(tm));
+    ep = sp * (E + O);
+    em = sm * (E - O);
+}
+
 // exp(x) alone from the same reduction and table: exp(r) by its Taylor polynomial
 // through r^4 (first omitted term r^5/120 < 4e-17 relative), one table factor.
 __device__ __forceinline__ double exp64(double x) {
@@ -315,6 +336,22 @@ __device__ __forceinline__ double log64(double x) {
     const double head = fma(md, LN2_HI, __ldg(&g_log_tab[3 * j + 1]));
     const double tail = fma(md, LN2_LO, __ldg(&g_log_tab[3 * j + 2])) + p;
     return head + tail;
+}
+
+// The mixed path's ln T (its arguments of the Gibbs factors and FP32 forward rates):
+// the same table and reduction without the low parts of ln 2 and ln F and without the
+// r^6/6 term, absolute error below 5e-14 for normal x > 0 with |exponent| <= 64.
+__device__ __forceinline__ double log64_mixed(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const int m = ((hi >> 20) & 0x7ff) - 1023;
+    const int mant = hi & 0xfffff;
+    const int j = (mant + (1 << 13)) >> 14;
+    const double y = __hiloint2double(0x3ff00000 | mant, lo);
+    const double F = __hiloint2double(0x3ff00000 + (j << 14), 0);
+    const double r = (y - F) * __ldg(&g_log_tab[3 * j]);
+    const double q = fma(r, fma(r, fma(r, 0.2, -0.25), 1.0 / 3.0), -0.5);
+    const double p = fma(r * r, q, r);
+    return fma(f2d((float)m), LN2_HI, __ldg(&g_log_tab[3 * j + 1])) + p;
 }
 
 // FP64 instances of the bulk-type helpers (transport and chemistry of the FP64

@@ -125,7 +125,8 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
     for (int s = 0; s < NS; ++s) {
         const double C = rs[s] * M.invW[s];
         double G, iG;
-        exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
+        if (sizeof(R) == 4) exp_pair_mixed(lnG(M, rng, s, T, invT, lnT), G, iG);
+        else exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
         sCb[s * stride] = narrow<R>(C);
         sP[s * stride] = C * G;
         sRr[s * stride] = iG;
@@ -229,7 +230,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
 
         const int rng = nasa_range(M, T);
         const double invT = rcp64(T);
-        const double lnT = log64(T);
+        const double lnT = sizeof(R) == 4 ? log64_mixed(T) : log64(T);
         R pb, c, cpb, irmb, Wbarb;                        // P is density-weighted
         if constexpr (sizeof(R) == 4) {
             // bulk quantities of the mixed path in FP32: R_m, cv from the FP32 mixture

@@ -253,6 +253,16 @@ def probe_exp(x, y, stream=None):
     _check(_lib.rf_probe_math(2, _ptr(x), _ptr(y), None, int(x.numel()), _stream(stream)), "rf_probe_math")
 
 
+def probe_exp_pair_mixed(x, ep, em, stream=None):
+    """ep = exp(x), em = exp(-x) by the mixed path's FP64 exponential pair (device tensors)."""
+    _check(_lib.rf_probe_math(5, _ptr(x), _ptr(ep), _ptr(em), int(x.numel()), _stream(stream)), "rf_probe_math")
+
+
+def probe_log_mixed(x, y, stream=None):
+    """y = ln x by the mixed path's FP64 logarithm (device tensors)."""
+    _check(_lib.rf_probe_math(6, _ptr(x), _ptr(y), None, int(x.numel()), _stream(stream)), "rf_probe_math")
+
+
 def probe_d2f(x, y, y2, stream=None):
     """y = the kernels' binary32 rounding of x, y2 = the hardware's (float64 device tensors)."""
     _check(_lib.rf_probe_math(3, _ptr(x), _ptr(y), _ptr(y2), int(x.numel()), _stream(stream)), "rf_probe_math")

@@ -1,6 +1,7 @@
 """The FP64 elementary functions of the kernels (the exponential pair of G_s and
 1/G_s, the single exponential, the logarithm) against CUDA's functions (through
-torch) and numpy's."""
+torch) and numpy's; the mixed path's shorter exponential pair and logarithm
+against their stated bounds."""
 import numpy as np
 import pytest
 import torch
@@ -73,3 +74,29 @@ def test_single_exp64_within_a_few_ulp():
     torch.cuda.synchronize()
     assert float(np.max(np.abs(y.cpu().numpy() - np.exp(x)) / np.exp(x))) < 1e-15
     assert float(((y - torch.exp(xd)).abs() / torch.exp(xd)).max()) < 1e-15
+
+
+def test_mixed_exp_pair_within_2e_13():
+    from paper_2202_02319_b300 import native as nv
+    g = np.random.default_rng(12)
+    x = np.concatenate([g.uniform(-700.0, 700.0, 400_000), g.uniform(-1.0, 1.0, 200_000),
+                        g.uniform(-60.0, 60.0, 200_000), np.arange(-2000, 2001) * (np.log(2.0) / 256.0),
+                        [0.0, -0.0, 700.0, -700.0]])
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    ep, em = torch.empty_like(xd), torch.empty_like(xd)
+    nv.probe_exp_pair_mixed(xd, ep, em)
+    torch.cuda.synchronize()
+    for got, want in ((ep.cpu().numpy(), np.exp(x)), (em.cpu().numpy(), np.exp(-x))):
+        assert float(np.max(np.abs(got - want) / want)) < 2e-13
+
+
+def test_mixed_log_within_5e_14():
+    from paper_2202_02319_b300 import native as nv
+    g = np.random.default_rng(13)
+    x = np.concatenate([g.uniform(50.0, 1.0e5, 400_000), np.exp2(g.uniform(-60.0, 60.0, 200_000)),
+                        g.uniform(0.99, 1.01, 100_000), [1.0, 2.0, 0.5, 300.0, 1.0 + 1.0 / 128.0]])
+    xd = torch.as_tensor(x, dtype=torch.float64).cuda()
+    y = torch.empty_like(xd)
+    nv.probe_log_mixed(xd, y)
+    torch.cuda.synchronize()
+    assert float(np.max(np.abs(y.cpu().numpy() - np.log(x)))) < 5e-14
