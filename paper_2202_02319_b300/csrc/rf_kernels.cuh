@@ -33,6 +33,28 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) 
 
 // ----------------------------------------------------------------------------- chemistry
 
+// A finite FP64 (or FP32) value as an FP32 mantissa m with 1 <= |m| <= 2 and a binary
+// exponent e, value = m 2^e (m rounded to nearest by d2f; zero and subnormal inputs give
+// 2^-1023 or 2^-127 times a unit mantissa, i.e. a negligible value of the same sign).
+struct SplitF {
+    float m;
+    int e;
+};
+__device__ __forceinline__ SplitF split64(double d) {
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    SplitF r;
+    r.e = (int)((hi >> 20) & 0x7ffu) - 1023;
+    r.m = d2f(__hiloint2double((int)((hi & 0x800fffffu) | 0x3ff00000u), (int)lo));
+    return r;
+}
+__device__ __forceinline__ SplitF split32(float x) {
+    const unsigned u = __float_as_uint(x);
+    SplitF r;
+    r.e = (int)((u >> 23) & 0xffu) - 127;
+    r.m = __uint_as_float((u & 0x807fffffu) | 0x3f800000u);
+    return r;
+}
+
 // Reversible mass-action rates.  Per-species inputs sit in per-thread
 // shared-memory columns (stride = block size) so the compact stoichiometry can
 // index species at run time:
@@ -87,9 +109,38 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
                 const int s = M.reac[j][k];
                 sD[s * stride] = fma((R)M.dnu_reac[j][k], part, sD[s * stride]);
             }
-            // ... and the reverse term k_f G_s prod_(other products) (C G) prod_reac (1/G)
-            // in FP64, the reactant factors shared by every product position
-            if (M.rev[j]) {
+            // ... and the reverse term k_f G_s prod_(other products) (C G) prod_reac (1/G),
+            // the reactant factors shared by every product position.  FP64 path: in FP64.
+            // Mixed path: the factors span more than the FP32 range but the result only
+            // feeds the FP32 accumulator of a time-step estimate, so each factor is an
+            // FP32 mantissa in [1, 2] with an integer binary exponent (~3e-7 relative).
+            if (sizeof(R) == 4 && M.rev[j]) {
+                const SplitF f0 = split32(kf);
+                float krm = f0.m;
+                int kre = f0.e;
+#pragma unroll 1
+                for (int k2 = 0; k2 < nrc; ++k2) {
+                    const SplitF f = split64(sRr[M.reac[j][k2] * stride]);
+                    krm *= f.m;
+                    kre += f.e;
+                }
+#pragma unroll 1
+                for (int k = 0; k < npd; ++k) {
+                    const int s = M.prod[j][k];
+                    const SplitF g = split64(sG[s * stride]);
+                    float pm = krm * g.m;
+                    int pe = kre + g.e;
+#pragma unroll 1
+                    for (int k2 = 0; k2 < npd; ++k2)
+                        if (k2 != k) {
+                            const SplitF f = split64(sP[M.prod[j][k2] * stride]);
+                            pm *= f.m;
+                            pe += f.e;
+                        }
+                    const R part = (R)ldexpf(pm, max(min(pe, 300), -300));
+                    sD[s * stride] = fma(-(R)M.dnu_prod[j][k], part, sD[s * stride]);
+                }
+            } else if (M.rev[j]) {
                 double kr = wide(kf);
 #pragma unroll 1
                 for (int k2 = 0; k2 < nrc; ++k2) kr *= sRr[M.reac[j][k2] * stride];
