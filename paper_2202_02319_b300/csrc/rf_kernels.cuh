@@ -113,7 +113,8 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             // the reactant factors shared by every product position.  FP64 path: in FP64.
             // Mixed path: the factors span more than the FP32 range but the result only
             // feeds the FP32 accumulator of a time-step estimate, so each factor is an
-            // FP32 mantissa in [1, 2] with an integer binary exponent (~3e-7 relative).
+            // FP32 mantissa in [1, 2] with an integer binary exponent (~3e-7 relative), and
+            // G comes from 1/G, so that no FP64 copy of G is kept.
             if (sizeof(R) == 4 && M.rev[j]) {
                 const SplitF f0 = split32(kf);
                 float krm = f0.m;
@@ -127,9 +128,9 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
 #pragma unroll 1
                 for (int k = 0; k < npd; ++k) {
                     const int s = M.prod[j][k];
-                    const SplitF g = split64(sG[s * stride]);
-                    float pm = krm * g.m;
-                    int pe = kre + g.e;
+                    const SplitF ig = split64(sRr[s * stride]);        // G = 1 / (1/G)
+                    float pm = krm * __frcp_rn(ig.m);
+                    int pe = kre - ig.e;
 #pragma unroll 1
                     for (int k2 = 0; k2 < npd; ++k2)
                         if (k2 != k) {
@@ -183,7 +184,7 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
         sRr[s * stride] = iG;
         sW[s * stride] = (R)0;
         if (rates) {
-            sG[s * stride] = G;
+            if (sizeof(R) == 8) sG[s * stride] = G;
             sD[s * stride] = (R)0;
         }
     }
@@ -193,11 +194,12 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
 
 // Dynamic shared memory of one cell-state block of B threads: per species and thread
 // C G and 1/G (FP64), the rate accumulator and C (bulk type); with rates (the time-step
-// evaluation) also G (FP64) and the rate-Jacobian diagonal (bulk type), placed last so
-// that launches without rates need less.
+// evaluation) also the rate-Jacobian diagonal (bulk type) and, FP64 path, G (FP64),
+// placed last so that launches without rates need less.
 template <typename R, int NS>
 __host__ __device__ constexpr size_t cell_state_smem(int B, bool rates = true) {
-    return (size_t)B * NS * (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(double) + sizeof(R) : 0));
+    return (size_t)B * NS *
+           (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(R) + (sizeof(R) == 8 ? sizeof(double) : 0) : 0));
 }
 
 template <typename R, int NS>
@@ -205,13 +207,13 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                                                  int newton_maxit) {
     constexpr int NV = NS + 4;
     const int B = blockDim.x;
-    // sP, sRr (FP64), sW, sCb (bulk type) | rates only: sG (FP64), sD (bulk type)
+    // sP, sRr (FP64), sW, sCb (bulk type) | rates only: sD (bulk type), FP64 path sG (FP64)
     double *sP = (double *)smem_raw;
     double *sRr = sP + NS * B;
     R *sW = (R *)(sRr + NS * B);
     R *sCb = sW + NS * B;
-    double *sG = (double *)(sCb + NS * B);
-    R *sD = (R *)(sG + NS * B);
+    R *sD = sCb + NS * B;
+    double *sG = (double *)(sD + NS * B);
     __shared__ double s_laser[5];
     __shared__ R s_red[3][32];
 
