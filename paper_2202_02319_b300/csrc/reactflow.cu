@@ -223,7 +223,9 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             M.ec[r][s][3] = a[3] / 4.0;
             M.ec[r][s][4] = a[4] / 5.0;
             M.ec[r][s][5] = a[5];
+            // e_s = h_s - (R/W_s) T: the linear coefficient takes the -R/W_s
             for (int k = 0; k < 6; ++k) M.ecR[r][s][k] = M.ec[r][s][k] * M.RW[s];
+            M.ecR[r][s][0] = (M.ec[r][s][0] - 1.0) * M.RW[s];
             // ln G_s = g_s/RT + ln(R T / p_atm): the constant and the ln T coefficient absorb the second term
             M.gc[r][s][0] = a[0] - a[6] + std::log(RU / PATM);
             M.gc[r][s][1] = -a[1] / 2.0;

@@ -29,7 +29,7 @@ struct MechDev {
     double W[NSMAX], invW[NSMAX], RW[NSMAX];   // R/W_s
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
     double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
-    double ecR[2][NSMAX][6];                   // ec times R/W_s (mixture energy polynomial of the Newton solve)
+    double ecR[2][NSMAX][6];                   // e_s / T-powers: (a1 - 1) R/W_s, then ec times R/W_s (Newton solve)
     double gc[2][NSMAX][7];                    // ln G = g/RT + ln(RT/p_atm) = gc0 + T(gc1 + ... T gc4) + gc5/T + gc6 lnT
     float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
@@ -374,25 +374,24 @@ struct MixPoly {
     float cvf[5];
 };
 
-// The sums start from -Rm (the linear term) and from e5, the constant term of the
-// caller (zero, or the Newton solve's -e_target).
+// The species coefficients hold e_s = h_s - (R/W_s) T (the -R/W_s in the linear
+// term); the constant term's sum starts from e5 (the Newton solve's -e_target).
 template <int NS, bool CV64>
-__device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double Rm, double e5,
-                                         MixPoly &P) {
-    double c[6] = {-Rm, 0, 0, 0, 0, e5};
+__device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double e5, MixPoly &P) {
+    double c[6] = {0, 0, 0, 0, 0, e5};
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
 #pragma unroll
         for (int k = 0; k < 6; ++k) c[k] = fma(Y[s], M.ecR[r][s][k], c[k]);
     }
-    // sum_s Y_s (R/W_s) [a1 T + a2 T^2/2 + ... + a5 T^5/5 + a6] - Rm T + e5
+    // sum_s Y_s (R/W_s) [(a1 - 1) T + a2 T^2/2 + ... + a5 T^5/5 + a6] + e5
     P.e[0] = c[0];
     P.e[1] = c[1];
     P.e[2] = c[2];
     P.e[3] = c[3];
     P.e[4] = c[4];
     P.e[5] = c[5];
-    // cv = (c0 - Rm) + 2 c1 T + 3 c2 T^2 + 4 c3 T^3 + 5 c4 T^4
+    // cv = c0 + 2 c1 T + 3 c2 T^2 + 4 c3 T^3 + 5 c4 T^4
     if (CV64) {
         P.cv[0] = P.e[0];
         P.cv[1] = 2.0 * c[1];
@@ -414,8 +413,8 @@ __device__ __forceinline__ float mix_cvf(const MixPoly &P, float T) {
 
 __device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { return (M.two_ranges && ge_pos(T, M.Tmid)) ? 1 : 0; }
 
-// Newton solve of e(T) = e_target, warm-started from T, with e(T) = sum_s Y_s e_s(T)
-// and Rm = sum_s Y_s R/W_s; the weights may be mass fractions (energy per unit mass)
+// Newton solve of e(T) = e_target, warm-started from T, with e(T) = sum_s Y_s e_s(T);
+// the weights may be mass fractions (energy per unit mass)
 // or partial densities (energy per unit volume, e_target = rho e: the same root, and
 // the polynomial P is then density-weighted).  The residual is FP64; the derivative
 // cv is the FP32 polynomial, whose relative error (a few 1e-7) only sets the
@@ -423,10 +422,10 @@ __device__ __forceinline__ int nasa_range_of(const MechDev &M, double T) { retur
 // 1e-9 T (which leaves T within ~1e-16 T of the root, see the tolerance below) within
 // maxit iterations.  On return P holds the mixture polynomial of the range containing T.
 template <int NS, bool CV64>
-__device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double Rm, double e_target,
-                                         double &T, int maxit, MixPoly &P) {
+__device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS], double e_target, double &T, int maxit,
+                                         MixPoly &P) {
     int r = nasa_range_of(M, T);
-    mix_poly<NS, CV64>(M, r, Y, Rm, -e_target, P);      // P.e[5] holds e5 - e_target
+    mix_poly<NS, CV64>(M, r, Y, -e_target, P);      // P.e[5] holds e5 - e_target
     // Stop once the update just applied is below 1e-9 T: the iteration contracts the
     // error by the FP32 derivative's few 1e-7 per step (plus a quadratic term), so the
     // updated T is then within ~1e-16 T of the root, and a further step (the
@@ -436,14 +435,14 @@ __device__ __forceinline__ bool newton_T(const MechDev &M, const double (&Y)[NS]
         const int rn = nasa_range_of(M, T);
         if (rn != r) {
             r = rn;
-            mix_poly<NS, CV64>(M, r, Y, Rm, -e_target, P);
+            mix_poly<NS, CV64>(M, r, Y, -e_target, P);
         }
         // residual e(T) - e_target with the target folded into the constant term
         const double res = fma(T, fma(T, fma(T, fma(T, fma(T, P.e[4], P.e[3]), P.e[2]), P.e[1]), P.e[0]), P.e[5]);
         const double dT = res * f2d(__frcp_rn(mix_cvf(P, d2f(T))));
         T = T - dT;
         if (abs_le(dT, tol)) {
-            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS, CV64>(M, nasa_range_of(M, T), Y, Rm, -e_target, P);
+            if (M.two_ranges && nasa_range_of(M, T) != r) mix_poly<NS, CV64>(M, nasa_range_of(M, T), Y, -e_target, P);
             return true;
         }
     }

@@ -249,13 +249,11 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         const double irho = rcp64(rho);
         // Newton on the density-weighted energy rho e(T) = sum_s rho_s e_s(T) = E - |rho u|^2 / (2 rho):
         // the same root as e(T) = e without forming the mass fractions in FP64
-        double rhoRm = 0.0;
-#pragma unroll
-        for (int s = 0; s < NS; ++s) rhoRm = fma(rs[s], M.RW[s], rhoRm);
+        // R_m rho: FP64 in the FP64 path (p, gamma, c); the mixed path forms R_m in FP32 below
         const double rho_e = fma(-0.5 * irho, fma(mx, mx, fma(my, my, mz * mz)), E);
         double T = m.T[cell];
         MixPoly P;
-        const bool ok = newton_T<NS, sizeof(R) == 8>(M, rs, rhoRm, rho_e, T, newton_maxit, P);
+        const bool ok = newton_T<NS, sizeof(R) == 8>(M, rs, rho_e, T, newton_maxit, P);
         if (!ok) flag_error(m, ST_NEWTON, cell);
         // rho > 0 and 0 < T < T_MAX, compared on the bit patterns
         const bool rho_pos = (unsigned long long)(dbits(rho) - 1) < 0x7ff0000000000000ull;
@@ -289,7 +287,10 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             // bulk quantities of the mixed path in FP32: R_m, cv from the FP32 mixture
             // polynomial, cp, p, gamma and c, 1 / R_m and the mean molar mass
             const float Tf = d2f(T);
-            const float Rmf = d2f(rhoRm) * irhob;
+            float rhoRmf = 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rhoRmf = fmaf(d2f(rs[s]), M.RWf[s], rhoRmf);
+            const float Rmf = rhoRmf * irhob;
             const float cvf = mix_cvf(P, Tf) * irhob;
             cpb = cvf + Rmf;
             pb = d2f(rho) * (Rmf * Tf);
@@ -297,6 +298,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             irmb = rcp(Rmf);
             Wbarb = (float)RU * irmb;
         } else {
+            double rhoRm = 0.0;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) rhoRm = fma(rs[s], M.RW[s], rhoRm);
             const double Rm = rhoRm * irho;
             const double cv = mix_cv(P, T) * irho;
             const double cp = cv + Rm;
@@ -1476,16 +1480,12 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
         }
         const double irho = 1.0 / rho;
         const double u = m.U[NS * n + cell] * irho, v = m.U[(NS + 1) * n + cell] * irho, w = m.U[(NS + 2) * n + cell] * irho;
-        double Rm = 0.0;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            Y[s] = rs[s] * irho;
-            Rm = fma(Y[s], M.RW[s], Rm);
-        }
+        for (int s = 0; s < NS; ++s) Y[s] = rs[s] * irho;
         const double e = m.U[(NS + 3) * n + cell] * irho - 0.5 * (u * u + v * v + w * w);
         double T = m.T[cell];
         MixPoly P;
-        if (!newton_T<NS, true>(M, Y, Rm, e, T, newton_maxit, P)) flag_error(m, ST_NEWTON, cell);
+        if (!newton_T<NS, true>(M, Y, e, T, newton_maxit, P)) flag_error(m, ST_NEWTON, cell);
         m.T[cell] = T;
         const int rng = nasa_range(M, T);
         const double invT = 1.0 / T, lnT = log(T);
