@@ -168,8 +168,9 @@ int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, 
  * temperature to T_out (host, may equal T_in).  The state is copied in by eight
  * chunks of cells on a copy stream of the context, and the first stage's
  * cell-state kernel of each chunk starts once that chunk has arrived, so that the
- * transfer overlaps computation (with pinned host memory; pageable memory works
- * but copies synchronously).  t_dev, dt_fixed, cfl, laser, dt_dev as rf_rk_step.
+ * transfer overlaps computation; the temperature is copied out on the copy stream
+ * as soon as the last stage's cell state has written it, during that stage's sweeps
+ * (with pinned host memory; pageable memory works but copies synchronously).  t_dev, dt_fixed, cfl, laser, dt_dev as rf_rk_step.
  * Asynchronous on s: the host buffers must stay valid, and U_out unread, until s
  * has completed.  Errors: RF_EINVAL, RF_ENOMEM, RF_ECUDA. */
 int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U_out, double *T_out, double *t_dev,

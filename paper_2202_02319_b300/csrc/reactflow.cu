@@ -147,7 +147,9 @@ struct rf_ctx {
     // host-buffer step: device copies of U and T, a copy stream and its chunk events
     double *hU = nullptr, *hT = nullptr;
     cudaStream_t copy = nullptr;
-    cudaEvent_t hev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // host-buffer step: [0, 8) chunk copies in, [8] queued work before them, [9] the last
+    // stage's cell state (T final), [10] T copied out
+    cudaEvent_t hev[11] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
@@ -611,8 +613,10 @@ struct Path {
 
     // chunks > 0: the first stage's cell state runs on cells [q n / chunks, (q + 1) n / chunks)
     // once chunk_ev[q] has completed (the host-buffer step streams the state in by chunks)
+    // t_final_ev (if given) is recorded once the last stage's cell state has written T
     static int rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, double cfl, const rf_laser *L,
-                       double *dt_dev, cudaStream_t s, int chunks = 0, const cudaEvent_t *chunk_ev = nullptr) {
+                       double *dt_dev, cudaStream_t s, int chunks = 0, const cudaEvent_t *chunk_ev = nullptr,
+                       cudaEvent_t t_final_ev = nullptr) {
         // clock = (t, dt, cfl, dt_fixed)
         double hostclk[2] = {cfl, dt_fixed};
         CUDA_TRY(cudaMemcpyAsync(c->clock, t_dev, sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -646,6 +650,7 @@ struct Path {
             } else if ((rc = cell_state(c, m, s))) {
                 return rc;
             }
+            if (k == 2 && t_final_ev) CUDA_TRY(cudaEventRecord(t_final_ev, s));
             if (k == 0) {
                 dt_kernel<<<1, 1, 0, s>>>(c->clock, c->rates, hmin, !(c->flags & RF_NO_VISCOUS),
                                           !(c->flags & RF_NO_CHEMISTRY) && c->mech->nr > 0, m.laser_on && !(c->flags & RF_NO_LASER),
@@ -733,7 +738,7 @@ extern "C" int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double
 
 static int rk_step_chunked(rf_ctx *c, double *t_dev, double dt_fixed, double cfl, const rf_laser *L, double *dt_dev,
                            cudaStream_t s, int chunks) {
-    DISPATCH(c, rk_step(c, c->hU, c->hT, t_dev, dt_fixed, cfl, L, dt_dev, s, chunks, c->hev));
+    DISPATCH(c, rk_step(c, c->hU, c->hT, t_dev, dt_fixed, cfl, L, dt_dev, s, chunks, c->hev, c->hev[9]));
 }
 
 extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U_out, double *T_out,
@@ -766,8 +771,15 @@ extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in
         CUDA_TRY(cudaEventRecord(c->hev[q], c->copy));
     }
     if (int rc = rk_step_chunked(c, t_dev, dt_fixed, cfl, L, dt_dev, st, chunks)) return rc;
+    // T is final after the last stage's cell state: its copy out overlaps that stage's
+    // sweeps on the copy stream, and s waits for it, so completion of s covers it
+    if (T_out) {
+        CUDA_TRY(cudaStreamWaitEvent(c->copy, c->hev[9], 0));
+        CUDA_TRY(cudaMemcpyAsync(T_out, c->hT, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->copy));
+        CUDA_TRY(cudaEventRecord(c->hev[10], c->copy));
+    }
     CUDA_TRY(cudaMemcpyAsync(U_out, c->hU, (size_t)n * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (T_out) CUDA_TRY(cudaMemcpyAsync(T_out, c->hT, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (T_out) CUDA_TRY(cudaStreamWaitEvent(st, c->hev[10], 0));
     return RF_OK;
 }
 
