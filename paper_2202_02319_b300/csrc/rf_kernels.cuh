@@ -1344,7 +1344,7 @@ __device__ __forceinline__ void sweep_x_staged_block(const MechDev &M, const Mem
 }
 
 template <int NS, int MODE>
-__global__ void __launch_bounds__(128) sweep_x_staged_kernel(int mslot, const __grid_constant__ Member m) {
+__global__ void __launch_bounds__(128, 5) sweep_x_staged_kernel(int mslot, const __grid_constant__ Member m) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     sweep_x_staged_block<NS, MODE>(M, m, blockIdx.x, (float *)smem_raw);
