@@ -33,9 +33,10 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *a, double v) 
 
 // ----------------------------------------------------------------------------- chemistry
 
-// A finite FP64 (or FP32) value as an FP32 mantissa m with 1 <= |m| <= 2 and a binary
-// exponent e, value = m 2^e (m rounded to nearest by d2f; zero and subnormal inputs give
-// 2^-1023 or 2^-127 times a unit mantissa, i.e. a negligible value of the same sign).
+// A finite FP64 (or FP32) value as an FP32 mantissa m with 1 <= |m| < 2 and a binary
+// exponent e, value = m 2^e (m truncated to 23 fraction bits, relative error below
+// 1.2e-7; zero and subnormal inputs give 2^-1023 or 2^-127 times a unit mantissa, i.e. a
+// negligible value of the same sign).
 struct SplitF {
     float m;
     int e;
@@ -44,8 +45,14 @@ __device__ __forceinline__ SplitF split64(double d) {
     const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
     SplitF r;
     r.e = (int)((hi >> 20) & 0x7ffu) - 1023;
-    r.m = d2f(__hiloint2double((int)((hi & 0x800fffffu) | 0x3ff00000u), (int)lo));
+    r.m = __uint_as_float((hi & 0x80000000u) | 0x3f800000u | ((hi & 0xfffffu) << 3) | (lo >> 29));
     return r;
+}
+// m 2^e in FP32 for |m| in [0.5, 64): 0 when e < -126 (a value below 2^-120), infinity
+// from 2^128 on
+__device__ __forceinline__ float unsplit(float m, int e) {
+    const float scale = e < -126 ? 0.f : __uint_as_float((unsigned)(min(e, 128) + 127) << 23);
+    return m * scale;
 }
 __device__ __forceinline__ SplitF split32(float x) {
     const unsigned u = __float_as_uint(x);
@@ -113,7 +120,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             // the reactant factors shared by every product position.  FP64 path: in FP64.
             // Mixed path: the factors span more than the FP32 range but the result only
             // feeds the FP32 accumulator of a time-step estimate, so each factor is an
-            // FP32 mantissa in [1, 2] with an integer binary exponent (~3e-7 relative), and
+            // FP32 mantissa in [1, 2) with an integer binary exponent (~5e-7 relative), and
             // G comes from 1/G, so that no FP64 copy of G is kept.
             if (sizeof(R) == 4 && M.rev[j]) {
                 const SplitF f0 = split32(kf);
@@ -138,7 +145,7 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
                             pm *= f.m;
                             pe += f.e;
                         }
-                    const R part = (R)ldexpf(pm, max(min(pe, 300), -300));
+                    const R part = (R)unsplit(pm, pe);
                     sD[s * stride] = fma(-(R)M.dnu_prod[j][k], part, sD[s * stride]);
                 }
             } else if (M.rev[j]) {
