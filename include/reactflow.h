@@ -56,7 +56,9 @@ enum rf_precision {
     RF_FP64 = 0,          /* every operation in FP64 */
     RF_MIXED = 1          /* FP32 bulk arithmetic; FP64 for the temperature Newton solve,
                              Gibbs-energy equilibrium constants and reverse rates, and
-                             the conserved-variable stage accumulation */
+                             the conserved-variable stage accumulation (its exponentials
+                             and ln T to 2e-13 / 5e-14, the time-step estimate's rate
+                             derivatives as FP32 mantissas with integer exponents) */
 };
 
 enum rf_bc {
