@@ -241,6 +241,8 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
         }
         M.mu_ref[s] = d->mu_ref[s];
         M.mu_exp[s] = d->mu_exp[s];
+        M.hl_mu_ref[s] = 0.5 * std::log(d->mu_ref[s]);
+        M.h_mu_exp[s] = 0.5 * d->mu_exp[s];
         M.eucken[s] = 1.25 * RU / d->W[s];
         M.Wf[s] = (float)M.W[s];
         M.invWf[s] = (float)M.invW[s];

@@ -33,6 +33,7 @@ struct MechDev {
     double gc[2][NSMAX][7];                    // ln G = g/RT + ln(RT/p_atm) = gc0 + T(gc1 + ... T gc4) + gc5/T + gc6 lnT
     float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
+    double hl_mu_ref[NSMAX], h_mu_exp[NSMAX];  // ln(mu_ref) / 2, mu_exp / 2: sqrt(mu_s) by one exponential
     double invDref[NSMAX][NSMAX];
     double wc[NSMAX][NSMAX];                   // (W_j / W_i)^(1/4)
     double wd[NSMAX][NSMAX];                   // 1 / sqrt(8 (1 + W_i / W_j))
@@ -495,9 +496,15 @@ __device__ __forceinline__ void transport(const MechDev &M, int rng, R T, R p, R
     R mus[NS], sq[NS], isq[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        mus[s] = mech_mu_ref<R>(M, s) * exp_(mech_mu_exp<R>(M, s) * lnTs);
-        sq[s] = sqrt_(mus[s]);
-        isq[s] = rcp(sq[s]);
+        if constexpr (sizeof(R) == 8) {
+            // sqrt(mu_s) and its reciprocal from one exponential pair, mu_s as its square
+            exp_pair(fma(M.h_mu_exp[s], lnTs, M.hl_mu_ref[s]), sq[s], isq[s]);
+            mus[s] = sq[s] * sq[s];
+        } else {
+            mus[s] = mech_mu_ref<R>(M, s) * exp_(mech_mu_exp<R>(M, s) * lnTs);
+            sq[s] = sqrt_(mus[s]);
+            isq[s] = rcp(sq[s]);
+        }
     }
     R num_mu = 0, num_lam = 0;
 #pragma unroll
