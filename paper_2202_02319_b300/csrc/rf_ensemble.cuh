@@ -55,14 +55,14 @@ __device__ __forceinline__ void member_dt(const MechDev &M, const Member &m) {
     clock[1] = dt;
 }
 
-// Loads member descriptor it.m into shared memory; returns false (uniformly) if
-// the member has failed and must be skipped.
+// Loads member descriptor it.m into shared memory, eight bytes per thread; returns
+// false (uniformly) if the member has failed and must be skipped.
+static_assert(sizeof(Member) % 8 == 0 && sizeof(Member) / 8 <= 128, "Member copy layout");
 __device__ __forceinline__ bool load_member(const Member *tab, int mi, Member &sm, int &s_ok) {
     __syncthreads();
-    if (threadIdx.x == 0) {
-        sm = tab[mi];
-        s_ok = (*(volatile int *)sm.status) == 0;
-    }
+    if (threadIdx.x == 0) s_ok = (*(volatile int *)tab[mi].status) == 0;
+    if (threadIdx.x < sizeof(Member) / 8)
+        reinterpret_cast<long long *>(&sm)[threadIdx.x] = reinterpret_cast<const long long *>(tab + mi)[threadIdx.x];
     __syncthreads();
     return s_ok != 0;
 }
