@@ -107,14 +107,22 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
             // d q / d C_s at each position of the reactant / product lists (a species
             // repeated by its coefficient appears at as many positions): the forward term
             // without that reactant factor, in the bulk type ...
-#pragma unroll 1
-            for (int k = 0; k < nrc; ++k) {
-                R part = kf;
-#pragma unroll 1
-                for (int k2 = 0; k2 < nrc; ++k2)
-                    if (k2 != k) part *= sCb[M.reac[j][k2] * stride];
-                const int s = M.reac[j][k];
-                sD[s * stride] = fma((R)M.dnu_reac[j][k], part, sD[s * stride]);
+            // (straight-line code per reactant count, the same for every thread; products
+            // in list order)
+            if (nrc == 1) {
+                const int s0 = M.reac[j][0];
+                sD[s0 * stride] = fma((R)M.dnu_reac[j][0], kf, sD[s0 * stride]);
+            } else if (nrc == 2) {
+                const int s0 = M.reac[j][0], s1 = M.reac[j][1];
+                const R c0 = sCb[s0 * stride], c1 = sCb[s1 * stride];
+                sD[s0 * stride] = fma((R)M.dnu_reac[j][0], kf * c1, sD[s0 * stride]);
+                sD[s1 * stride] = fma((R)M.dnu_reac[j][1], kf * c0, sD[s1 * stride]);
+            } else if (nrc == 3) {
+                const int s0 = M.reac[j][0], s1 = M.reac[j][1], s2 = M.reac[j][2];
+                const R c0 = sCb[s0 * stride], c1 = sCb[s1 * stride], c2 = sCb[s2 * stride];
+                sD[s0 * stride] = fma((R)M.dnu_reac[j][0], kf * c1 * c2, sD[s0 * stride]);
+                sD[s1 * stride] = fma((R)M.dnu_reac[j][1], kf * c0 * c2, sD[s1 * stride]);
+                sD[s2 * stride] = fma((R)M.dnu_reac[j][2], kf * c0 * c1, sD[s2 * stride]);
             }
             // ... and the reverse term k_f G_s prod_(other products) (C G) prod_reac (1/G),
             // the reactant factors shared by every product position.  FP64 path: in FP64.
@@ -132,21 +140,35 @@ __device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT
                     krm *= f.m;
                     kre += f.e;
                 }
+                if (npd == 1) {
+                    const int s0 = M.prod[j][0];
+                    const SplitF ig0 = split64(sRr[s0 * stride]);      // G = 1 / (1/G)
+                    sD[s0 * stride] = fma(-(R)M.dnu_prod[j][0], (R)unsplit(krm * __frcp_rn(ig0.m), kre - ig0.e),
+                                          sD[s0 * stride]);
+                } else if (npd == 2) {
+                    const int s0 = M.prod[j][0], s1 = M.prod[j][1];
+                    const SplitF ig0 = split64(sRr[s0 * stride]), ig1 = split64(sRr[s1 * stride]);
+                    const SplitF p0 = split64(sP[s0 * stride]), p1 = split64(sP[s1 * stride]);
+                    sD[s0 * stride] = fma(-(R)M.dnu_prod[j][0],
+                                          (R)unsplit(krm * __frcp_rn(ig0.m) * p1.m, kre - ig0.e + p1.e), sD[s0 * stride]);
+                    sD[s1 * stride] = fma(-(R)M.dnu_prod[j][1],
+                                          (R)unsplit(krm * __frcp_rn(ig1.m) * p0.m, kre - ig1.e + p0.e), sD[s1 * stride]);
+                } else {
 #pragma unroll 1
-                for (int k = 0; k < npd; ++k) {
-                    const int s = M.prod[j][k];
-                    const SplitF ig = split64(sRr[s * stride]);        // G = 1 / (1/G)
-                    float pm = krm * __frcp_rn(ig.m);
-                    int pe = kre - ig.e;
+                    for (int k = 0; k < npd; ++k) {
+                        const int s = M.prod[j][k];
+                        const SplitF ig = split64(sRr[s * stride]);
+                        float pm = krm * __frcp_rn(ig.m);
+                        int pe = kre - ig.e;
 #pragma unroll 1
-                    for (int k2 = 0; k2 < npd; ++k2)
-                        if (k2 != k) {
-                            const SplitF f = split64(sP[M.prod[j][k2] * stride]);
-                            pm *= f.m;
-                            pe += f.e;
-                        }
-                    const R part = (R)unsplit(pm, pe);
-                    sD[s * stride] = fma(-(R)M.dnu_prod[j][k], part, sD[s * stride]);
+                        for (int k2 = 0; k2 < npd; ++k2)
+                            if (k2 != k) {
+                                const SplitF f = split64(sP[M.prod[j][k2] * stride]);
+                                pm *= f.m;
+                                pe += f.e;
+                            }
+                        sD[s * stride] = fma(-(R)M.dnu_prod[j][k], (R)unsplit(pm, pe), sD[s * stride]);
+                    }
                 }
             } else if (M.rev[j]) {
                 double kr = wide(kf);
