@@ -110,8 +110,16 @@ def sweep_bytes(ns: int, rsize: int, mode: str) -> int:
     return b + nv * rsize + 3 * nv * 8
 
 
+def sweep_bytes_method(ns: int) -> int:
+    """The fewest HBM bytes per cell a split flux sweep can move in FP32: the
+    primitives u, v, w, T, p, c and Y_s (6 + Ns; rho follows from the equation of
+    state), the coefficients mu, lambda and rho D_s (2 + Ns), and the RHS
+    accumulator (4 + Ns) read and written: 208 B for 9 species."""
+    return 4 * ((6 + ns) + (2 + ns)) + 2 * 4 * (ns + 4)
+
+
 # Counts of the mixed-precision cell-state kernel (9 species, 19 reactions) from one
-# ncu capture of the 96^3 case (profiles/cell_state_mixed_jet96.md), per cell and
+# ncu capture of the 96^3 jet case, per cell and
 # averaged over the three launches of an RK step (the first also forms the chemical
 # time-step rates: 190.0 DFMA, 112.0 DMUL, 33.0 DADD and 323.2 DRAM bytes; the other
 # two 190.4, 112.1, 33.2 and 327.6): FP64 thread instructions (DFMA, DMUL, DADD; FLOP =
@@ -219,7 +227,7 @@ def run_ours(args):
     Th.copy_(T)
     s = torch.cuda.current_stream()
     te = torch.zeros(1, dtype=torch.float64, device=dev)
-    e2e_steps = max(1, min(3, args.steps))
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
     nv.rk_step_host(ctx, Uh, Th, Uh, Th, te, 0.0, case.cfl, las, None)      # allocates the context's copies
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -281,6 +289,13 @@ def run_ours(args):
                       "share": round(ms_k / sum(v for kk, v in tot.items() if kk != "stage_update"), 4),
                       "alg_bytes_per_cell": b, "achieved_gbs": round(gbs, 1),
                       "hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+        if k.startswith("sweep"):
+            # the method's own minimum for a split sweep: 26 FP32 primitive and
+            # coefficient fields read, the 13-variable FP32 RHS read and written
+            bm = sweep_bytes_method(ns)
+            gm = bm * ncell / (avg * 1e-3) / 1e9
+            kernels[k].update({"method_bytes_per_cell": bm, "method_gbs": round(gm, 1),
+                               "method_hbm_frac": round(gm / peaks["hbm_gbs"], 4)})
     k64 = {}
     for k in ("cell_state", "sweep_x", "sweep_y", "sweep_z"):
         ms_k, nl = prof64[k]
@@ -328,7 +343,8 @@ def run_ours(args):
         "sim": {"t_end_s": t_end, "dt_last_s": dt_last, "generation_s": round(gen_s, 2)},
     }
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args, case_n=args.cpu_n)
+        case.prim = prim.reshape(case.prim.shape)
+        out["cpu_baseline"] = cpu_baseline(case, block=args.cpu_n, full=args.cpu_full)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -340,35 +356,42 @@ def run_ours(args):
 
 def run_adjoint_leg(args, dev):
     """Gradient of the time-integrated heat release with respect to (E, x0, y0, z0,
-    sigma_r, ln A_j) for one jet member: forward run with checkpoints, then the
-    reverse sweep (recomputation within segments, RK-step adjoints), both FP64.
-    The pulse is centred inside the window so that every laser gradient is nonzero."""
+    sigma_r, ln A_j) for jet members of n^3 cells, each with its own laser: forward
+    run with a checkpoint every `adjoint_ck` steps, then the reverse sweep
+    (recomputation within segments, RK-step adjoints), both FP64.  The pulse is
+    centred inside the window so that every laser gradient is nonzero."""
     import time
     import torch
     from paper_2202_02319_b300 import adjoint, synth
-    n, nsteps, dt = args.adjoint_n, args.adjoint_steps, 1e-9
-    case = synth.case_jet(0, n, device=dev)
-    case.laser.t0 = 0.5 * nsteps * dt
-    prob = adjoint.HeatReleaseProblem(case.mech, case.grid, case.prim, case.laser, nsteps=nsteps, dt=dt,
-                                      checkpoint_every=max(1, nsteps // 2), device=dev)
-    p0 = prob.default_params()
-    prob.run(p0, keep=False)                      # warm-up (also builds the kernels' first launches)
+    n, nsteps, dt, nm = args.adjoint_n, args.adjoint_steps, 1e-9, max(1, args.adjoint_members)
+    cases = synth.adjoint_members(0, nm, n, t0=0.5 * nsteps * dt)
+    ck = args.adjoint_ck if args.adjoint_ck > 0 else max(1, nsteps // 2)
+    probs = [adjoint.HeatReleaseProblem(c.mech, c.grid, c.prim, c.laser, nsteps=nsteps, dt=dt,
+                                        checkpoint_every=ck, device=dev) for c in cases]
+    p0 = [pr.default_params() for pr in probs]
+    probs[0].run(p0[0], keep=False)               # warm-up (also builds the kernels' first launches)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    prob.run(p0, keep=False)
+    for pr, p in zip(probs, p0):
+        pr.run(p, keep=False)
     torch.cuda.synchronize()
     t_fwd = time.perf_counter() - t0
     t0 = time.perf_counter()
-    J = prob.run(p0, keep=True)
-    g = prob.gradient()
+    grads, Js = [], []
+    for pr, p in zip(probs, p0):
+        J, st = pr.run_with_state(p)
+        grads.append(pr.gradient(st))
+        Js.append(J)
     torch.cuda.synchronize()
     t_grad = time.perf_counter() - t0
-    cells = case.grid.ncells
-    return {"cells": cells, "steps": nsteps, "dt_s": dt, "checkpoint_every": prob.ck, "params": int(p0.numel()),
+    cells = cases[0].grid.ncells
+    return {"members": nm, "cells": cells, "steps": nsteps, "dt_s": dt, "checkpoint_every": ck,
+            "params": int(p0[0].numel()),
             "forward_ms": round(t_fwd * 1e3, 2), "forward_and_gradient_ms": round(t_grad * 1e3, 2),
             "gradient_over_forward": round(t_grad / t_fwd, 2),
-            "cell_updates_per_s_forward": cells * 3 * nsteps / t_fwd, "J": J,
-            "dJ_dE": float(g[0]), "timing": "host clock around synchronised calls, FP64"}
+            "members_per_s_gradient": nm / t_grad,
+            "cell_updates_per_s_forward": nm * cells * 3 * nsteps / t_fwd, "J": Js[0],
+            "dJ_dE": float(grads[0][0]), "timing": "host clock around synchronised calls, FP64"}
 
 
 # ----------------------------------------------------------------------------- ensemble leg
@@ -421,34 +444,68 @@ def run_ensemble_leg(args, dev):
 
 # ----------------------------------------------------------------------------- oracle arm
 
-def _oracle_sample(n):
-    """A bounded sample of the workload: the same generator and mechanism on an
-    n^3 periodic box (jet radius scaled), on the host."""
-    from paper_2202_02319_b300 import synth
-    return synth.case_jet(0, n)
-
-
-def cpu_baseline(args, case_n=32, budget_s=20.0):
+def workload_block(prim, grid, b):
+    """A b^3 block of the workload's primitive fields (on the host), centred on the
+    jet axis (y, z) and the middle of the box in x, with zero-gradient ghost
+    cells: the same state, mechanism and per-cell work as the full box."""
     import torch
+    nz, ny, nx = prim.shape[1:]
+    b = min(b, nx, ny, nz)
+    z0, y0, x0 = (nz - b) // 2, (ny - b) // 2, (nx - b) // 2
+    blk = prim[:, z0:z0 + b, y0:y0 + b, x0:x0 + b].to("cpu", torch.float64).contiguous()
+    from oracle.mech import GridT
+    return blk, GridT(b, b, b, grid.dx, grid.dy, grid.dz, (1, 1, 1))
+
+
+def _time_oracle_rhs(mt, g, prim, las, budget_s, min_evals=2, max_evals=1000):
     import oracle
-    from oracle.mech import from_synth, grid_from_synth
-    case = _oracle_sample(case_n)
-    mt = from_synth(case.mech)
-    g = grid_from_synth(case.grid)
-    U, T = oracle.rhs.init_state(mt, torch.as_tensor(case.prim, dtype=torch.float64))
-    las = case.laser.as_tuple()
+    U, T = oracle.rhs.init_state(mt, prim)
     oracle.rhs.rhs(mt, g, U, T, 0.0, las)            # warm-up
     t0 = time.time()
     k = 0
-    while True:
+    while k < max_evals and (k < min_evals or time.time() - t0 < budget_s):
         oracle.rhs.rhs(mt, g, U, T, 0.0, las)
         k += 1
-        if time.time() - t0 > budget_s or k >= 50:
-            break
-    el = time.time() - t0
-    return {"value": case.grid.ncells * k / el, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"{k} oracle RHS evaluations of the same generator and mechanism on a {case_n}^3 box "
-                      f"({el:.1f} s)"}
+    return k, time.time() - t0
+
+
+def cpu_baseline(case, block=64, block1=24, budget_s=12.0, budget1_s=6.0, full=False):
+    """The oracle as it stands (vectorised torch-CPU FP64) timed on the host cores,
+    on blocks of the workload itself: all threads on a `block`^3 block, one thread
+    on a `block1`^3 block; with `full`, one RHS on the whole box as well."""
+    import torch
+    from oracle.mech import from_synth
+    mt = from_synth(case.mech)
+    las = case.laser.as_tuple()
+    ns = case.mech.n_species
+    prim = case.prim.reshape(5 + ns, case.grid.nz, case.grid.ny, case.grid.nx)
+    cores = len(os.sched_getaffinity(0))
+    threads = torch.get_num_threads()
+    blk, g = workload_block(prim, case.grid, block)
+    k, el = _time_oracle_rhs(mt, g, blk, las, budget_s)
+    ncell = g.nx * g.ny * g.nz
+    out = {"value": ncell * k / el, "unit": UNIT, "cores": threads, "host_cores": cores, "kind": "oracle",
+           "sample": f"{k} oracle RHS evaluations on a {g.nx}^3 block of the {case.grid.nx}^3 workload "
+                     f"(centred on the jet, zero-gradient edges) in {el:.1f} s on {threads} threads"}
+    blk1, g1 = workload_block(prim, case.grid, block1)
+    torch.set_num_threads(1)
+    try:
+        k1, el1 = _time_oracle_rhs(mt, g1, blk1, las, budget1_s)
+    finally:
+        torch.set_num_threads(threads)
+    out["single_core"] = {"value": g1.nx * g1.ny * g1.nz * k1 / el1, "unit": UNIT, "threads": 1,
+                          "sample": f"{k1} oracle RHS evaluations on a {g1.nx}^3 block in {el1:.1f} s"}
+    if full:
+        import oracle
+        from oracle.mech import grid_from_synth
+        gf = grid_from_synth(case.grid)
+        Uf, Tf = oracle.rhs.init_state(mt, prim.to("cpu", torch.float64))
+        t0 = time.time()
+        oracle.rhs.rhs(mt, gf, Uf, Tf, 0.0, las)
+        elf = time.time() - t0
+        out["full_box"] = {"value": case.grid.ncells / elf, "unit": UNIT, "threads": threads,
+                           "sample": f"one oracle RHS on the whole {case.grid.nx}^3 box in {elf:.1f} s"}
+    return out
 
 
 def run_reference(args):
@@ -456,14 +513,38 @@ def run_reference(args):
     if rank != 0:
         return
     import torch
-    cb = cpu_baseline(args, case_n=args.cpu_n, budget_s=max(5.0, args.steps * 4.0))
-    out = {"metric": METRIC, "value": cb["value"], "unit": UNIT, "impl": "reference", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jet-in-a-box)",
-           "config": {"workload": f"jet_in_box_{args.n}^3_9sp_19r_laser",
-                      "sample": f"{args.cpu_n}^3 box of the same generator and mechanism"},
+    from paper_2202_02319_b300 import synth
+    from oracle.mech import from_synth
+    case = synth.case_jet(0, args.n)                 # the same generator, on the host
+    mt = from_synth(case.mech)
+    las = case.laser.as_tuple()
+    ns = case.mech.n_species
+    prim = case.prim.reshape(5 + ns, case.grid.nz, case.grid.ny, case.grid.nx)
+    blk, g = workload_block(prim, case.grid, args.cpu_n)
+    import oracle
+    U, T = oracle.rhs.init_state(mt, blk)
+    for _ in range(args.warmup):
+        oracle.rhs.rhs(mt, g, U, T, 0.0, las)
+    t0 = time.time()
+    for _ in range(args.steps):
+        oracle.rhs.rhs(mt, g, U, T, 0.0, las)
+    el = time.time() - t0
+    ncell = g.nx * g.ny * g.nz
+    value = ncell * args.steps / el
+    threads = torch.get_num_threads()
+    cb = {"value": value, "unit": UNIT, "cores": threads, "host_cores": len(os.sched_getaffinity(0)),
+          "kind": "oracle",
+          "sample": f"each step one oracle RHS evaluation on a {g.nx}^3 block of the {args.n}^3 workload "
+                    f"(centred on the jet, zero-gradient edges); {args.steps} steps in {el:.1f} s"}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded jet-in-a-box, host-generated)",
+           "config": {"workload": f"jet_in_box_{args.n}^3_9sp_19r_laser", "cells": case.grid.ncells,
+                      "species": ns, "reactions": case.mech.n_reactions, "precision": "fp64 (oracle)",
+                      "sample_block": f"{g.nx}^3"},
            "cpu_baseline": cb,
-           "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
@@ -472,15 +553,19 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--n", type=int, default=256)
-    ap.add_argument("--cpu-n", type=int, default=32)
+    ap.add_argument("--cpu-n", type=int, default=64)
+    ap.add_argument("--cpu-full", action="store_true", help="also time one oracle RHS on the whole box")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble-members", type=int, default=64)
-    ap.add_argument("--ensemble-steps", type=int, default=2)
+    ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--adjoint-n", type=int, default=64)
     ap.add_argument("--adjoint-steps", type=int, default=20)
+    ap.add_argument("--adjoint-members", type=int, default=1)
+    ap.add_argument("--adjoint-ck", type=int, default=0, help="checkpoint interval (0: half the steps)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

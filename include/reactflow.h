@@ -306,23 +306,26 @@ int rf_probe_math(int fn, const double *x, double *y, double *y2, long long n, r
 /* Allocation-free RHS (the paper has no counterpart: this is a service of the
  * library, not a step of the method).  Computes the same dU/dt as rf_rhs for a
  * mechanism and grid without a context, for callers that cannot allocate device
- * memory: code running inside CUDA stream capture (where cudaMalloc is not
- * allowed), loops that must not add allocator latency, and processes whose
- * device memory is budgeted by a host framework.  Its scratch (primitive and
- * coefficient fields, RHS accumulator, status words) lives in one static
- * device array of 16 MiB that every GPU loading the library holds until the
- * process exits; grids needing more (n (12 + 4 Ns) values of the bulk type, plus
- * the FP32 state copy in mixed precision and a 256-byte header; e.g. at most
- * 43,000 cells for 9 species in FP64) are rejected with RF_EINVAL before any
- * device work.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) and the first call per precision and species count sets
- * kernel attributes (shared-memory limits), so make those calls before any
- * stream capture.
+ * memory: a host framework whose caching allocator already holds the device's
+ * memory budget (a library cudaMalloc would fail, or fragment and shrink that
+ * budget behind the framework's back), and latency-critical loops, where
+ * cudaMalloc and cudaFree may synchronise the device and stall work already
+ * queued on other streams.  Its scratch (primitive and coefficient fields, RHS
+ * accumulator, status words) lives in one static device array of 16 MiB that
+ * every GPU loading the library holds until the process exits; grids needing
+ * more (n (12 + 4 Ns) values of the bulk type, plus the FP32 state copy in
+ * mixed precision and a 256-byte header; e.g. at most 43,000 cells for 9
+ * species in FP64) are rejected with RF_EINVAL before any device work.  The
+ * first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) and the first call per precision and species count
+ * sets kernel attributes (shared-memory limits); make those first calls before
+ * any stream capture.
  * Calls share the array and its last contents (the status word is cleared at
  * each call); calls that overlap on the GPU race, so issue them on one stream.
  * Arguments as rf_rhs; m, g, precision and flags as rf_create_ctx.  The call
- * waits for its stream and returns the device status as an RF_E* code.
- * It calls no cudaMalloc, cudaFree or other allocating routine. */
+ * waits for its stream (it copies the status word to the host and synchronises
+ * s) and returns the device status as an RF_E* code.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine. */
 int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int precision, uint32_t flags, const double *U,
                    double *T, double t, const rf_laser *laser, double *dUdt, rf_stream s);
 

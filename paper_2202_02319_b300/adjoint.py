@@ -54,22 +54,36 @@ class HeatReleaseProblem:
         nv.init_state(ctx, self.prim.to(self.device), U, T)
         return mech, ctx, U, T, las
 
-    def run(self, params, keep: bool = True) -> float:
+    def run_with_state(self, params):
+        """J(p) and the run's reverse-sweep state (handles and checkpoints), which
+        gradient() takes; each call owns its state, so several runs can be
+        differentiated in any order."""
         mech, ctx, U, T, las = self._setup(params)
         J = 0.0
         cks = {}
         for k in range(self.nsteps):
-            if keep and k % self.ck == 0:
+            if k % self.ck == 0:
                 cks[k] = (U.clone(), T.clone())
             J += nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las)
         nv.check(ctx)
+        return J, (mech, ctx, las, cks)
+
+    def run(self, params, keep: bool = True) -> float:
+        """J(p); with keep, the run's state is also kept as the default of gradient()."""
         if keep:
-            self._state = (mech, ctx, las, cks)
+            J, self._state = self.run_with_state(params)
+            return J
+        mech, ctx, U, T, las = self._setup(params)
+        J = 0.0
+        for k in range(self.nsteps):
+            J += nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las)
+        nv.check(ctx)
         return J
 
-    def gradient(self) -> torch.Tensor:
-        """dJ/dp of the last run(), by the reverse sweep."""
-        mech, ctx, las, cks = self._state
+    def gradient(self, state=None) -> torch.Tensor:
+        """dJ/dp of the run that produced `state` (default: the last run(keep=True)),
+        by the reverse sweep."""
+        mech, ctx, las, cks = state if state is not None else self._state
         lam = torch.zeros((mech.n_species + 4, self.grid.ncells), dtype=torch.float64, device=self.device)
         grads = torch.zeros(self.np, dtype=torch.float64, device=self.device)
         for k0 in sorted(cks, reverse=True):
@@ -90,13 +104,17 @@ class HeatReleaseProblem:
 class _Objective(torch.autograd.Function):
     @staticmethod
     def forward(fctx, params, problem):
-        J = problem.run(params)
+        # the checkpoints of this run travel with this graph node, so a later run of
+        # the same problem does not change this node's gradient
+        J, fctx.state = problem.run_with_state(params)
         fctx.problem = problem
         return params.new_tensor(J)
 
     @staticmethod
     def backward(fctx, gJ):
-        return gJ * fctx.problem.gradient().to(gJ.device, gJ.dtype), None
+        g = fctx.problem.gradient(fctx.state)
+        fctx.state = None
+        return gJ * g.to(gJ.device, gJ.dtype), None
 
 
 def ignition_objective(params: torch.Tensor, problem: HeatReleaseProblem) -> torch.Tensor:

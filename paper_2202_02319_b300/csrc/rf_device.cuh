@@ -248,8 +248,11 @@ template <> __device__ __forceinline__ float mech_cpc<float>(const MechDev &M, i
 // relative).  ln2/256 is split into its double value and the remainder so that r
 // keeps full precision for every k; 2^(+-m) is added to the exponent fields of the
 // correctly rounded table entries.  A few ulp from exp itself for |x| <= 707;
-// beyond that (up to |x| ~ 5e6) the power of two is clamped to 2^(+-1020) and the
-// results saturate.
+// for 707 < |x| < 45,000 the power of two is clamped to 2^(+-1020) and the results
+// saturate.  The reduction is valid only while k = round(256 x / ln 2) converts
+// exactly through FP32 (|k| < 2^24, i.e. |x| < 45,000); callers keep their
+// arguments far inside that (Gibbs energies and Arrhenius exponents of a few
+// hundred, the laser exponent bounded at -740).
 constexpr double LN2_256_HI = 0.6931471805599453094 / 256.0;   // double(ln 2) / 256, exact
 constexpr double LN2_256_LO = 2.3190468138462996e-17 / 256.0;  // (ln 2 - double(ln 2)) / 256
 __device__ double g_exp_tab[512];                              // 2^(j/256), then 2^(-j/256), j = 0..255

@@ -505,3 +505,21 @@ def ensemble_members(seed: int = 0, n_members: int = 64, lo: int = 48, hi: int =
                     sigma_r=3.0 * dx, t0=g.uniform(0.0, t0_max), sigma_t=10e-9)
         out.append(Case(f"member{m}_{nx}x{ny}x{nz}", mech, Grid(nx, ny, nz, dx, dx, dx), prim, las, steps=10))
     return out
+
+
+def adjoint_members(seed: int = 0, n_members: int = 16, n: int = 64, t0: float = 0.0) -> List[Case]:
+    """Sensitivity workload: members sharing the n^3 jet-in-a-box state of
+    case_jet(seed, n), each with its own laser (energy U[5, 40] mJ at a point on
+    the shear layer, sigma_r = 3 cells, sigma_t = 10 ns, deposition time t0)."""
+    base = case_jet(seed, n)
+    g = stream(seed, f"adjoint/{n}/members")
+    dx = base.grid.dx
+    r_jet = max(2, (16 * n) // 256) * dx
+    out = []
+    for m in range(n_members):
+        th = g.uniform(0.0, 2.0 * np.pi)
+        las = Laser(E=g.uniform(5e-3, 40e-3), x0=g.uniform(0.25, 0.75) * n * dx,
+                    y0=n * dx / 2 + r_jet * np.cos(th), z0=n * dx / 2 + r_jet * np.sin(th),
+                    sigma_r=3.0 * dx, t0=t0, sigma_t=10e-9)
+        out.append(Case(f"adjoint_member{m}_{n}^3", base.mech, base.grid, base.prim, las, steps=200))
+    return out

@@ -162,3 +162,26 @@ def test_checkpointed_gradient_vs_finite_differences_and_oracle():
     go = torch.cat([torch.stack(res[:5]), res[5]])
     assert abs(float(J) - float(Jo)) <= 1e-10 * abs(float(Jo))
     assert float(((g - go).abs() / go.abs().clamp_min(go.abs().max() * 1e-12)).max()) < 1e-8
+
+
+def test_objective_nodes_keep_their_own_checkpoints():
+    """Two differentiable runs of one problem before either backward: each graph node
+    differentiates its own run (the checkpoints travel with the node), so the
+    gradient of J(p1) taken after J(p2) was formed equals that of a lone J(p1)."""
+    from paper_2202_02319_b300 import adjoint
+    case = _case()
+    prob = adjoint.HeatReleaseProblem(case.mech, case.grid, case.prim, case.laser, nsteps=6, dt=4e-9,
+                                      checkpoint_every=4)
+    p0 = prob.default_params()
+    p1 = p0.clone()
+    p1[0] *= 1.5
+    a = p0.clone().requires_grad_(True)
+    adjoint.ignition_objective(a, prob).backward()
+    b0 = p0.clone().requires_grad_(True)
+    b1 = p1.clone().requires_grad_(True)
+    J0 = adjoint.ignition_objective(b0, prob)
+    J1 = adjoint.ignition_objective(b1, prob)
+    J0.backward()
+    J1.backward()
+    assert torch.allclose(b0.grad, a.grad, rtol=1e-9, atol=1e-12 * float(a.grad.abs().max()))
+    assert not torch.allclose(b1.grad, a.grad, rtol=1e-6, atol=0.0)

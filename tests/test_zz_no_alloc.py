@@ -1,11 +1,12 @@
 """The allocation-free RHS entry point (rf_rhs_noalloc), called through the C
 ABI, gives the same dU/dt as the context-based rf_rhs on two calls in a row.
 
-This entry point exists for callers that cannot allocate device memory (code
-inside CUDA stream capture, allocation-free hot loops, processes whose device
-memory a host framework budgets): its scratch is a fixed 16 MiB device array
-shared by all calls.  The file sorts last so that a run stopping at the first
-failure has run every other test before this one."""
+This entry point exists for callers that cannot allocate device memory: a host
+framework whose caching allocator already holds the device's memory budget,
+and latency-critical loops where cudaMalloc / cudaFree may synchronise the
+device.  Its scratch is a fixed 16 MiB device array shared by all calls.  The
+file sorts last so that a run stopping at the first failure has run every
+other test before this one."""
 import ctypes
 
 import numpy as np
