@@ -101,9 +101,10 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
         hp = fluxes.pad(st["h_s"], grid)
         mup = fluxes.pad(st["mu"], grid)
         lamp = fluxes.pad(st["lam"], grid)
+    scheme = (flags or {}).get("scheme", "weno3z")
     for d in range(3):
         if _flag(flags, "inviscid"):
-            Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns)
+            Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns, scheme)
             out = out - fluxes.divergence(Fa, grid, d)
         if _flag(flags, "viscous"):
             Fd = fluxes.diffusive_flux(velp, Tp, Xp, Yp, Dcp, hp, mup, lamp, grid, d, ns)

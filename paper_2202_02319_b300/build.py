@@ -34,10 +34,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     # -fmad=true: multiply-add pairs contract into FMAs (the flux sweeps are issue-bound,
     # the FP64 path FP64-bound).  Kernels that inline the same device code (single-grid
     # and ensemble launches, chunked and whole cell-state launches) still round alike:
-    # the tests compare them bit for bit.
+    # the tests compare them bit for bit.  ptxas compiles the kernels on all host cores.
     cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-fmad=true", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
            "-I", os.path.join(ROOT, "include"), "-I", CSRC, "--expt-relaxed-constexpr",
-           "-cudart", "static", *extra, *sources(), "-o", OUT + ".tmp"]
+           "-cudart", "static", "-Xptxas", "--split-compile=0", *extra, *sources(), "-o", OUT + ".tmp"]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)

@@ -368,6 +368,7 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     for (int a = 0; a < 3; ++a)
         if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_create_ctx: bc[%d] = %d unknown", a, g->bc[a]);
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
+    if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_create_ctx: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
     int mslot = 0;
     {
         int rc = mech_slot(m, &mslot);
@@ -448,6 +449,7 @@ static Member base_member(rf_ctx *c) {
     m.h[1] = c->g.dy;
     m.h[2] = c->g.dz;
     for (int a = 0; a < 3; ++a) m.invh[a] = 1.0 / m.h[a];
+    for (int a = 0; a < 3; ++a) m.weps[a] = m.h[a] * m.h[a] / 3.0;
     m.n = c->n;
     m.Q = c->Q;
     m.rhs = c->rhs;
@@ -517,9 +519,44 @@ struct Path {
         return RF_OK;
     }
 
+    // TENO6 sweeps: thread per face from global memory (six-cell stencils), both precisions
+    template <int MODE>
+    static int sweep_teno(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
+        constexpr int NV = NS + 4;
+        if (dir == 0) {
+            const int nx = c->g.nx;
+            int W, rpb;
+            if (nx <= c->x_block) {
+                W = nx;
+                rpb = std::max(1, std::min(c->x_block / nx, 320 / (nx + 2)));
+            } else {
+                W = c->x_block;
+                rpb = 1;
+            }
+            const int threads = ((W * rpb + 31) / 32) * 32;
+            const int nrows = c->g.ny * c->g.nz;
+            const int blocks = (nrows + rpb - 1) / rpb;
+            const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
+            ProfScope ps(c, PROF_SWEEP_X, s);
+            sweep_x_kernel<R, UT, NS, MODE, 1><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+        } else {
+            const int nd = dir == 1 ? c->g.ny : c->g.nz;
+            const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
+            dim3 grid((unsigned)((lines + c->walk_block - 1) / c->walk_block), (unsigned)((nd + c->walk_seg - 1) / c->walk_seg));
+            ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
+            if (dir == 1)
+                sweep_walk_kernel<R, UT, NS, 1, MODE, 1><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+            else
+                sweep_walk_kernel<R, UT, NS, 2, MODE, 1><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+        }
+        LAUNCH_CHECK();
+        return RF_OK;
+    }
+
     template <int MODE>
     static int sweep(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
+        if (c->flags & RF_TENO6) return sweep_teno<MODE>(c, m, dir, s);
         if (dir == 0 && sizeof(R) == 4) {
             // staged x sweep: a row per warp, four rows per block
             const int nrows = c->g.ny * c->g.nz;
@@ -1103,6 +1140,10 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d has a null context or buffer", i);
         }
+        if (c->flags & RF_TENO6) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d uses TENO6; batched ensembles run WENO3-Z", i);
+        }
         if (i == 0) {
             e->mech = c->mech;
             e->mslot = c->mslot;
@@ -1334,6 +1375,7 @@ struct AdjWs {
 };
 
 static int adj_ws(rf_ctx *c, AdjWs &w) {
+    if (c->flags & RF_TENO6) return fail(RF_EINVAL, "the discrete adjoint is built for WENO3-Z, not TENO6");
     const size_t n = (size_t)c->n, nv = c->nv, nq = c->nq;
     const size_t tot = nq * n + 6 * nv * n + 3 * n;
     if (!c->adj) {
@@ -1627,6 +1669,7 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
     for (int a = 0; a < 3; ++a)
         if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_rhs_noalloc: bc[%d] = %d unknown", a, g->bc[a]);
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_rhs_noalloc: precision %d unknown", precision);
+    if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_rhs_noalloc: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
     const long long n = (long long)g->nx * g->ny * g->nz;
     const int ns = m->ns, nv = ns + 4, nq = Q_X0 + 3 * ns;
     const size_t rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);

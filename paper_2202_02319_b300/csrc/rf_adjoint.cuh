@@ -434,15 +434,21 @@ __global__ void __launch_bounds__(64) adjoint_cell_kernel(int mslot, const __gri
 
 // ----------------------------------------------------------------------------- face adjoint
 
-// Reverse of weno3z(a, b, c): adds wbar * dW/d(a, b, c) into (ga, gb, gc).
-__device__ __forceinline__ void weno3z_adj(double a, double b, double c, double wbar, double &ga, double &gb, double &gc) {
+// Reverse of weno3z(a, b, c, e2): adds wbar * dW/d(a, b, c) into (ga, gb, gc), the
+// grid-scaled eps = e2 (a^2 + b^2 + c^2) + EPS_WENO included.  Without the eps path
+// the three derivatives sum to wbar (a common shift of a, b, c shifts W by as much);
+// the eps path's share of that sum, epsb (a + b + c) with epsb = wbar dW/d eps 2 e2,
+// is added to seps, so that callers can use the shift identity exactly.
+__device__ __forceinline__ void weno3z_adj(double a, double b, double c, double e2, double wbar, double &ga, double &gb,
+                                           double &gc, double &seps) {
     // w = q1 + omega0 (q0 - q1), q0 - q1 = (d0 - d1) / 2: every factor of the
     // reverse pass is a difference of f (no q - w of O(f) values that cancel)
     const double d0 = b - a, d1 = c - b;
     const double dq = 0.5 * (d0 - d1);
     const double b0 = d0 * d0, b1 = d1 * d1;
     const double tau = fabs(b1 - b0);
-    const double e0 = b0 + EPS_WENO, e1 = b1 + EPS_WENO;
+    const double eps = fma(e2, fma(a, a, fma(b, b, c * c)), EPS_WENO);
+    const double e0 = b0 + eps, e1 = b1 + eps;
     const double al0 = (1.0 / 3.0) * (1.0 + tau / e0), al1 = (2.0 / 3.0) * (1.0 + tau / e1);
     const double S = al0 + al1;
     const double om0 = al0 / S, om1 = al1 / S;
@@ -450,13 +456,16 @@ __device__ __forceinline__ void weno3z_adj(double a, double b, double c, double 
     const double al0b = om0b * om1 / S, al1b = -om0b * om0 / S;
     const double taub = al0b * (1.0 / 3.0) / e0 + al1b * (2.0 / 3.0) / e1;
     const double sg = b1 > b0 ? 1.0 : (b1 < b0 ? -1.0 : 0.0);
-    const double b0b = -al0b * (1.0 / 3.0) * tau / (e0 * e0) - sg * taub;
-    const double b1b = -al1b * (2.0 / 3.0) * tau / (e1 * e1) + sg * taub;
+    const double e0b = -al0b * (1.0 / 3.0) * tau / (e0 * e0), e1b = -al1b * (2.0 / 3.0) * tau / (e1 * e1);
+    const double b0b = e0b - sg * taub;
+    const double b1b = e1b + sg * taub;
+    const double epsb2 = 2.0 * e2 * (e0b + e1b);
     const double d0b = 0.5 * dqb + 2.0 * d0 * b0b;
     const double d1b = -0.5 * dqb + 2.0 * d1 * b1b;
-    ga += -d0b;
-    gb += 0.5 * wbar + d0b - d1b;
-    gc += 0.5 * wbar + d1b;
+    ga += -d0b + epsb2 * a;
+    gb += 0.5 * wbar + d0b - d1b + epsb2 * b;
+    gc += 0.5 * wbar + d1b + epsb2 * c;
+    seps += epsb2 * ((a + b) + c);
 }
 
 // One face of axis DIR per thread: face f (left face of cell f) with
@@ -547,13 +556,15 @@ __global__ void __launch_bounds__(128) adjoint_face_kernel(const __grid_constant
                 fp[o] = 0.5 * (F + alpha * Uv[o]);
                 fm[o] = 0.5 * (F - alpha * Uv[o]);
             }
-            double fpb[4] = {0, 0, 0, 0}, fmb[4] = {0, 0, 0, 0};
-            weno3z_adj(fp[0], fp[1], fp[2], -Gb[v], fpb[0], fpb[1], fpb[2]);
-            weno3z_adj(fm[3], fm[2], fm[1], -Gb[v], fmb[3], fmb[2], fmb[1]);
+            double fpb[4] = {0, 0, 0, 0}, fmb[4] = {0, 0, 0, 0}, sp = 0.0, sm = 0.0;
+            weno3z_adj(fp[0], fp[1], fp[2], m.weps[DIR], -Gb[v], fpb[0], fpb[1], fpb[2], sp);
+            weno3z_adj(fm[3], fm[2], fm[1], m.weps[DIR], -Gb[v], fmb[3], fmb[2], fmb[1], sm);
             // d Fhat / d alpha = (Uhat+ - Uhat-) / 2 is a difference of two
-            // reconstructions; the partial derivatives of each reconstruction sum to
-            // one, so a reference value U_L can be taken out of the sum exactly,
-            // which keeps it free of cancellation between O(U) terms.
+            // reconstructions; apart from the eps path the partial derivatives of each
+            // reconstruction sum to its weight, so a reference value U_L can be taken
+            // out of the sum exactly, which keeps it free of cancellation between O(U)
+            // terms; the eps paths' share (sp, sm) is added back with U_L.
+            alphab += 0.5 * Uv[1] * (sp - sm);
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const double Fb = 0.5 * (fpb[o] + fmb[o]);

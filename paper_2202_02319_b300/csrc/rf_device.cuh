@@ -66,6 +66,7 @@ struct Member {
     int nx, ny, nz;
     int bc[3];
     double h[3], invh[3];
+    double weps[3];              // h^2 / 3 per axis: the WENO3-Z eps is weps (a^2 + b^2 + c^2) + EPS_WENO
     long long n;                 // cells
     const double *U;             // stage input state (FP64, [nv][n])
     const double *Un;            // state at the start of the step (stage update)

@@ -13,7 +13,7 @@
 namespace rf {
 
 enum SweepMode { MODE_ACCUM = 0, MODE_RHS = 1, MODE_STAGE = 2 };
-enum Flags { F_NO_INVISCID = 1, F_NO_VISCOUS = 2, F_NO_CHEM = 4, F_NO_LASER = 8 };
+enum Flags { F_NO_INVISCID = 1, F_NO_VISCOUS = 2, F_NO_CHEM = 4, F_NO_LASER = 8, F_TENO6 = 16 };
 
 __device__ __forceinline__ int map_idx(int i, int n, int bc) {
     if (i < 0) return bc == 0 ? i + n * ((n - 1 - i) / n) : 0;
@@ -465,20 +465,24 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 5) cell_state_kernel
 
 // ----------------------------------------------------------------------------- face flux
 
-// WENO3-Z value at i+1/2 from (f_{i-1}, f_i, f_{i+1}) with d = (1/3, 2/3), p = 1.
-// The Z weights alpha_k = d_k (1 + tau / (beta_k + eps)) are formed after
+// WENO3-Z value at i+1/2 from (f_{i-1}, f_i, f_{i+1}) = (a, b, c) with d = (1/3, 2/3),
+// p = 1 and the grid-scaled eps = e2 (a^2 + b^2 + c^2) + EPS_WENO, e2 = h^2 / 3 (h the
+// spacing along the sweep): of order h^2 relative to the values' squares, which keeps
+// third order at smooth extrema and makes the weights independent of each variable's
+// scale.  The Z weights alpha_k = d_k (1 + tau / (beta_k + eps)) are formed after
 // multiplying both by (beta_0 + eps)(beta_1 + eps) / S^2, S = beta_0 + beta_1 + 2 eps:
 // omega_0 = d0 b1 (b0 + t) / (d0 b1 (b0 + t) + d1 b0 (b1 + t)) with b_k = (beta_k + eps) / S,
 // t = tau / S.  Every scaled quantity lies in [0, 2], so the weights cannot overflow
-// even in FP32, where tau / (beta + 1e-30) would for any |f_{i+1} - f_i| above ~2e4.
+// even in FP32 (values up to |f| ~ 1e19 there).
 template <typename R>
-__device__ __forceinline__ R weno3z(R a, R b, R c) {
+__device__ __forceinline__ R weno3z(R a, R b, R c, R e2) {
     const R q0 = fma(R(-0.5), a, R(1.5) * b);
     const R q1 = R(0.5) * b + R(0.5) * c;
     const R d0 = b - a, d1 = c - b;
     const R beta0 = d0 * d0, beta1 = d1 * d1;
-    const R iS = rcp(beta0 + beta1 + R(2.0 * EPS_WENO));
-    const R b0 = (beta0 + R(EPS_WENO)) * iS, b1 = (beta1 + R(EPS_WENO)) * iS;
+    const R eps = fma(e2, fma(a, a, fma(b, b, c * c)), R(EPS_WENO));
+    const R iS = rcp(beta0 + beta1 + R(2) * eps);
+    const R b0 = (beta0 + eps) * iS, b1 = (beta1 + eps) * iS;
     const R t = fabs(beta1 - beta0) * iS;
     const R a0 = R(1.0 / 3.0) * b1 * (b0 + t);
     const R a1 = R(2.0 / 3.0) * b0 * (b1 + t);
@@ -500,11 +504,12 @@ __device__ __forceinline__ double rcp_face(double x) { return rcp64(x); }
 // omega0 q0 + omega1 q1 = q1 + omega0 (d0 - d1)/2.  S >= 2 eps and a0 + a1 >= 1/12 are
 // normal, so the SFU reciprocals apply.
 template <>
-__device__ __forceinline__ float weno3z<float>(float a, float b, float c) {
+__device__ __forceinline__ float weno3z<float>(float a, float b, float c, float e2) {
     const float d0 = b - a, d1 = c - b;
     const float beta0 = d0 * d0, beta1 = d1 * d1;
-    const float iS = rcp_approx((beta0 + beta1) + (float)(2.0 * EPS_WENO));
-    const float eS = (float)EPS_WENO * iS;
+    const float eps = fmaf(e2, fmaf(a, a, fmaf(b, b, c * c)), (float)EPS_WENO);
+    const float iS = rcp_approx((beta0 + beta1) + 2.0f * eps);
+    const float eS = eps * iS;
     const float b0 = fmaf(beta0, iS, eS), b1 = fmaf(beta1, iS, eS);
     const float t = fabsf(beta1 - beta0) * iS;
     const float a0 = (1.0f / 3.0f) * (b1 * (b0 + t));
@@ -514,16 +519,17 @@ __device__ __forceinline__ float weno3z<float>(float a, float b, float c) {
 }
 
 // The same value in FP64.  The weights are invariant under a common scale of the
-// betas, so S is normalised by the exact power of two 2^-E(S) (E the exponent of S,
-// read from its bits): no rounding, and no division.  a0 + a1 lies in [1/12, 4], so
-// the one remaining reciprocal is the Newton-Raphson rcp64.
+// betas and eps, so S is normalised by the exact power of two 2^-E(S) (E the exponent
+// of S, read from its bits): no rounding, and no division.  a0 + a1 lies in [1/12, 4],
+// so the one remaining reciprocal is the Newton-Raphson rcp64.
 template <>
-__device__ __forceinline__ double weno3z<double>(double a, double b, double c) {
+__device__ __forceinline__ double weno3z<double>(double a, double b, double c, double e2) {
     const double d0 = b - a, d1 = c - b;
     const double beta0 = d0 * d0, beta1 = d1 * d1;
-    const double S = (beta0 + beta1) + 2.0 * EPS_WENO;
+    const double eps = fma(e2, fma(a, a, fma(b, b, c * c)), EPS_WENO);
+    const double S = (beta0 + beta1) + 2.0 * eps;
     const double iS = __hiloint2double((2046 - ((__double2hiint(S) >> 20) & 0x7ff)) << 20, 0);
-    const double eS = EPS_WENO * iS;
+    const double eS = eps * iS;
     const double b0 = fma(beta0, iS, eS), b1 = fma(beta1, iS, eS);
     const double t = fabs(beta1 - beta0) * iS;
     const double a0 = (1.0 / 3.0) * (b1 * (b0 + t));
@@ -531,6 +537,128 @@ __device__ __forceinline__ double weno3z<double>(double a, double b, double c) {
     const double om0 = a0 * rcp64(a0 + a1);
     return fma(om0, 0.5 * (d0 - d1), fma(0.5, d1, b));
 }
+
+// ----------------------------------------------------------------------------- TENO6
+
+// TENO6 value at i+1/2 from f0..f5 = f_{i-2} .. f_{i+3} (after Fu, Hu and Adams, J.
+// Comput. Phys. 305 (2016)): candidate stencils S0 = {i-1, i, i+1}, S1 = {i, i+1, i+2},
+// S2 = {i-2, i-1, i}, S3 = {i, i+1, i+2, i+3} with optimal weights d = (9, 6, 1, 4) / 20;
+// Jiang-Shu indicators beta_k and beta_6 of the whole stencil; tau = |beta_6 - (beta_1 +
+// beta_2 + 4 beta_0) / 6|; stencil k is kept where chi_k = gamma_k / sum gamma >= C_T,
+// gamma_k = (1 + tau / (beta_k + eps))^6; the value is sum over kept k of d_k q_k,
+// normalised by the kept d_k.
+//
+// Everything is written in the first differences e_m = f_{m+1} - f_m (exact for
+// neighbouring values within a factor two), so that a constant is reproduced exactly
+// and FP32 indicators of smooth data are not swamped by the rounding of O(f) values:
+//   q_k - f_i:  (e1 + 2 e2)/6, (4 e2 - e3)/6, (5 e1 - 2 e0)/6, (9 e2 - 4 e3 + e4)/12,
+//   beta_0 = 13/12 (e2 - e1)^2 + 1/4 (e1 + e2)^2,
+//   beta_1 = 13/12 (e3 - e2)^2 + 1/4 (e3 - 3 e2)^2,
+//   beta_2 = 13/12 (e1 - e0)^2 + 1/4 (3 e1 - e0)^2,
+//   beta_3 = 1/36 (11 e2 - 7 e3 + 2 e4)^2 + 13/12 (3 e3 - 2 e2 - e4)^2 + 781/720 (e2 - 2 e3 + e4)^2,
+//   beta_6 = sum_k D_k (L_k . e)^2, an exact LDL^T factorisation of the six-point form
+// (the indicators are sums of squares, so they cannot round below zero).  The cut test
+// chi_k >= C_T is taken without forming gamma (which overflows): with b_k = beta_k + eps,
+// s_k = gamma_k / gamma_max = b_min (b_k + tau) / (b_k (b_min + tau)) lies in (0, 1] and
+// chi_k >= C_T  <=>  s_k^6 >= C_T sum_m s_m^6; b and tau are scaled by one exact power of
+// two first, so the products cannot overflow.
+constexpr double TENO_CT = 1.0e-7;
+constexpr double TENO_EPS = 1.0e-30;
+
+__device__ __forceinline__ float pow2_scale(float x) {       // 2^-E(x) for normal x > 0
+    return __uint_as_float((unsigned)(254 - ((__float_as_uint(x) >> 23) & 0xff)) << 23);
+}
+__device__ __forceinline__ double pow2_scale(double x) {
+    return __hiloint2double((2046 - ((__double2hiint(x) >> 20) & 0x7ff)) << 20, 0);
+}
+__device__ __forceinline__ float rdiv(float a, float b) { return a * rcp_approx(b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
+
+template <typename R>
+__device__ __forceinline__ R teno6(R f0, R f1, R f2, R f3, R f4, R f5) {
+    const R e0 = f1 - f0, e1 = f2 - f1, e2 = f3 - f2, e3 = f4 - f3, e4 = f5 - f4;
+    const R q0 = (e1 + R(2) * e2) * R(1.0 / 6.0);
+    const R q1 = fma(R(4), e2, -e3) * R(1.0 / 6.0);
+    const R q2 = fma(R(5), e1, R(-2) * e0) * R(1.0 / 6.0);
+    const R q3 = (fma(R(9), e2, R(-4) * e3) + e4) * R(1.0 / 12.0);
+    auto sq = [](R x) { return x * x; };
+    const R b0 = fma(R(13.0 / 12.0), sq(e2 - e1), R(0.25) * sq(e1 + e2));
+    const R b1 = fma(R(13.0 / 12.0), sq(e3 - e2), R(0.25) * sq(fma(R(-3), e2, e3)));
+    const R b2 = fma(R(13.0 / 12.0), sq(e1 - e0), R(0.25) * sq(fma(R(3), e1, -e0)));
+    const R b3 = fma(R(1.0 / 36.0), sq(fma(R(11), e2, fma(R(-7), e3, R(2) * e4))),
+                     fma(R(13.0 / 12.0), sq(fma(R(3), e3, fma(R(-2), e2, -e4))),
+                         R(781.0 / 720.0) * sq(fma(R(-2), e3, e2 + e4))));
+    // six-point indicator: D_k (L_k . e)^2, L_k with unit leading coefficient
+    const R l0 = fma(R(-3.3800293620919937), e1, fma(R(4.137755308541131), e2,
+                 fma(R(-2.2318538224071762), e3, fma(R(0.4518745009732172), e4, e0))));
+    const R l1 = fma(R(-1.8788632502196132), e2, fma(R(1.2398246217680282), e3, fma(R(-0.2835945203123665), e4, e1)));
+    const R l2 = fma(R(-0.8641384480158466), e3, fma(R(0.22441845180562248), e4, e2));
+    const R l3 = fma(R(-0.3841978250666033), e4, e3);
+    const R b6 = fma(R(2.2468501984126985), sq(l0), fma(R(3.6320275079835525), sq(l1),
+                 fma(R(4.2138861378223531), sq(l2), fma(R(1.0316113515772065), sq(l3), R(0.038978122273068759) * sq(e4)))));
+    const R tau = fabs(b6 - (b1 + b2 + R(4) * b0) * R(1.0 / 6.0));
+    const R c0 = b0 + R(TENO_EPS), c1 = b1 + R(TENO_EPS), c2 = b2 + R(TENO_EPS), c3 = b3 + R(TENO_EPS);
+    const R cmin = fmin(fmin(c0, c1), fmin(c2, c3));
+    const R sc = pow2_scale(fmax(fmax(fmax(c0, c1), fmax(c2, c3)), tau));
+    const R ts = tau * sc, ms = cmin * sc, mt = ms + ts;
+    auto ratio = [&](R c) -> R {
+        if (c <= cmin) return R(1);
+        const R cs = c * sc;
+        const R den = cs * mt;
+        return den > R(0) ? rdiv(ms * (cs + ts), den) : R(1);
+    };
+    auto p6 = [&](R x) { const R x2 = x * x; return sq(x2 * x); };
+    const R p0 = p6(ratio(c0)), p1 = p6(ratio(c1)), p2 = p6(ratio(c2)), p3 = p6(ratio(c3));
+    const R lim = R(TENO_CT) * ((p0 + p1) + (p2 + p3));
+    const R w0 = p0 >= lim ? R(9.0 / 20.0) : R(0), w1 = p1 >= lim ? R(6.0 / 20.0) : R(0);
+    const R w2 = p2 >= lim ? R(1.0 / 20.0) : R(0), w3 = p3 >= lim ? R(4.0 / 20.0) : R(0);
+    const R num = fma(w0, q0, fma(w1, q1, fma(w2, q2, w3 * q3)));
+    return f2 + rdiv(num, (w0 + w1) + (w2 + w3));
+}
+
+// Stencil of one face along DIR read from global memory for the six-point TENO6
+// flux: cells o = 0..5 are f-3 .. f+2 (L = f-1 at o = 2, R = f at o = 3).
+template <typename R, typename UT, int DIR>
+struct GlobalStencil6 {
+    const UT *__restrict__ U;
+    const R *__restrict__ Q;
+    long long n;
+    long long id[6];
+    long long tp[3], tm[3];
+
+    __device__ __forceinline__ GlobalStencil6(const Member &m, const UT *U_, const R *Q_, const int (&cc)[3])
+        : U(U_), Q(Q_), n(m.n) {
+        const long long st[3] = {1, m.nx, (long long)m.nx * m.ny};
+        const int nd = DIR == 0 ? m.nx : (DIR == 1 ? m.ny : m.nz);
+        const long long base = (long long)cc[0] * st[0] + (long long)cc[1] * st[1] + (long long)cc[2] * st[2] -
+                               (long long)cc[DIR] * st[DIR];
+#pragma unroll
+        for (int o = 0; o < 6; ++o) id[o] = base + (long long)map_idx(cc[DIR] + o - 3, nd, m.bc[DIR]) * st[DIR];
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            if (t == DIR) {
+                tp[t] = tm[t] = 0;
+                continue;
+            }
+            const int nt = t == 0 ? m.nx : (t == 1 ? m.ny : m.nz);
+            tp[t] = (long long)(map_idx(cc[t] + 1, nt, m.bc[t]) - cc[t]) * st[t];
+            tm[t] = (long long)(map_idx(cc[t] - 1, nt, m.bc[t]) - cc[t]) * st[t];
+        }
+    }
+    __device__ __forceinline__ R u(int v, int o) const { return (R)U[v * n + id[o]]; }
+    __device__ __forceinline__ R q(int f, int o) const { return Q[f * n + id[o]]; }
+    __device__ __forceinline__ R qt(int f, int o, int t, bool plus) const { return Q[f * n + id[o] + (plus ? tp[t] : tm[t])]; }
+};
+
+// The four-cell view (o = 0..3 as f-2 .. f+1) of a six-cell stencil, for the
+// diffusive flux, which reads L and R and their tangential neighbours only.
+template <class S>
+struct InnerFour {
+    const S &s;
+    __device__ __forceinline__ auto u(int v, int o) const { return s.u(v, o + 1); }
+    __device__ __forceinline__ auto q(int f, int o) const { return s.q(f, o + 1); }
+    __device__ __forceinline__ auto qt(int f, int o, int t, bool plus) const { return s.qt(f, o + 1, t, plus); }
+};
 
 // Stencil of one face along DIR read from global memory.  Cells o = 0..3 are
 // f-2, f-1 (L), f (R), f+1 along DIR; qt reads the tangential neighbours of L or R.
@@ -687,6 +815,7 @@ __device__ __forceinline__ void face_invisc(const Member &m, const S &st, R (&G)
         // f+- = (F(U) +- alpha U) / 2 = (u_n/2 +- alpha/2) U + (p/2 or p u_n/2 for the
         // momentum along DIR and the energy)
         const R ha = R(0.5) * alpha;
+        const R e2 = (R)m.weps[DIR];
         R lp[4], lm[4], hp[4], hpu[4];
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
@@ -717,9 +846,62 @@ __device__ __forceinline__ void face_invisc(const Member &m, const S &st, R (&G)
                     fm[o] += hpu[o];
                 }
             }
-            G[v] = -(weno3z<R>(fp[0], fp[1], fp[2]) + weno3z<R>(fm[3], fm[2], fm[1]));
+            G[v] = -(weno3z<R>(fp[0], fp[1], fp[2], e2) + weno3z<R>(fm[3], fm[2], fm[1], e2));
         }
     }
+}
+
+// Inviscid part with TENO6 on a six-cell stencil (o = 0..5, L = 2, R = 3): f+ from
+// cells f-3 .. f+2, f- mirrored, alpha the largest |u_n| + c of the six cells.
+template <typename R, int NS, int DIR, class S>
+__device__ __forceinline__ void face_invisc_teno(const Member &m, const S &st, R (&G)[NS + 4], R &rhoL, R &rhoR) {
+    constexpr int NV = NS + 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    rhoL = 0;
+    rhoR = 0;
+    if (!(m.flags & F_NO_INVISCID)) {
+        R un[6], hp[6];
+        R alpha = 0;
+#pragma unroll
+        for (int o = 0; o < 6; ++o) {
+            un[o] = st.q(Q_U + DIR, o);
+            hp[o] = R(0.5) * st.q(Q_P, o);
+            const R lam = fabs(un[o]) + st.q(Q_C, o);
+            alpha = lam > alpha ? lam : alpha;
+        }
+        const R ha = R(0.5) * alpha;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R fp[6], fm[6];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const R Uv = st.u(v, o);
+                if (v < NS) {
+                    if (o == 2) rhoL += Uv;
+                    if (o == 3) rhoR += Uv;
+                }
+                const R h = R(0.5) * un[o];
+                R extra = 0;
+                if (v == NS + DIR) extra = hp[o];
+                if (v == NS + 3) extra = hp[o] * un[o];
+                fp[o] = fma(h + ha, Uv, extra);
+                fm[o] = fma(h - ha, Uv, extra);
+            }
+            G[v] = -(teno6<R>(fp[0], fp[1], fp[2], fp[3], fp[4], fp[5]) + teno6<R>(fm[5], fm[4], fm[3], fm[2], fm[1], fm[0]));
+        }
+    }
+}
+
+// Face flux with TENO6 from global memory.
+template <typename R, typename UT, int NS, int DIR>
+__device__ __forceinline__ void face_flux_teno(const Member &m, const UT *__restrict__ U, const R *__restrict__ Q,
+                                               const int (&cc)[3], R (&G)[NS + 4]) {
+    const GlobalStencil6<R, UT, DIR> st(m, U, Q, cc);
+    R rhoL, rhoR;
+    face_invisc_teno<R, NS, DIR>(m, st, G, rhoL, rhoR);
+    const InnerFour<GlobalStencil6<R, UT, DIR>> in{st};
+    face_visc<R, NS, DIR, true>(m, in, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
 }
 
 template <typename R, int NS>
@@ -800,7 +982,7 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
 
 // x sweep: each block row group processes its rows in chunks of W faces; face
 // f = c W + lx goes to slot lx+1, slot 0 carries the previous chunk's last face.
-template <typename R, typename UT, int NS, int MODE>
+template <typename R, typename UT, int NS, int MODE, int SCHEME = 0>
 __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m, int blk, int W, int rpb,
                                               unsigned char *smem_raw) {
     constexpr int NV = NS + 4;
@@ -824,7 +1006,8 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
         if (active && (f < nx || (f == nx && !periodic))) {
             R G[NV];
             const int cc[3] = {f, j, k};
-            face_flux<R, UT, NS, 0>(m, U, Q, cc, G);
+            if (SCHEME == 1) face_flux_teno<R, UT, NS, 0>(m, U, Q, cc, G);
+            else face_flux<R, UT, NS, 0>(m, U, Q, cc, G);
 #pragma unroll
             for (int v = 0; v < NV; ++v) slot(v, lx + 1) = G[v];
             if (f == 0) {
@@ -849,16 +1032,17 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
     }
 }
 
-template <typename R, typename UT, int NS, int MODE>
+// SCHEME 0: WENO3-Z, 1: TENO6
+template <typename R, typename UT, int NS, int MODE, int SCHEME = 0>
 __global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_constant__ Member m,
                                                       int W, int rpb) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_x_block<R, UT, NS, MODE>(M, m, blockIdx.x, W, rpb, smem_raw);
+    sweep_x_block<R, UT, NS, MODE, SCHEME>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
 
 // y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
-template <typename R, typename UT, int NS, int DIR, int MODE>
+template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0>
 __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member &m, long long lblk, int sblk, int seg) {
     constexpr int NV = NS + 4;
     const long long line = lblk * blockDim.x + threadIdx.x;
@@ -883,7 +1067,8 @@ __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member 
     // whichever segment computes it (bitwise independence of the segmentation)
     for (int c = c0 - 1; c < c1; ++c) {
         cc[DIR] = c + 1;
-        face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
+        if (SCHEME == 1) face_flux_teno<R, UT, NS, DIR>(m, U, Q, cc, Gn);
+        else face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
         if (c >= c0) {
             R dG[NV];
 #pragma unroll
@@ -895,11 +1080,11 @@ __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member 
     }
 }
 
-template <typename R, typename UT, int NS, int DIR, int MODE>
+template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0>
 __global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid_constant__ Member m,
                                                          int seg) {
     const MechDev &M = c_mech[mslot];
-    sweep_walk_block<R, UT, NS, DIR, MODE>(M, m, blockIdx.x, blockIdx.y, seg);
+    sweep_walk_block<R, UT, NS, DIR, MODE, SCHEME>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
 // ----------------------------------------------------------------------------- staged y / z sweep (FP32 bulk)
