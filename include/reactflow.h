@@ -66,11 +66,19 @@ enum rf_bc {
     RF_BC_EXTRAPOLATE = 1 /* zero-gradient ghost cells (copies of the edge cell) */
 };
 
-enum rf_flags {           /* switches for tests; 0 = full method */
+enum rf_flags {           /* term switches for tests (0 = full method) and the scheme */
     RF_NO_INVISCID = 1,
     RF_NO_VISCOUS = 2,
     RF_NO_CHEMISTRY = 4,
-    RF_NO_LASER = 8
+    RF_NO_LASER = 8,
+    RF_TENO6 = 16,        /* inviscid fluxes by TENO6 (Results, Solver; Methods, Numerical
+                             method: the paper's sixth-order targeted ENO scheme, after Fu,
+                             Hu and Adams 2016) instead of WENO3-Z: candidate stencils of
+                             three and four cells inside a six-cell stencil (halo 3), kept
+                             where their smoothness share chi_k >= 1e-7, LLF alpha over the
+                             six cells.  Single-grid RHS and RK steps in both precisions;
+                             rejected by rf_ensemble_create and the adjoint entry points */
+    RF_FLAGS_ALL = 31
 };
 
 /* Mechanism description (host arrays, copied by rf_init_mechanism).
