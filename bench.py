@@ -255,8 +255,14 @@ def run_ours(args):
     value64 = world * ncell * 3 * args.fp64_steps / (ms64 * 1e-3)
     del ctx64, U64, T64
 
+    # --- TENO6 (the paper's sixth-order scheme) on the same workload, both precisions
+    teno = run_teno_leg(args, mech, case, prim, dev) if args.teno_steps > 0 else None
+
     # --- batched ensemble (64 members of uneven size): members/s per launch mode
     ens = run_ensemble_leg(args, dev) if args.ensemble_members > 0 else None
+
+    # --- minimum ignition energy: bisection rounds over batched ensembles
+    mie = run_mie_leg(args, dev) if args.mie_members > 0 else None
 
     # --- discrete adjoint: checkpointed ignition gradient of one 64^3 member (FP64)
     adj = run_adjoint_leg(args, dev) if args.adjoint_steps > 0 else None
@@ -332,6 +338,8 @@ def run_ours(args):
                  "kernels": k64},
         "kernels": kernels,
         "roofline": roofline,
+        "teno6": teno,
+        "min_ignition_energy": mie,
         "ensemble": ens,
         "adjoint": adj,
         "peaks_measured": {"fp64_tflops": round(fp64_peak, 4), "fp32_tflops": round(fp32_peak, 3),
@@ -350,6 +358,74 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- TENO6 leg
+
+def run_teno_leg(args, mech, case, prim, dev):
+    """Cell-updates/s of the same workload with the inviscid fluxes by TENO6 (six-cell
+    stencils, sweeps from global memory), mixed and FP64, CUDA events on the
+    launching stream, per-kernel times from the library's profile events."""
+    import torch
+    from paper_2202_02319_b300 import native as nv
+    ns = case.mech.n_species
+    ncell = case.grid.ncells
+    las = case.laser.as_tuple()
+    out = {}
+    for name, prec, steps in (("mixed", nv.RF_MIXED, args.teno_steps), ("fp64", nv.RF_FP64, max(1, args.teno_steps // 2))):
+        ctx = nv.create_ctx(mech, case.grid, prec, nv.RF_TENO6)
+        U = torch.empty((ns + 4, ncell), dtype=torch.float64, device=dev)
+        T = torch.empty(ncell, dtype=torch.float64, device=dev)
+        nv.init_state(ctx, prim, U, T)
+        t = torch.zeros(1, dtype=torch.float64, device=dev)
+        nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        nv.check(ctx)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(steps):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        nv.set_option(ctx, "profile", 1)
+        nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        prof = nv.profile_read(ctx)
+        nv.set_option(ctx, "profile", 0)
+        nv.check(ctx)
+        out[name] = {"value": ncell * 3 * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "steps": steps,
+                     "kernels_ms_per_launch": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]}}
+        del ctx, U, T
+        torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------- ignition leg
+
+def run_mie_leg(args, dev):
+    """Minimum-ignition-energy bisection: `mie_members` copies of the jet state at
+    `mie_n`^3 per round, laser energies spread in the bracket, one batched
+    ensemble (CUDA graph, mixed precision) per round; members/s of the search."""
+    import time
+    import torch
+    from paper_2202_02319_b300 import ignition, native as nv, synth
+    case = synth.case_jet(0, args.mie_n)
+    case.laser.t0 = 2e-8
+    runner = ignition.EnsembleIgnition(case, args.mie_members, args.mie_steps, 1e-9, precision=nv.RF_MIXED,
+                                       mode=nv.ENS_GRAPH, device=dev)
+    runner.run([case.laser.E] * args.mie_members)          # warm-up (captures the graphs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ignition.minimum_ignition_energy(runner, 1e-3, 40e-3, rounds=args.mie_rounds)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    n = len(res.rounds) * args.mie_members
+    return {"members": args.mie_members, "cells_per_member": case.grid.ncells, "steps": args.mie_steps,
+            "rounds": len(res.rounds), "bracket_J": list(res.bracket), "seconds": round(el, 3),
+            "members_per_s": n / el, "cell_updates_per_s": n * case.grid.ncells * 3 * args.mie_steps / el,
+            "timing": "host clock around synchronised rounds (ensemble set-up and diagnostics included)"}
 
 
 # ----------------------------------------------------------------------------- adjoint leg
@@ -560,6 +636,11 @@ def main():
     ap.add_argument("--cpu-full", action="store_true", help="also time one oracle RHS on the whole box")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--teno-steps", type=int, default=4)
+    ap.add_argument("--mie-members", type=int, default=8)
+    ap.add_argument("--mie-n", type=int, default=48)
+    ap.add_argument("--mie-steps", type=int, default=40)
+    ap.add_argument("--mie-rounds", type=int, default=2)
     ap.add_argument("--ensemble-members", type=int, default=64)
     ap.add_argument("--ensemble-steps", type=int, default=10)
     ap.add_argument("--adjoint-n", type=int, default=64)
