@@ -86,7 +86,7 @@ enum rf_flags {           /* term switches for tests (0 = full method) and the s
  * mixture-averaged diffusion) and Methods, Combustion chemistry (finite-rate
  * Arrhenius reactions).  Ns in {1, 2, 4, 9}; Nr <= 32; every species uses the
  * same T_mid; at most 3 reactant and 3 product molecules per reaction.  At most
- * six mechanisms can be in use on a device at a time (each occupies a slot of
+ * five mechanisms can be in use on a device at a time (each occupies a slot of
  * constant memory from its first context until rf_free_mechanism). */
 typedef struct {
     int n_species;            /* Ns */
@@ -104,6 +104,19 @@ typedef struct {
     const int *nu_f;          /* [Nr][Ns] reactant stoichiometric coefficients */
     const int *nu_r;          /* [Nr][Ns] product stoichiometric coefficients */
     const int *reversible;    /* [Nr] 1 = reversible (k_r = k_f / K_c), 0 = irreversible */
+    /* Pressure-dependent reactions (the paper's CH4/O2 mechanisms, Methods - Combustion
+     * chemistry, contain them; CHEMKIN conventions).  rxn_type NULL: every reaction is
+     * elementary (the other five arrays are then ignored).  At most 8 reactions of a
+     * mechanism may be pressure dependent. */
+    const int *rxn_type;      /* [Nr] 0 elementary; 1 third body: both directions times
+                                 [M] = sum_s efficiency_s C_s; 2 Lindemann, 3 Troe fall-off:
+                                 k = k_inf P_r / (1 + P_r) F, P_r = k_0 [M] / k_inf, with
+                                 (A, b, Theta) the high-pressure k_inf */
+    const double *efficiency; /* [Nr][Ns] third-body efficiencies (rows of type 1..3) */
+    const double *A0;         /* [Nr] low-pressure k_0 = A0 T^b0 exp(-Theta0 / T), (m^3/mol)^order / s */
+    const double *b0;         /* [Nr] */
+    const double *Theta0;     /* [Nr] K */
+    const double *troe;       /* [Nr][4] alpha, T***, T*, T** of the Troe broadening factor (type 3) */
 } rf_mech_desc;
 
 typedef struct {

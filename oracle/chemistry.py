@@ -15,6 +15,19 @@ kinetics, no third-body or fall-off terms):
 
 Concentration products are formed by repeated multiplication over the
 species that take part, so that species with zero coefficient never enter.
+
+Pressure-dependent reactions (the paper's CH4/O2 mechanisms use them and omits
+the details; reading: the CHEMKIN conventions):
+  third body:  q_j = [M]_j (k_f prod C^nu' - k_r prod C^nu''),  [M]_j = sum_s eps_sj C_s
+  fall-off:    k_f = k_inf P_r / (1 + P_r) F,  P_r = k_0 [M]_j / k_inf, with
+               k_inf = A T^b exp(-Theta/T), k_0 = A0 T^b0 exp(-Theta0/T);
+               Lindemann F = 1; Troe
+               log10 F = log10 F_c / (1 + ((log10 P_r + c) / (n - 0.14 (log10 P_r + c)))^2),
+               F_c = (1 - alpha) exp(-T/T***) + alpha exp(-T/T*) + exp(-T**/T),
+               c = -0.4 - 0.67 log10 F_c, n = 0.75 - 1.27 log10 F_c;
+               no further [M] factor; k_r = k_f / K_c as for every reaction.
+The chemical time-step estimate (chemical_rate) differentiates at fixed [M]_j
+and fixed fall-off factor.
 """
 from __future__ import annotations
 
@@ -25,11 +38,52 @@ from .thermo import _bcast, h_RT, s_R, species_h
 
 
 def forward_rate_constants(mech: MechT, T: torch.Tensor) -> torch.Tensor:
-    """k_f [Nr, ...]."""
+    """k_f [Nr, ...] of the Arrhenius form (for a fall-off reaction, its
+    high-pressure limit k_inf)."""
     A = _bcast(mech.A, T)
     b = _bcast(mech.b, T)
     Th = _bcast(mech.Theta, T)
     return A * T[None] ** b * torch.exp(-Th / T[None])
+
+
+def third_body_concentration(mech: MechT, C: torch.Tensor, j: int) -> torch.Tensor:
+    """[M]_j = sum_s eps_sj C_s."""
+    out = torch.zeros_like(C[0])
+    for s in range(mech.ns):
+        out = out + mech.efficiency[j, s] * C[s]
+    return out
+
+
+def troe_factor(mech: MechT, j: int, T: torch.Tensor, Pr: torch.Tensor) -> torch.Tensor:
+    al, T3, T1, T2 = (float(x) for x in mech.troe[j])
+    Fc = (1.0 - al) * torch.exp(-T / T3) + al * torch.exp(-T / T1) + torch.exp(-T2 / T)
+    lFc = torch.log10(Fc)
+    c = -0.4 - 0.67 * lFc
+    n = 0.75 - 1.27 * lFc
+    x = torch.log10(Pr) + c
+    return 10.0 ** (lFc / (1.0 + (x / (n - 0.14 * x)) ** 2))
+
+
+def effective_rate_factors(mech: MechT, C: torch.Tensor, T: torch.Tensor) -> torch.Tensor:
+    """Per reaction the factor g_j multiplying the Arrhenius k_f in both directions:
+    1 (elementary), [M]_j (third body) or P_r/(1 + P_r) F (fall-off)."""
+    g = torch.ones((mech.nr,) + T.shape, dtype=T.dtype)
+    if mech.rxn_type is None:
+        return g
+    for j in range(mech.nr):
+        kind = int(mech.rxn_type[j])
+        if kind == 0:
+            continue
+        M = third_body_concentration(mech, C, j)
+        if kind == 1:
+            g[j] = M
+            continue
+        kinf = mech.A[j] * T ** mech.b[j] * torch.exp(-mech.Theta[j] / T)
+        k0 = mech.A0[j] * T ** mech.b0[j] * torch.exp(-mech.Theta0[j] / T)
+        Pr = k0 * M / kinf
+        F = troe_factor(mech, j, T, Pr) if kind == 3 else torch.ones_like(T)
+        g[j] = Pr / (1.0 + Pr) * F
+    return g
 
 
 def equilibrium_constants(mech: MechT, T: torch.Tensor) -> torch.Tensor:
@@ -58,7 +112,7 @@ def _conc_product(C: torch.Tensor, nu_row: torch.Tensor, skip: int = -1) -> torc
 
 def rates_of_progress(mech: MechT, C: torch.Tensor, T: torch.Tensor):
     """Returns (q, forward term, reverse term), each [Nr, ...]."""
-    kf = forward_rate_constants(mech, T)
+    kf = forward_rate_constants(mech, T) * effective_rate_factors(mech, C, T)
     Kc = equilibrium_constants(mech, T)
     fwd, rev = [], []
     for j in range(mech.nr):
@@ -100,7 +154,7 @@ def chemical_rate(mech: MechT, rho_s: torch.Tensor, T: torch.Tensor) -> torch.Te
     """max_s |d omega_s / d rho_s| at fixed T (diagonal of the chemical Jacobian),
     used by the time-step rule."""
     C = rho_s / _bcast(mech.W, T)
-    kf = forward_rate_constants(mech, T)
+    kf = forward_rate_constants(mech, T) * effective_rate_factors(mech, C, T)
     Kc = equilibrium_constants(mech, T)
     dnu = mech.nu_r - mech.nu_f
     best = torch.zeros_like(T)

@@ -27,6 +27,15 @@ class MechT:
     nu_f: torch.Tensor       # [Nr, Ns] (float)
     nu_r: torch.Tensor       # [Nr, Ns] (float)
     reversible: torch.Tensor  # [Nr] bool
+    # pressure-dependent reactions (None: all elementary): type [Nr] 0 elementary,
+    # 1 third body, 2 Lindemann, 3 Troe; efficiencies [Nr, Ns]; low-pressure
+    # Arrhenius A0, b0, Theta0 [Nr]; Troe alpha, T***, T*, T** [Nr, 4]
+    rxn_type: Optional[torch.Tensor] = None
+    efficiency: Optional[torch.Tensor] = None
+    A0: Optional[torch.Tensor] = None
+    b0: Optional[torch.Tensor] = None
+    Theta0: Optional[torch.Tensor] = None
+    troe: Optional[torch.Tensor] = None
 
     @property
     def ns(self) -> int:
@@ -63,10 +72,16 @@ class GridT:
 
 def from_synth(m) -> MechT:
     t = lambda a: torch.as_tensor(a, dtype=DT).clone()
+    opt = lambda a: None if a is None else t(a)
+    rt = getattr(m, "rxn_type", None)
     return MechT(W=t(m.W), elem=t(m.elem), nasa_low=t(m.nasa_low), nasa_high=t(m.nasa_high),
                  T_mid=t(m.T_mid), mu_ref=t(m.mu_ref), mu_exp=t(m.mu_exp), D_ref=t(m.D_ref),
                  A=t(m.A), b=t(m.b), Theta=t(m.Theta), nu_f=t(m.nu_f), nu_r=t(m.nu_r),
-                 reversible=torch.as_tensor(m.reversible).bool())
+                 reversible=torch.as_tensor(m.reversible).bool(),
+                 rxn_type=None if rt is None else torch.as_tensor(rt, dtype=torch.int64).clone(),
+                 efficiency=opt(getattr(m, "efficiency", None)), A0=opt(getattr(m, "A0", None)),
+                 b0=opt(getattr(m, "b0", None)), Theta0=opt(getattr(m, "Theta0", None)),
+                 troe=opt(getattr(m, "troe", None)))
 
 
 def grid_from_synth(g) -> GridT:

@@ -59,6 +59,7 @@ static constexpr int RF_MAX_DEVICES = 64;
 struct rf_mech {
     MechDev d;
     int ns, nr;
+    int npress;                      // pressure-dependent reactions
     int slot[RF_MAX_DEVICES];        // constant-memory slot per device, -1 if not uploaded
 };
 
@@ -315,6 +316,70 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             const int sp = M.prod[j][k];
             M.dnu_prod[j][k] = (int8_t)(d->nu_r[j * ns + sp] - d->nu_f[j * ns + sp]);
         }
+        M.pslot[j] = -1;
+        const int kind = d->rxn_type ? d->rxn_type[j] : 0;
+        if (kind < 0 || kind > 3) { delete m; return fail(RF_EINVAL, "rf_init_mechanism: rxn_type[%d] = %d unknown", j, kind); }
+        if (kind == 0) continue;
+        if (m->npress >= NPMAX) { delete m; return fail(RF_EINVAL, "rf_init_mechanism: more than %d pressure-dependent reactions", NPMAX); }
+        if (!d->efficiency || (kind >= 2 && (!d->A0 || !d->b0 || !d->Theta0)) || (kind == 3 && !d->troe)) {
+            delete m;
+            return fail(RF_EINVAL, "rf_init_mechanism: reaction %d of type %d lacks its efficiency / fall-off arrays", j, kind);
+        }
+        const int p = m->npress++;
+        M.ptype[j] = (int8_t)kind;
+        M.pslot[j] = (int8_t)p;
+        for (int s2 = 0; s2 < ns; ++s2) {
+            const double e = d->efficiency[j * ns + s2];
+            if (!(e >= 0.0)) { delete m; return fail(RF_EINVAL, "rf_init_mechanism: efficiency[%d][%d] = %g must be >= 0", j, s2, e); }
+            M.eff[p][s2] = e;
+            M.efff[p][s2] = (float)e;
+        }
+        if (kind >= 2) {
+            if (!(d->A0[j] > 0.0)) { delete m; return fail(RF_EINVAL, "rf_init_mechanism: A0[%d] = %g must be > 0", j, d->A0[j]); }
+            M.lnA0[p] = std::log(d->A0[j]);
+            M.b0[p] = d->b0[j];
+            M.Theta0[p] = d->Theta0[j];
+            M.lnA0f[p] = (float)M.lnA0[p];
+            M.b0f[p] = (float)M.b0[p];
+            M.Theta0f[p] = (float)M.Theta0[p];
+        }
+        if (kind == 3) {
+            const double *tr = d->troe + 4 * j;
+            if (!(tr[1] > 0.0 && tr[2] > 0.0)) { delete m; return fail(RF_EINVAL, "rf_init_mechanism: Troe T***, T* of reaction %d must be > 0", j); }
+            for (int k = 0; k < 4; ++k) {
+                M.troe[p][k] = tr[k];
+                M.troef[p][k] = (float)tr[k];
+            }
+        }
+    }
+    M.npress = m->npress;
+    // shape classes of the mixed path's rate-of-progress pass, and the species-major
+    // net coefficient lists (reactions ascending)
+    {
+        int nc[5] = {0, 0, 0, 0, 0};
+        auto cls = [&](int j) {
+            const int a = M.n_reac[j], b = M.n_prod[j];
+            if (!M.rev[j] || M.ptype[j] || a < 1 || a > 2 || b < 1 || b > 2) return 4;
+            return (a - 1) * 2 + (b - 1);
+        };
+        for (int j = 0; j < nr; ++j) ++nc[cls(j)];
+        M.cls_start[0] = 0;
+        for (int c = 0; c < 5; ++c) M.cls_start[c + 1] = (int8_t)(M.cls_start[c] + nc[c]);
+        int fill[5];
+        for (int c = 0; c < 5; ++c) fill[c] = M.cls_start[c];
+        for (int j = 0; j < nr; ++j) M.cls_rx[fill[cls(j)]++] = (int8_t)j;
+        int e = 0;
+        for (int s2 = 0; s2 < ns; ++s2) {
+            M.sp_start[s2] = (int16_t)e;
+            for (int j = 0; j < nr; ++j)
+                for (int k = 0; k < M.n_net[j]; ++k)
+                    if (M.net_sp[j][k] == s2) {
+                        M.sp_rx[e] = (int8_t)j;
+                        M.sp_nu[e] = M.net_nu[j][k];
+                        ++e;
+                    }
+        }
+        M.sp_start[ns] = (int16_t)e;
     }
     *out = m;
     return RF_OK;
@@ -489,9 +554,9 @@ struct Path {
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
 
     // kernel attributes, set once per context before any launch (or capture)
-    static int prepare(rf_ctx *) {
+    static int prepare(rf_ctx *c) {
         CUDA_TRY(cudaFuncSetAttribute(cell_state_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)cell_state_smem<R, NS>(128)));
+                                      (int)cell_state_smem_max<R, NS>(128, c->mech->nr)));
         if constexpr (sizeof(R) == 4) {
             const int sm = (int)walk_smem<R, NS>();
             CUDA_TRY(cudaFuncSetAttribute(sweep_walk_staged_kernel<NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -512,7 +577,7 @@ struct Path {
         const int B = 128;
         const long long nb = (m.c_hi - m.c_lo + B - 1) / B;
         if (nb <= 0) return RF_OK;
-        const size_t smem = cell_state_smem<R, NS>(B, m.want_rates != 0);
+        const size_t smem = cell_state_smem<R, NS>(B, m.want_rates != 0, c->mech->nr);
         ProfScope ps(c, PROF_CELL, s);
         cell_state_kernel<R, NS><<<(unsigned)nb, B, smem, s>>>(c->mslot, m, c->newton_maxit);
         LAUNCH_CHECK();
@@ -1031,7 +1096,7 @@ struct EnsPath {
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
 
     static int setup(rf_ensemble *e) {
-        e->smem_cell = cell_state_smem<R, NS>(128);
+        e->smem_cell = cell_state_smem_max<R, NS>(128, e->mech->nr);
         CUDA_TRY(cudaFuncSetAttribute(ens_cell_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem_cell));
         CUDA_TRY(cudaFuncSetAttribute(ens_x_kernel<R, UT, NS, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)std::max<size_t>(e->smem_x, 1)));
@@ -1056,7 +1121,7 @@ struct EnsPath {
         const int M = e->mslot;
         for (int k = 0; k < 3; ++k) {
             EnsDev E0 = ens_dev(e, e->nitems[0]);
-            ens_cell_kernel<R, NS><<<e->nitems[0], 128, cell_state_smem<R, NS>(128, k == 0), s>>>(M, E0, k);
+            ens_cell_kernel<R, NS><<<e->nitems[0], 128, cell_state_smem<R, NS>(128, k == 0, e->mech->nr), s>>>(M, E0, k);
             LAUNCH_CHECK();
             if (k == 0) {
                 ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);
@@ -1376,6 +1441,7 @@ struct AdjWs {
 
 static int adj_ws(rf_ctx *c, AdjWs &w) {
     if (c->flags & RF_TENO6) return fail(RF_EINVAL, "the discrete adjoint is built for WENO3-Z, not TENO6");
+    if (c->mech->npress > 0) return fail(RF_EINVAL, "the discrete adjoint is built for elementary reactions (the mechanism has %d pressure-dependent ones)", c->mech->npress);
     const size_t n = (size_t)c->n, nv = c->nv, nq = c->nq;
     const size_t tot = nq * n + 6 * nv * n + 3 * n;
     if (!c->adj) {

@@ -14,6 +14,7 @@ namespace rf {
 
 constexpr int NSMAX = 9;
 constexpr int NRMAX = 32;
+constexpr int NPMAX = 8;                  // pressure-dependent reactions per mechanism
 constexpr double RU = 8.314462618;    // J/mol/K
 constexpr double PATM = 101325.0;     // Pa
 constexpr double EPS_WENO = 1.0e-30;
@@ -24,7 +25,7 @@ enum StatusBits : int { ST_NEWTON = 1, ST_NONFINITE = 2, ST_RANGE = 4, ST_TIMEOU
 
 // Mechanism constants (species, NASA-7 sets, transport, compact reactions).
 struct MechDev {
-    int ns, nr, two_ranges, pad_;
+    int ns, nr, two_ranges, npress;            // npress: pressure-dependent reactions
     double Tmid;
     double W[NSMAX], invW[NSMAX], RW[NSMAX];   // R/W_s
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
@@ -53,12 +54,27 @@ struct MechDev {
     int8_t n_revf[NRMAX], revf[NRMAX][6];
     // net coefficient nu''_s - nu'_s of the species at each reactant / product position
     int8_t dnu_reac[NRMAX][3], dnu_prod[NRMAX][3];
+    // pressure-dependent reactions: ptype 0 elementary, 1 third body, 2 Lindemann,
+    // 3 Troe fall-off; pslot indexes the tables below (efficiencies of [M], the
+    // low-pressure Arrhenius ln A0, b0, Theta0, Troe alpha, T***, T*, T**)
+    int8_t ptype[NRMAX], pslot[NRMAX];
+    // reactions grouped by shape for the mixed path's rate-of-progress pass: classes
+    // 0..3 are reversible elementary reactions with (1, 1), (1, 2), (2, 1), (2, 2)
+    // reactant and product molecules, class 4 everything else; cls_rx[cls_start[c] ..
+    // cls_start[c + 1]) lists the reactions of class c
+    int8_t cls_start[6], cls_rx[NRMAX];
+    // species-major lists of the net coefficients (reactions ascending): species s
+    // takes nu = sp_nu[e] times q of reaction sp_rx[e] for e in [sp_start[s], sp_start[s + 1])
+    int16_t sp_start[NSMAX + 1];
+    int8_t sp_rx[NRMAX * 6], sp_nu[NRMAX * 6];
+    double eff[NPMAX][NSMAX], lnA0[NPMAX], b0[NPMAX], Theta0[NPMAX], troe[NPMAX][4];
+    float efff[NPMAX][NSMAX], lnA0f[NPMAX], b0f[NPMAX], Theta0f[NPMAX], troef[NPMAX][4];
 };
 
 // Mechanisms in use live in constant-memory slots; kernels receive the slot
 // index, so their constants are read through the constant cache and graph
 // nodes carry no large parameter block.
-constexpr int MECH_SLOTS = 6;
+constexpr int MECH_SLOTS = 5;             // 5 x sizeof(MechDev) within the 64 KB constant bank
 __constant__ MechDev c_mech[MECH_SLOTS];
 
 // One grid and the buffers of one evaluation or RK stage.

@@ -72,16 +72,90 @@ __device__ __forceinline__ SplitF split32(float x) {
 // per reaction, and the reverse rate stays in FP64.  sW accumulates
 // sum_j nu_sj q_j in the bulk type.  If want_rate, sD accumulates the diagonal of
 // d omega / d C and the function returns max_s |d omega_s / d rho_s|.
+// Factor g of a pressure-dependent reaction j (M.ptype[j] != 0) that multiplies its
+// Arrhenius k_f in both directions: [M] = sum_s eff_s C_s for a third body; for a
+// fall-off P_r / (1 + P_r) F with P_r = k_0 [M] / k_inf, written 1 / (1 + exp(-ln P_r))
+// from ln P_r = ln k_0 - ln k_inf + ln [M] (no quotient of rate constants that may
+// underflow), Lindemann F = 1, Troe log10 F = log10 F_c / (1 + (x / (n - 0.14 x))^2),
+// x = log10 P_r + c, c = -0.4 - 0.67 log10 F_c, n = 0.75 - 1.27 log10 F_c,
+// F_c = (1 - alpha) exp(-T/T***) + alpha exp(-T/T*) + exp(-T**/T).  akf is the exponent
+// of k_inf.  Bulk type throughout.
 template <typename R, int NS>
-__device__ __forceinline__ R chemistry(const MechDev &M, double lnT, double invT, const double *__restrict__ sG,
+__device__ __noinline__ R pressure_factor(const MechDev &M, int j, R akf, R T, R lnT, R invT,
+                                          const R *__restrict__ sCb, int stride) {
+    const int p = M.pslot[j];
+    R Mc = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Mc = fma(sizeof(R) == 8 ? (R)M.eff[p][s] : (R)M.efff[p][s], sCb[s * stride], Mc);
+    if (M.ptype[j] == 1) return Mc;
+    if (!(Mc > R(0))) return R(0);
+    const R a0 = sizeof(R) == 8 ? (R)(M.lnA0[p] + M.b0[p] * lnT - M.Theta0[p] * invT)
+                                : (R)(M.lnA0f[p] + M.b0f[p] * lnT - M.Theta0f[p] * invT);
+    const R lnPr = a0 - akf + log_(Mc);
+    R g = R(1) / (R(1) + exp_(-lnPr));
+    if (M.ptype[j] == 3) {
+        const R al = sizeof(R) == 8 ? (R)M.troe[p][0] : (R)M.troef[p][0];
+        const R T3 = sizeof(R) == 8 ? (R)M.troe[p][1] : (R)M.troef[p][1];
+        const R T1 = sizeof(R) == 8 ? (R)M.troe[p][2] : (R)M.troef[p][2];
+        const R T2 = sizeof(R) == 8 ? (R)M.troe[p][3] : (R)M.troef[p][3];
+        const R Fc = (R(1) - al) * exp_(-T / T3) + al * exp_(-T / T1) + exp_(-T2 * invT);
+        const R il10 = R(0.43429448190325182765);          // 1 / ln 10
+        const R lFc = log_(Fc) * il10;
+        const R c = R(-0.4) - R(0.67) * lFc, n = R(0.75) - R(1.27) * lFc;
+        const R x = lnPr * il10 + c;
+        const R y = x / (n - R(0.14) * x);
+        g *= exp_(lFc / (R(1) + y * y) * R(2.30258509299404568402));
+    }
+    return g;
+}
+
+// Rates of progress q_j of the reactions outside the shape classes (irreversible,
+// pressure dependent, three molecules on a side), mixed path, one at a time, into sQ.
+template <int NS>
+__device__ __noinline__ void chemistry_q_generic(const MechDev &M, double T, double lnT, double invT,
+                                                 const float *__restrict__ sCb, const double *__restrict__ sP,
+                                                 const double *__restrict__ sRr, float *__restrict__ sQ, int stride) {
+    const float lnTf = d2f(lnT), invTf = d2f(invT);
+    for (int i = M.cls_start[4]; i < M.cls_start[5]; ++i) {
+        const int j = M.cls_rx[i];
+        const float a = M.lnAf[j] + M.bf[j] * lnTf - M.Thetaf[j] * invTf;
+        float kf = expf(a);
+        if (M.ptype[j]) kf *= pressure_factor<float, NS>(M, j, a, d2f(T), lnTf, invTf, sCb, stride);
+        float cf = kf;
+        for (int k = 0; k < M.n_reac[j]; ++k) cf *= sCb[M.reac[j][k] * stride];
+        float q = cf;
+        if (M.rev[j]) {
+            const int nf = M.n_revf[j];
+            double pr = 1.0;
+#pragma unroll 1
+            for (int k = 0; k < nf; ++k) {
+                const int e = M.revf[j][k];
+                pr *= e < 16 ? sP[e * stride] : sRr[(e - 16) * stride];
+            }
+            q = d2f(fma(-f2d(kf), pr, f2d(cf)));
+        }
+        sQ[j * stride] = q;
+    }
+}
+
+template <typename R, int NS>
+__device__ __forceinline__ R chemistry(const MechDev &M, double T, double lnT, double invT, const double *__restrict__ sG,
                                        const R *__restrict__ sCb, const double *__restrict__ sP,
                                        const double *__restrict__ sRr, R *__restrict__ sW, R *__restrict__ sD,
                                        int stride, bool want_rate) {
     const R lnTb = narrow<R>(lnT), invTb = narrow<R>(invT);
+    const bool anyp = M.npress != 0;
     for (int j = 0; j < M.nr; ++j) {
         R kf;
-        if (sizeof(R) == 8) kf = (R)exp64(M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT);
-        else kf = (R)expf(M.lnAf[j] + M.bf[j] * (float)lnTb - M.Thetaf[j] * (float)invTb);
+        if (sizeof(R) == 8) {
+            const double a = M.lnA[j] + M.b[j] * lnT - M.Theta[j] * invT;
+            kf = (R)exp64(a);
+            if (anyp && M.ptype[j]) kf *= pressure_factor<R, NS>(M, j, (R)a, (R)T, (R)lnT, (R)invT, sCb, stride);
+        } else {
+            const float a = M.lnAf[j] + M.bf[j] * (float)lnTb - M.Thetaf[j] * (float)invTb;
+            kf = (R)expf(a);
+            if (anyp && M.ptype[j]) kf *= pressure_factor<R, NS>(M, j, (R)a, narrow<R>(T), lnTb, invTb, sCb, stride);
+        }
         const int nrc = M.n_reac[j], npd = M.n_prod[j];
         R cf = kf;
         for (int k = 0; k < nrc; ++k) cf *= sCb[M.reac[j][k] * stride];
@@ -222,13 +296,59 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
 // ----------------------------------------------------------------------------- cell state
 
 // Dynamic shared memory of one cell-state block of B threads: per species and thread
-// C G and 1/G (FP64), the rate accumulator and C (bulk type); with rates (the time-step
-// evaluation) also the rate-Jacobian diagonal (bulk type) and, FP64 path, G (FP64),
-// placed last so that launches without rates need less.
+// C G and 1/G (FP64) and C (bulk type); then the rate accumulator, per species in the
+// bulk type, except in the mixed path's launches without time-step rates, which keep
+// the rates of progress q_j per reaction there (max(NS, nr) columns); with rates (the
+// time-step evaluation) also the rate-Jacobian diagonal (bulk type) and, FP64 path, G
+// (FP64), placed last so that launches without rates need less.
 template <typename R, int NS>
-__host__ __device__ constexpr size_t cell_state_smem(int B, bool rates = true) {
-    return (size_t)B * NS *
-           (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(R) + (sizeof(R) == 8 ? sizeof(double) : 0) : 0));
+__host__ __device__ constexpr size_t cell_state_smem(int B, bool rates, int nr) {
+    return (sizeof(R) == 4 && !rates)
+               ? (size_t)B * (NS * (2 * sizeof(double) + sizeof(R)) + (size_t)(nr > NS ? nr : NS) * sizeof(R))
+               : (size_t)B * NS *
+                     (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(R) + (sizeof(R) == 8 ? sizeof(double) : 0) : 0));
+}
+template <typename R, int NS>
+__host__ __device__ constexpr size_t cell_state_smem_max(int B, int nr) {
+    return cell_state_smem<R, NS>(B, true, nr) > cell_state_smem<R, NS>(B, false, nr) ? cell_state_smem<R, NS>(B, true, nr)
+                                                                                     : cell_state_smem<R, NS>(B, false, nr);
+}
+
+// Rate of progress of a reversible elementary reaction j with NRC reactant and NPD
+// product molecules (mixed path): k_f in FP32, the forward term k_f prod C in FP32,
+// the reverse factors prod_prod (C G) prod_reac (1/G) in FP64 (as a two-level product)
+// and q = k_f (prod C - reverse factors) joined by one FP64 FMA.
+template <int NRC, int NPD>
+__device__ __forceinline__ float q_elementary(const MechDev &M, int j, float lnT, float invT, const float *__restrict__ sCb,
+                                              const double *__restrict__ sP, const double *__restrict__ sRr, int stride) {
+    const float kf = expf(M.lnAf[j] + M.bf[j] * lnT - M.Thetaf[j] * invT);
+    const int r0 = M.reac[j][0] * stride, p0 = M.prod[j][0] * stride;
+    float cf = kf * sCb[r0];
+    double pp = sP[p0], rr = sRr[r0];
+    if (NRC == 2) {
+        const int r1 = M.reac[j][1] * stride;
+        cf *= sCb[r1];
+        rr *= sRr[r1];
+    }
+    if (NPD == 2) pp *= sP[M.prod[j][1] * stride];
+    return d2f(fma(-f2d(kf), pp * rr, f2d(cf)));
+}
+
+// The rates of progress of one shape class, two reactions per iteration so that their
+// independent FP64 products overlap (an odd last reaction is computed twice).
+template <int NRC, int NPD>
+__device__ __forceinline__ void q_class(const MechDev &M, int c, float lnT, float invT, const float *__restrict__ sCb,
+                                        const double *__restrict__ sP, const double *__restrict__ sRr, float *__restrict__ sQ,
+                                        int stride) {
+    const int i0 = M.cls_start[c], i1 = M.cls_start[c + 1];
+#pragma unroll 1
+    for (int i = i0; i < i1; i += 2) {
+        const int ja = M.cls_rx[i], jb = M.cls_rx[i + 1 < i1 ? i + 1 : i];
+        const float qa = q_elementary<NRC, NPD>(M, ja, lnT, invT, sCb, sP, sRr, stride);
+        const float qb = q_elementary<NRC, NPD>(M, jb, lnT, invT, sCb, sP, sRr, stride);
+        sQ[ja * stride] = qa;
+        sQ[jb * stride] = qb;
+    }
 }
 
 template <typename R, int NS>
@@ -236,12 +356,13 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                                                  int newton_maxit) {
     constexpr int NV = NS + 4;
     const int B = blockDim.x;
-    // sP, sRr (FP64), sW, sCb (bulk type) | rates only: sD (bulk type), FP64 path sG (FP64)
+    // sP, sRr (FP64), sCb, sW (bulk type; in the mixed path without rates sW holds q_j) |
+    // rates only: sD (bulk type), FP64 path sG (FP64)
     double *sP = (double *)smem_raw;
     double *sRr = sP + NS * B;
-    R *sW = (R *)(sRr + NS * B);
-    R *sCb = sW + NS * B;
-    R *sD = sCb + NS * B;
+    R *sCb = (R *)(sRr + NS * B);
+    R *sW = sCb + NS * B;
+    R *sD = sW + NS * B;
     double *sG = (double *)(sD + NS * B);
     __shared__ double s_laser[5];
     __shared__ R s_red[3][32];
@@ -371,8 +492,28 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         for (int s = 0; s < NS; ++s) Q[(QL<NS>::DC + s) * n + cell] = Dc[s];
 
         R *rhs = (R *)m.rhs;
-        if (chem_on) {
-            r_ch = chemistry<R, NS>(M, lnT, invT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
+        if (chem_on && sizeof(R) == 4 && !m.want_rates) {
+            // mixed path without time-step rates: the rates of progress by shape class
+            // (straight-line code, two reactions at a time), the others one by one, then
+            // omega_s = W_s sum_j nu_sj q_j from the species-major lists, in registers
+            const float *cb = (const float *)sCb + tid;
+            float *sQ = (float *)sW + tid;
+            const float lnTf = d2f(lnT), invTf = d2f(invT);
+            q_class<1, 1>(M, 0, lnTf, invTf, cb, sP + tid, sRr + tid, sQ, B);
+            q_class<1, 2>(M, 1, lnTf, invTf, cb, sP + tid, sRr + tid, sQ, B);
+            q_class<2, 1>(M, 2, lnTf, invTf, cb, sP + tid, sRr + tid, sQ, B);
+            q_class<2, 2>(M, 3, lnTf, invTf, cb, sP + tid, sRr + tid, sQ, B);
+            if (M.cls_start[5] > M.cls_start[4])
+                chemistry_q_generic<NS>(M, T, lnT, invT, cb, sP + tid, sRr + tid, sQ, B);
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                float w = 0.f;
+#pragma unroll 1
+                for (int e = M.sp_start[s]; e < M.sp_start[s + 1]; ++e) w = fmaf((float)M.sp_nu[e], sQ[M.sp_rx[e] * B], w);
+                rhs[s * n + cell] = (R)(w * M.Wf[s]);
+            }
+        } else if (chem_on) {
+            r_ch = chemistry<R, NS>(M, T, lnT, invT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
                                     m.want_rates != 0);
 #pragma unroll
             for (int s = 0; s < NS; ++s) rhs[s * n + cell] = sW[s * B + tid] * mech_W<R>(M, s);
@@ -1710,7 +1851,7 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
         if (M.nr > 0) {
             chemistry_inputs<double, NS>(M, rng, rs, T, invT, lnT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid,
                                          sD + tid, B, false);
-            chemistry<double, NS>(M, lnT, invT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B, false);
+            chemistry<double, NS>(M, T, lnT, invT, sC + tid, sC + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B, false);
 #pragma unroll
             for (int s = 0; s < NS; ++s) hrr -= hs[s] * sW[s * B + tid] * M.W[s];
         }

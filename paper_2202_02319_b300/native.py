@@ -32,7 +32,8 @@ _ip = ctypes.POINTER(ctypes.c_int)
 class MechDesc(ctypes.Structure):
     _fields_ = [("n_species", ctypes.c_int), ("n_reactions", ctypes.c_int), ("W", _dp), ("nasa_low", _dp),
                 ("nasa_high", _dp), ("T_mid", _dp), ("mu_ref", _dp), ("mu_exp", _dp), ("D_ref", _dp),
-                ("A", _dp), ("b", _dp), ("Theta", _dp), ("nu_f", _ip), ("nu_r", _ip), ("reversible", _ip)]
+                ("A", _dp), ("b", _dp), ("Theta", _dp), ("nu_f", _ip), ("nu_r", _ip), ("reversible", _ip),
+                ("rxn_type", _ip), ("efficiency", _dp), ("A0", _dp), ("b0", _dp), ("Theta0", _dp), ("troe", _dp)]
 
 
 class GridDesc(ctypes.Structure):
@@ -139,6 +140,12 @@ class Mechanism:
                         d(m.D_ref), d(m.A if nr else np.zeros(1)), d(m.b if nr else np.zeros(1)),
                         d(m.Theta if nr else np.zeros(1)), i(m.nu_f if nr else np.zeros(1)),
                         i(m.nu_r if nr else np.zeros(1)), i(m.reversible if nr else np.zeros(1)))
+        rt = getattr(m, "rxn_type", None)
+        if rt is not None and nr and np.any(np.asarray(rt) != 0):
+            desc.rxn_type = i(rt)
+            desc.efficiency = d(m.efficiency)
+            desc.A0, desc.b0, desc.Theta0 = d(m.A0), d(m.b0), d(m.Theta0)
+            desc.troe = d(m.troe)
         h = _vp()
         _check(_lib.rf_init_mechanism(ctypes.byref(desc), ctypes.byref(h)), "rf_init_mechanism")
         self.handle = h

@@ -64,6 +64,16 @@ class Mechanism:
     nu_f: np.ndarray
     nu_r: np.ndarray
     reversible: np.ndarray
+    # pressure-dependent reactions (None: every reaction elementary).  rxn_type [Nr]:
+    # 0 elementary, 1 third body (rate times [M] = sum_s efficiency_s C_s), 2 Lindemann
+    # and 3 Troe fall-off (A, b, Theta the high-pressure limit, A0, b0, Theta0 the
+    # low-pressure one in (m^3/mol)^order / s, troe [Nr, 4] = alpha, T***, T*, T**)
+    rxn_type: Optional[np.ndarray] = None
+    efficiency: Optional[np.ndarray] = None
+    A0: Optional[np.ndarray] = None
+    b0: Optional[np.ndarray] = None
+    Theta0: Optional[np.ndarray] = None
+    troe: Optional[np.ndarray] = None
 
     @property
     def n_species(self) -> int:
@@ -257,6 +267,34 @@ def mechanism_9sp(seed: int = 0, n_reactions: int = 19) -> Mechanism:
     A, b, Theta = _arrhenius(stream(seed, "mech9/arrhenius"), nu_f, nu_r, hf_all)
     return Mechanism(names, W, elem, nasa.copy(), nasa.copy(), np.full(9, 1000.0),
                      mu_ref, mu_exp, D, A, b, Theta, nu_f, nu_r, np.ones(nr, dtype=np.int32))
+
+
+def mechanism_9sp_pressure(seed: int = 0, n_reactions: int = 19) -> Mechanism:
+    """mechanism_9sp with pressure-dependent reactions: of the reactions that join
+    two molecules into one (or split one into two), the first becomes a third-body
+    reaction, the second a Lindemann fall-off and the third a Troe fall-off.
+    Efficiencies U[0.5, 3] (the inert Z2 at 1); low-pressure limits with
+    P_r = k0 [M] / k_inf of order one at 1 atm and 1000 K."""
+    m = mechanism_9sp(seed, n_reactions)
+    nr, ns = m.n_reactions, m.n_species
+    g = stream(seed, "mech9/pressure")
+    rt = np.zeros(nr, dtype=np.int32)
+    eff = np.ones((nr, ns))
+    A0, b0, Th0 = m.A.copy(), m.b.copy(), m.Theta.copy()
+    troe = np.zeros((nr, 4))
+    cand = [j for j in range(nr) if sorted((int(m.nu_f[j].sum()), int(m.nu_r[j].sum()))) == [1, 2]]
+    for kind, j in zip((1, 2, 3), cand):
+        rt[j] = kind
+        eff[j] = g.uniform(0.5, 3.0, ns)
+        eff[j, m.index("Z2")] = 1.0
+        if kind >= 2:
+            A0[j] = m.A[j] * g.uniform(0.01, 1.0)
+            b0[j] = m.b[j] - g.uniform(0.5, 1.5)
+            Th0[j] = m.Theta[j] * g.uniform(0.5, 0.9)
+        if kind == 3:
+            troe[j] = [g.uniform(0.3, 0.8), g.uniform(100.0, 300.0), g.uniform(1000.0, 3000.0), g.uniform(3000.0, 6000.0)]
+    m.rxn_type, m.efficiency, m.A0, m.b0, m.Theta0, m.troe = rt, eff, A0, b0, Th0, troe
+    return m
 
 
 # --------------------------------------------------------------------------- cases

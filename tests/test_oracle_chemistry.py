@@ -22,7 +22,7 @@ def _random_state(m, n, seed):
     return tensor(rho_s), tensor(T)
 
 
-@pytest.mark.parametrize("mk", [synth.mechanism_4sp, synth.mechanism_9sp])
+@pytest.mark.parametrize("mk", [synth.mechanism_4sp, synth.mechanism_9sp, synth.mechanism_9sp_pressure])
 def test_mass_and_element_conservation(mk):
     m = mk(0)
     mt = mech_t(m)
@@ -96,12 +96,13 @@ def test_chemical_rate_is_jacobian_diagonal(mk):
     np.testing.assert_allclose(est.numpy(), fd.numpy(), rtol=1e-5)
 
 
-def test_homogeneous_reactor_against_stiff_integration():
+@pytest.mark.parametrize("mk", [synth.mechanism_9sp, synth.mechanism_9sp_pressure])
+def test_homogeneous_reactor_against_stiff_integration(mk):
     """A uniform 4^3 periodic box evolves as a constant-volume reactor: the RK3
     trajectory at a chemically resolved dt matches a Radau integration of
     d rho_s/dt = omega_s(rho, e) to 1e-6, total energy is constant and the box stays
-    uniform."""
-    m = synth.mechanism_9sp(0)
+    uniform (elementary reactions, and with third-body and fall-off reactions)."""
+    m = mk(0)
     mt = mech_t(m)
     n = 4
     grid = GridT(n, n, n, 1e-4, 1e-4, 1e-4)
