@@ -294,23 +294,27 @@ __device__ __forceinline__ void exp_pair(double x, double &ep, double &em) {
 
 // The mixed path's exponential pair.  Its Gibbs factors feed a reverse term that is
 // subtracted from an FP32 forward term, so a relative error of 2e-13 loses nothing
-// there: the same reduction without the low part of ln2/256 (which moves r by at most
-// |x| 3.4e-17) and E = 1 + r^2/2 (the dropped r^4/24 is below 1.4e-13); still FP64.
+// there.  The same reduction without the low part of ln2/256 (which moves r by at most
+// |x| 3.4e-17), and exp(+-r) = 1 +- r + p(+-r) with the small part
+// p(r) = r^2 (1/2 + r (1/6 + r/24)) <= 9.2e-7 formed in FP32 from r rounded to FP32
+// (relative error about 1.2e-7, so at most 1.1e-13 absolute; the first omitted term
+// r^5/120 < 4e-17): the FP64 work is the reduction and two FMAs per exponential,
+// s (1 + p) then + s r, with the scale s the table entry.
 __device__ __forceinline__ void exp_pair_mixed(double x, double &ep, double &em) {
     const double shifter = 6755399441055744.0;
     const double t = fma(x, 369.3299304675746 /* 256 / ln 2 */, shifter);
     const int k = __double2loint(t);
     const double kd = f2d((float)k);                          // = t - shifter, exactly (|k| < 2^24)
     const double r = fma(-kd, LN2_256_HI, x);
-    const double r2 = r * r;
-    const double E = fma(r2, 0.5, 1.0);
-    const double O = fma(r * r2, 1.0 / 6.0, r);
+    const float rf = d2f(r), r2f = rf * rf;
+    const float pp = r2f * fmaf(rf, fmaf(rf, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
+    const float pm = r2f * fmaf(-rf, fmaf(-rf, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
     const int j = k & 255, m = min(max(k >> 8, -1020), 1020);
     const double tp = __ldg(&g_exp_tab[j]), tm = __ldg(&g_exp_tab[256 + j]);
     const double sp = __hiloint2double(__double2hiint(tp) + (m << 20), __double2loint(tp));
     const double sm = __hiloint2double(__double2hiint(tm) - (m << 20), __double2loint(tm));
-    ep = sp * (E + O);
-    em = sm * (E - O);
+    ep = fma(sp, r, fma(sp, f2d(pp), sp));
+    em = fma(-sm, r, fma(sm, f2d(pm), sm));
 }
 
 // exp(x) alone from the same reduction and table: exp(r) by its Taylor polynomial

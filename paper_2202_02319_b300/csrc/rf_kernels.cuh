@@ -138,6 +138,87 @@ __device__ __noinline__ void chemistry_q_generic(const MechDev &M, double T, dou
     }
 }
 
+// Mixed path, stage with time-step rates: the diagonal of the chemistry Jacobian
+// d omega_s / d C_s into sD (cleared here) and its largest magnitude, after the rates
+// of progress are done: per reactant position the forward term without that factor
+// (FP32); per product position the reverse term k_f G_s prod_(other products) (C G)
+// prod_reac (1/G), whose factors span more than the FP32 range but only feed an FP32
+// time-step estimate, as FP32 mantissas in [1, 2) with integer binary exponents (~5e-7
+// relative), G from 1/G.  Pressure-dependent reactions differentiate at fixed factor.
+template <int NS>
+__device__ __noinline__ float chemistry_rates_mixed(const MechDev &M, double T, double lnT, double invT,
+                                                    const float *__restrict__ sCb, const double *__restrict__ sP,
+                                                    const double *__restrict__ sRr, float *__restrict__ sD, int stride) {
+#pragma unroll
+    for (int s = 0; s < NS; ++s) sD[s * stride] = 0.f;
+    const float lnTf = d2f(lnT), invTf = d2f(invT);
+    const bool anyp = M.npress != 0;
+    for (int j = 0; j < M.nr; ++j) {
+        const float a = M.lnAf[j] + M.bf[j] * lnTf - M.Thetaf[j] * invTf;
+        float kf = expf(a);
+        if (anyp && M.ptype[j]) kf *= pressure_factor<float, NS>(M, j, a, d2f(T), lnTf, invTf, sCb, stride);
+        const int nrc = M.n_reac[j], npd = M.n_prod[j];
+        if (nrc == 1) {
+            const int s0 = M.reac[j][0];
+            sD[s0 * stride] = fmaf((float)M.dnu_reac[j][0], kf, sD[s0 * stride]);
+        } else if (nrc == 2) {
+            const int s0 = M.reac[j][0], s1 = M.reac[j][1];
+            const float c0 = sCb[s0 * stride], c1 = sCb[s1 * stride];
+            sD[s0 * stride] = fmaf((float)M.dnu_reac[j][0], kf * c1, sD[s0 * stride]);
+            sD[s1 * stride] = fmaf((float)M.dnu_reac[j][1], kf * c0, sD[s1 * stride]);
+        } else if (nrc == 3) {
+            const int s0 = M.reac[j][0], s1 = M.reac[j][1], s2 = M.reac[j][2];
+            const float c0 = sCb[s0 * stride], c1 = sCb[s1 * stride], c2 = sCb[s2 * stride];
+            sD[s0 * stride] = fmaf((float)M.dnu_reac[j][0], kf * c1 * c2, sD[s0 * stride]);
+            sD[s1 * stride] = fmaf((float)M.dnu_reac[j][1], kf * c0 * c2, sD[s1 * stride]);
+            sD[s2 * stride] = fmaf((float)M.dnu_reac[j][2], kf * c0 * c1, sD[s2 * stride]);
+        }
+        if (!M.rev[j]) continue;
+        const SplitF f0 = split32(kf);
+        float krm = f0.m;
+        int kre = f0.e;
+#pragma unroll 1
+        for (int k2 = 0; k2 < nrc; ++k2) {
+            const SplitF f = split64(sRr[M.reac[j][k2] * stride]);
+            krm *= f.m;
+            kre += f.e;
+        }
+        if (npd == 1) {
+            const int s0 = M.prod[j][0];
+            const SplitF ig0 = split64(sRr[s0 * stride]);
+            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0], unsplit(krm * __frcp_rn(ig0.m), kre - ig0.e), sD[s0 * stride]);
+        } else if (npd == 2) {
+            const int s0 = M.prod[j][0], s1 = M.prod[j][1];
+            const SplitF ig0 = split64(sRr[s0 * stride]), ig1 = split64(sRr[s1 * stride]);
+            const SplitF p0 = split64(sP[s0 * stride]), p1 = split64(sP[s1 * stride]);
+            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0], unsplit(krm * __frcp_rn(ig0.m) * p1.m, kre - ig0.e + p1.e),
+                                   sD[s0 * stride]);
+            sD[s1 * stride] = fmaf(-(float)M.dnu_prod[j][1], unsplit(krm * __frcp_rn(ig1.m) * p0.m, kre - ig1.e + p0.e),
+                                   sD[s1 * stride]);
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < npd; ++k) {
+                const int s = M.prod[j][k];
+                const SplitF ig = split64(sRr[s * stride]);
+                float pm = krm * __frcp_rn(ig.m);
+                int pe = kre - ig.e;
+#pragma unroll 1
+                for (int k2 = 0; k2 < npd; ++k2)
+                    if (k2 != k) {
+                        const SplitF f = split64(sP[M.prod[j][k2] * stride]);
+                        pm *= f.m;
+                        pe += f.e;
+                    }
+                sD[s * stride] = fmaf(-(float)M.dnu_prod[j][k], unsplit(pm, pe), sD[s * stride]);
+            }
+        }
+    }
+    float best = 0.f;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) best = fmaxf(best, fabsf(sD[s * stride]));
+    return best;
+}
+
 template <typename R, int NS>
 __device__ __forceinline__ R chemistry(const MechDev &M, double T, double lnT, double invT, const double *__restrict__ sG,
                                        const R *__restrict__ sCb, const double *__restrict__ sP,
@@ -296,14 +377,14 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
 // ----------------------------------------------------------------------------- cell state
 
 // Dynamic shared memory of one cell-state block of B threads: per species and thread
-// C G and 1/G (FP64) and C (bulk type); then the rate accumulator, per species in the
-// bulk type, except in the mixed path's launches without time-step rates, which keep
-// the rates of progress q_j per reaction there (max(NS, nr) columns); with rates (the
-// time-step evaluation) also the rate-Jacobian diagonal (bulk type) and, FP64 path, G
-// (FP64), placed last so that launches without rates need less.
+// C G and 1/G (FP64) and C (bulk type); then, mixed path, the rates of progress q_j per
+// reaction (max(NS, nr) columns), which the rate-Jacobian diagonal of the time-step
+// evaluation reuses once omega is formed; FP64 path, the per-species rate accumulator
+// and, with rates, the Jacobian diagonal and G (FP64), placed last so that launches
+// without rates need less.
 template <typename R, int NS>
 __host__ __device__ constexpr size_t cell_state_smem(int B, bool rates, int nr) {
-    return (sizeof(R) == 4 && !rates)
+    return sizeof(R) == 4
                ? (size_t)B * (NS * (2 * sizeof(double) + sizeof(R)) + (size_t)(nr > NS ? nr : NS) * sizeof(R))
                : (size_t)B * NS *
                      (2 * sizeof(double) + 2 * sizeof(R) + (rates ? sizeof(R) + (sizeof(R) == 8 ? sizeof(double) : 0) : 0));
@@ -480,8 +561,9 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         // scheduler can interleave the two pipes' work
         R mu, lam, Dc[NS], Dmax;
         if (chem_on) {
+            // (the mixed path clears its Jacobian diagonal itself, in the q columns)
             chemistry_inputs<R, NS>(M, rng, rs, T, invT, lnT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid,
-                                    sD + tid, B, m.want_rates != 0);
+                                    sD + tid, B, m.want_rates != 0 && sizeof(R) == 8);
             transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
         } else {
             transport<R, NS>(M, rng, Tb, pb, narrow<R>(rho), Wbarb, X, mu, lam, Dc, Dmax);
@@ -492,10 +574,11 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
         for (int s = 0; s < NS; ++s) Q[(QL<NS>::DC + s) * n + cell] = Dc[s];
 
         R *rhs = (R *)m.rhs;
-        if (chem_on && sizeof(R) == 4 && !m.want_rates) {
-            // mixed path without time-step rates: the rates of progress by shape class
-            // (straight-line code, two reactions at a time), the others one by one, then
-            // omega_s = W_s sum_j nu_sj q_j from the species-major lists, in registers
+        if (chem_on && sizeof(R) == 4) {
+            // mixed path: the rates of progress by shape class (straight-line code, two
+            // reactions at a time), the others one by one, then omega_s = W_s sum_j nu_sj
+            // q_j from the species-major lists, in registers; with time-step rates, the
+            // Jacobian diagonal afterwards in the q columns
             const float *cb = (const float *)sCb + tid;
             float *sQ = (float *)sW + tid;
             const float lnTf = d2f(lnT), invTf = d2f(invT);
@@ -512,6 +595,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                 for (int e = M.sp_start[s]; e < M.sp_start[s + 1]; ++e) w = fmaf((float)M.sp_nu[e], sQ[M.sp_rx[e] * B], w);
                 rhs[s * n + cell] = (R)(w * M.Wf[s]);
             }
+            if (m.want_rates) r_ch = (R)chemistry_rates_mixed<NS>(M, T, lnT, invT, cb, sP + tid, sRr + tid, sQ, B);
         } else if (chem_on) {
             r_ch = chemistry<R, NS>(M, T, lnT, invT, sG + tid, sCb + tid, sP + tid, sRr + tid, sW + tid, sD + tid, B,
                                     m.want_rates != 0);
