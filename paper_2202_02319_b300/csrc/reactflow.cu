@@ -237,6 +237,7 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             M.gc[r][s][4] = -a[4] / 20.0;
             M.gc[r][s][5] = a[5];
             M.gc[r][s][6] = 1.0 - a[0];
+            M.gc0w[r][s] = M.gc[r][s][0] - std::log(d->W[s]);
             for (int k = 0; k < 5; ++k) M.cpcf[r][s][k] = (float)a[k];
             for (int k = 0; k < 6; ++k) M.ecf[r][s][k] = (float)M.ec[r][s][k];
         }
@@ -301,6 +302,11 @@ extern "C" int rf_init_mechanism(const rf_mech_desc *d, rf_mech **out) {
             }
         }
         M.n_reac[j] = (int8_t)nrc;
+        {
+            double kap = 1.0;
+            for (int k = 0; k < nrc; ++k) kap /= d->W[M.reac[j][k]];
+            M.kapf[j] = (float)kap;
+        }
         M.n_prod[j] = (int8_t)npd;
         M.n_net[j] = (int8_t)nnet;
         M.dnu_sum[j] = (int8_t)dsum;

@@ -32,6 +32,7 @@ struct MechDev {
     double ec[2][NSMAX][6];                    // a1, a2/2, a3/3, a4/4, a5/5, a6 (h/RT Horner + a6/T)
     double ecR[2][NSMAX][6];                   // e_s / T-powers: (a1 - 1) R/W_s, then ec times R/W_s (Newton solve)
     double gc[2][NSMAX][7];                    // ln G = g/RT + ln(RT/p_atm) = gc0 + T(gc1 + ... T gc4) + gc5/T + gc6 lnT
+    double gc0w[2][NSMAX];                     // gc0 - ln W_s: ln (G_s / W_s), the mixed path's Gibbs factor
     float ecf[2][NSMAX][6];                    // FP32 copy of ec
     double mu_ref[NSMAX], mu_exp[NSMAX], eucken[NSMAX];     // eucken = 1.25 R / W_s
     double hl_mu_ref[NSMAX], h_mu_exp[NSMAX];  // ln(mu_ref) / 2, mu_exp / 2: sqrt(mu_s) by one exponential
@@ -67,6 +68,7 @@ struct MechDev {
     // takes nu = sp_nu[e] times q of reaction sp_rx[e] for e in [sp_start[s], sp_start[s + 1])
     int16_t sp_start[NSMAX + 1];
     int8_t sp_rx[NRMAX * 6], sp_nu[NRMAX * 6];
+    float kapf[NRMAX];                         // prod over reactant molecules of 1 / W_s (mixed path)
     double eff[NPMAX][NSMAX], lnA0[NPMAX], b0[NPMAX], Theta0[NPMAX], troe[NPMAX][4];
     float efff[NPMAX][NSMAX], lnA0f[NPMAX], b0f[NPMAX], Theta0f[NPMAX], troef[NPMAX][4];
 };
@@ -491,6 +493,11 @@ __device__ __forceinline__ double h_RT(const MechDev &M, int r, int s, double T,
 __device__ __forceinline__ double lnG(const MechDev &M, int r, int s, double T, double invT, double lnT) {
     const double *c = M.gc[r][s];
     return fma(c[6], lnT, fma(c[5], invT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), c[0])));
+}
+// ln (G_s / W_s), the same Horner pass with the constant term less ln W_s.
+__device__ __forceinline__ double lnG_w(const MechDev &M, int r, int s, double T, double invT, double lnT) {
+    const double *c = M.gc[r][s];
+    return fma(c[6], lnT, fma(c[5], invT, fma(T, fma(T, fma(T, fma(T, c[4], c[3]), c[2]), c[1]), M.gc0w[r][s])));
 }
 
 // h_s/RT in the bulk type.

@@ -132,7 +132,7 @@ __device__ __noinline__ void chemistry_q_generic(const MechDev &M, double T, dou
                 const int e = M.revf[j][k];
                 pr *= e < 16 ? sP[e * stride] : sRr[(e - 16) * stride];
             }
-            q = d2f(fma(-f2d(kf), pr, f2d(cf)));
+            q = d2f(fma(-f2d(kf * M.kapf[j]), pr, f2d(cf)));
         }
         sQ[j * stride] = q;
     }
@@ -174,7 +174,9 @@ __device__ __noinline__ float chemistry_rates_mixed(const MechDev &M, double T, 
             sD[s2 * stride] = fmaf((float)M.dnu_reac[j][2], kf * c0 * c1, sD[s2 * stride]);
         }
         if (!M.rev[j]) continue;
-        const SplitF f0 = split32(kf);
+        // the reactant factors are W_s / G_s: k_f prod_reac (1 / W_s) restores 1 / G_s,
+        // and a product position's G_s is W_s / (W_s / G_s)
+        const SplitF f0 = split32(kf * M.kapf[j]);
         float krm = f0.m;
         int kre = f0.e;
 #pragma unroll 1
@@ -186,15 +188,16 @@ __device__ __noinline__ float chemistry_rates_mixed(const MechDev &M, double T, 
         if (npd == 1) {
             const int s0 = M.prod[j][0];
             const SplitF ig0 = split64(sRr[s0 * stride]);
-            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0], unsplit(krm * __frcp_rn(ig0.m), kre - ig0.e), sD[s0 * stride]);
+            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0] * M.Wf[s0], unsplit(krm * __frcp_rn(ig0.m), kre - ig0.e),
+                                   sD[s0 * stride]);
         } else if (npd == 2) {
             const int s0 = M.prod[j][0], s1 = M.prod[j][1];
             const SplitF ig0 = split64(sRr[s0 * stride]), ig1 = split64(sRr[s1 * stride]);
             const SplitF p0 = split64(sP[s0 * stride]), p1 = split64(sP[s1 * stride]);
-            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0], unsplit(krm * __frcp_rn(ig0.m) * p1.m, kre - ig0.e + p1.e),
-                                   sD[s0 * stride]);
-            sD[s1 * stride] = fmaf(-(float)M.dnu_prod[j][1], unsplit(krm * __frcp_rn(ig1.m) * p0.m, kre - ig1.e + p0.e),
-                                   sD[s1 * stride]);
+            sD[s0 * stride] = fmaf(-(float)M.dnu_prod[j][0] * M.Wf[s0],
+                                   unsplit(krm * __frcp_rn(ig0.m) * p1.m, kre - ig0.e + p1.e), sD[s0 * stride]);
+            sD[s1 * stride] = fmaf(-(float)M.dnu_prod[j][1] * M.Wf[s1],
+                                   unsplit(krm * __frcp_rn(ig1.m) * p0.m, kre - ig1.e + p0.e), sD[s1 * stride]);
         } else {
 #pragma unroll 1
             for (int k = 0; k < npd; ++k) {
@@ -209,7 +212,7 @@ __device__ __noinline__ float chemistry_rates_mixed(const MechDev &M, double T, 
                         pm *= f.m;
                         pe += f.e;
                     }
-                sD[s * stride] = fmaf(-(float)M.dnu_prod[j][k], unsplit(pm, pe), sD[s * stride]);
+                sD[s * stride] = fmaf(-(float)M.dnu_prod[j][k] * M.Wf[s], unsplit(pm, pe), sD[s * stride]);
             }
         }
     }
@@ -359,12 +362,20 @@ __device__ __forceinline__ void chemistry_inputs(const MechDev &M, int rng, cons
                                                  int stride, bool rates) {
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        const double C = rs[s] * M.invW[s];
         double G, iG;
-        if (sizeof(R) == 4) exp_pair_mixed(lnG(M, rng, s, T, invT, lnT), G, iG);
-        else exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
-        sCb[s * stride] = narrow<R>(C);
-        sP[s * stride] = C * G;
+        if (sizeof(R) == 4) {
+            // mixed path: G' = G_s / W_s from the folded constant, so C_s G_s = rho_s G'
+            // takes one FP64 product and the reactant factors are W_s / G_s (the
+            // reverse term carries prod_reac 1 / W_s in FP32 with k_f); C_s in FP32
+            exp_pair_mixed(lnG_w(M, rng, s, T, invT, lnT), G, iG);
+            sCb[s * stride] = (R)(d2f(rs[s]) * M.invWf[s]);
+            sP[s * stride] = rs[s] * G;
+        } else {
+            const double C = rs[s] * M.invW[s];
+            exp_pair(lnG(M, rng, s, T, invT, lnT), G, iG);
+            sCb[s * stride] = narrow<R>(C);
+            sP[s * stride] = C * G;
+        }
         sRr[s * stride] = iG;
         sW[s * stride] = (R)0;
         if (rates) {
@@ -412,7 +423,7 @@ __device__ __forceinline__ float q_elementary(const MechDev &M, int j, float lnT
         rr *= sRr[r1];
     }
     if (NPD == 2) pp *= sP[M.prod[j][1] * stride];
-    return d2f(fma(-f2d(kf), pp * rr, f2d(cf)));
+    return d2f(fma(-f2d(kf * M.kapf[j]), pp * rr, f2d(cf)));
 }
 
 // The rates of progress of one shape class, two reactions per iteration so that their
