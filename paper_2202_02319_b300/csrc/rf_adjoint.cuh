@@ -17,6 +17,14 @@
 
 namespace rf {
 
+// 1/x in FP64: the Newton-Raphson rcp64 where x lies in the FP32 normal range (its
+// seed's domain), a division elsewhere.
+__device__ __forceinline__ double rcp_any(double x) {
+    const double ax = fabs(x);
+    return (ax > 1.0e-37 && ax < 1.0e37) ? rcp64(x) : 1.0 / x;
+}
+
+
 // ----------------------------------------------------------------------------- per-cell map
 
 // Reverse (vector-Jacobian product) of the FP64 cell-state map U -> (Q, omega,
@@ -86,7 +94,7 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
     for (int s = 0; s < NS; ++s) {
         mus[s] = exp(lnTs * M.mu_exp[s]) * M.mu_ref[s];
         sq[s] = sqrt(mus[s]);
-        isq[s] = 1.0 / sq[s];
+        isq[s] = rcp_any(sq[s]);
     }
 #pragma unroll
     for (int i = 0; i < NS; ++i) {
@@ -96,8 +104,8 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
             const double a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
             d += X[j] * (a * a) * M.wd[i][j];
         }
-        den[i] = d;
-        xr[i] = X[i] / d;
+        den[i] = rcp_any(d);                    // 1 / sum_j X_j Phi_ij
+        xr[i] = X[i] * den[i];
     }
     // ---------------------------------------------------------------- reverse
     double Yb[NS], Xb[NS], hsb[NS], cpsb[NS];
@@ -123,7 +131,7 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
             G[s] = exp((((T * g[4] + g[3]) * T + g[2]) * T + g[1]) * T + g[0] + invT * g[5] + lnT * g[6]);
             C[s] = U[s] * M.invW[s];
             sP[s] = C[s] * G[s];
-            sR[s] = 1.0 / G[s];
+            sR[s] = rcp_any(G[s]);
             sCb[s] = sPb[s] = sRb[s] = 0.0;
             wd[s] = 0.0;
         }
@@ -226,9 +234,9 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
             const double QDb = QB(QL<NS>::DC + s2);
             rhoWb += QDb * Dm * M.W[s2];
             const double t = QDb * rhoW * M.W[s2] * Dm;          // Dm_bar * Dm
-            const double numb = t / num, ddb = -t / dd;
-            fTb += t / fT;
-            Wbeb -= t / Wbe;
+            const double numb = t * rcp_any(num), ddb = -t * rcp_any(dd);
+            fTb += t * rcp_any(fT);
+            Wbeb -= t * rcp_any(Wbe);
 #pragma unroll
             for (int j = 0; j < NS; ++j) {
                 if (j == s2) continue;
@@ -252,8 +260,8 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
         const double xrb = mub * mus[i] + lamb * mus[i] * fac;
         musb[i] = mub * xr[i] + lamb * xr[i] * fac;
         cpsb[i] += lamb * xr[i] * mus[i];
-        Xb[i] += xrb / den[i];
-        const double denb = -xrb * xr[i] / den[i];
+        Xb[i] += xrb * den[i];
+        const double denb = -xrb * xr[i] * den[i];
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
             const double a = sq[i] * isq[j] * M.wc[i][j] + 1.0;
@@ -266,7 +274,7 @@ __device__ void cell_map_reverse(const MechDev &M, const double (&U)[NS + 4], do
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         sqb[s] -= isqb[s] * isq[s] * isq[s];
-        musb[s] += sqb[s] * 0.5 / sq[s];
+        musb[s] += sqb[s] * 0.5 * isq[s];
         lnTsb += musb[s] * mus[s] * M.mu_exp[s];
     }
     Tb += lnTsb / T;
@@ -449,14 +457,18 @@ __device__ __forceinline__ void weno3z_adj(double a, double b, double c, double 
     const double tau = fabs(b1 - b0);
     const double eps = fma(e2, fma(a, a, fma(b, b, c * c)), EPS_WENO);
     const double e0 = b0 + eps, e1 = b1 + eps;
-    const double al0 = (1.0 / 3.0) * (1.0 + tau / e0), al1 = (2.0 / 3.0) * (1.0 + tau / e1);
-    const double S = al0 + al1;
-    const double om0 = al0 / S, om1 = al1 / S;
+    // three reciprocals instead of ten divisions (FP64 divisions are long sequences on
+    // the FP64 pipe, which bounds this kernel)
+    const double ie0 = rcp_any(e0), ie1 = rcp_any(e1);
+    const double te0 = tau * ie0, te1 = tau * ie1;
+    const double al0 = (1.0 / 3.0) * (1.0 + te0), al1 = (2.0 / 3.0) * (1.0 + te1);
+    const double S = al0 + al1, iS = rcp_any(S);
+    const double om0 = al0 * iS, om1 = al1 * iS;
     const double dqb = wbar * om0, om0b = wbar * dq;
-    const double al0b = om0b * om1 / S, al1b = -om0b * om0 / S;
-    const double taub = al0b * (1.0 / 3.0) / e0 + al1b * (2.0 / 3.0) / e1;
+    const double al0b = om0b * om1 * iS, al1b = -om0b * om0 * iS;
+    const double taub = al0b * (1.0 / 3.0) * ie0 + al1b * (2.0 / 3.0) * ie1;
     const double sg = b1 > b0 ? 1.0 : (b1 < b0 ? -1.0 : 0.0);
-    const double e0b = -al0b * (1.0 / 3.0) * tau / (e0 * e0), e1b = -al1b * (2.0 / 3.0) * tau / (e1 * e1);
+    const double e0b = -al0b * (1.0 / 3.0) * te0 * ie0, e1b = -al1b * (2.0 / 3.0) * te1 * ie1;
     const double b0b = e0b - sg * taub;
     const double b1b = e1b + sg * taub;
     const double epsb2 = 2.0 * e2 * (e0b + e1b);
@@ -622,12 +634,13 @@ __global__ void __launch_bounds__(128) adjoint_face_kernel(const __grid_constant
         for (int q = 0; q < 3; ++q) tau[q] = q == DIR ? mu * (2.0 * dn[DIR]) - (2.0 / 3.0) * mu * div : mu * (dtd[q] + dn[q]);
         double dX[NS], Dcf[NS], Yf[NS], hf[NS], YL[NS], YR[NS];
         double corr = 0.0;
+        const double irL = rcp_any(rhoL), irR = rcp_any(rhoR);
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
             dX[s] = (Q[(size_t)(QL<NS>::X + s) * n + cR] - Q[(size_t)(QL<NS>::X + s) * n + cL]) * ih;
             Dcf[s] = 0.5 * (Q[(size_t)(QL<NS>::DC + s) * n + cL] + Q[(size_t)(QL<NS>::DC + s) * n + cR]);
-            YL[s] = U[(size_t)s * n + cL] / rhoL;
-            YR[s] = U[(size_t)s * n + cR] / rhoR;
+            YL[s] = U[(size_t)s * n + cL] * irL;
+            YR[s] = U[(size_t)s * n + cR] * irR;
             Yf[s] = 0.5 * (YL[s] + YR[s]);
             hf[s] = 0.5 * (Q[(size_t)(QL<NS>::H + s) * n + cL] + Q[(size_t)(QL<NS>::H + s) * n + cR]);
             corr += Dcf[s] * dX[s];
@@ -682,8 +695,8 @@ __global__ void __launch_bounds__(128) adjoint_face_kernel(const __grid_constant
         }
 #pragma unroll
         for (int s = 0; s < NS; ++s) {
-            addU(s, cL, (YLb[s] - sL) / rhoL);
-            addU(s, cR, (YRb[s] - sR) / rhoR);
+            addU(s, cL, (YLb[s] - sL) * irL);
+            addU(s, cR, (YRb[s] - sR) * irR);
         }
         double mub = 0.0, dnb[3] = {0, 0, 0}, dtdb[3] = {0, 0, 0}, dttb[3] = {0, 0, 0}, divb = 0.0;
 #pragma unroll
