@@ -59,7 +59,7 @@ class GridT:
     dx: float
     dy: float
     dz: float
-    bc: tuple = (0, 0, 0)     # per axis x, y, z: 0 periodic, 1 zero-gradient extrapolation
+    bc: tuple = (0, 0, 0)     # per axis x, y, z: 0 periodic, 1 zero-gradient extrapolation, 2 NSCBC
 
     @property
     def n(self):

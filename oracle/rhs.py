@@ -8,13 +8,15 @@ variable-major [nv, nz, ny, nx].  The RHS is
   S = (omega_1 .. omega_Ns, 0, 0, 0, q_L).
 
 `flags` switches terms off for tests: keys 'inviscid', 'viscous', 'chemistry',
-'laser' (all default True).
+'laser' (all default True); 'scheme' picks the inviscid reconstruction
+('weno3z' or 'teno6'); 'nscbc' maps an axis whose bc is 2 to its {side: Side}
+(oracle.nscbc; a missing side is an outflow with the defaults).
 """
 from __future__ import annotations
 
 import torch
 
-from . import chemistry, fluxes, laser as laser_mod, thermo, transport
+from . import chemistry, fluxes, laser as laser_mod, nscbc, thermo, transport
 from .mech import R_U, MechT
 
 
@@ -106,6 +108,8 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
         if _flag(flags, "inviscid"):
             Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns, scheme)
             out = out - fluxes.divergence(Fa, grid, d)
+            if grid.bc[d] == nscbc.BC_NSCBC:
+                out = nscbc.correct(mech, grid, st, Fa, out, d, (flags or {}).get("nscbc", {}).get(d))
         if _flag(flags, "viscous"):
             Fd = fluxes.diffusive_flux(velp, Tp, Xp, Yp, Dcp, hp, mup, lamp, grid, d, ns)
             out = out + fluxes.divergence(Fd, grid, d)
