@@ -258,6 +258,9 @@ def run_ours(args):
     # --- TENO6 (the paper's sixth-order scheme) on the same workload, both precisions
     teno = run_teno_leg(args, mech, case, prim, dev) if args.teno_steps > 0 else None
 
+    # --- characteristic inflow / outflow boundaries: injection case, mixed
+    nscbc = run_nscbc_leg(args, dev) if args.nscbc_steps > 0 else None
+
     # --- batched ensemble (64 members of uneven size): members/s per launch mode
     ens = run_ensemble_leg(args, dev) if args.ensemble_members > 0 else None
 
@@ -339,6 +342,7 @@ def run_ours(args):
         "kernels": kernels,
         "roofline": roofline,
         "teno6": teno,
+        "nscbc": nscbc,
         "min_ignition_energy": mie,
         "ensemble": ens,
         "adjoint": adj,
@@ -399,6 +403,63 @@ def run_teno_leg(args, mech, case, prim, dev):
                      "kernels_ms_per_launch": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]}}
         del ctx, U, T
         torch.cuda.empty_cache()
+    return out
+
+
+# ----------------------------------------------------------------------------- NSCBC leg
+
+def run_nscbc_leg(args, dev):
+    """Injection through characteristic boundaries (x inflow / outflow, y and z
+    zero-gradient) on an nx x ny x ny box, mixed precision: cell-updates/s, and the
+    same grid with zero-gradient x ends, so the difference is the boundary kernels'
+    cost (their time per step from the profile's 'other' class, less the stage
+    updates')."""
+    import torch
+    from paper_2202_02319_b300 import native as nv, synth
+    nx, ny = args.nscbc_nx, args.nscbc_ny
+    case = synth.case_jet_inflow(0, nx, ny, ny)
+    ns = case.mech.n_species
+    ncell = case.grid.ncells
+    mech = nv.init_mechanism(case.mech)
+    prim = torch.as_tensor(case.prim, dtype=torch.float64).reshape(5 + ns, ncell).to(dev)
+    out = {"grid": [nx, ny, ny], "cells": ncell, "steps": args.nscbc_steps}
+    for name, bcx in (("nscbc", synth.BC_NSCBC), ("zero_gradient", synth.BC_EXTRAPOLATE)):
+        grid = synth.Grid(nx, ny, ny, case.grid.dx, case.grid.dy, case.grid.dz, (bcx,) + tuple(case.grid.bc[1:]))
+        ctx = nv.create_ctx(mech, grid, nv.RF_MIXED)
+        if bcx == synth.BC_NSCBC:
+            for (axis, side), spec in case.nscbc.items():
+                kw = {k: v for k, v in spec.items() if k != "target"}
+                tg = spec.get("target")
+                tg = torch.as_tensor(tg, dtype=torch.float64).to(dev).contiguous() if tg is not None else None
+                nv.set_nscbc(ctx, axis, side, target=tg, **kw)
+        U = torch.empty((ns + 4, ncell), dtype=torch.float64, device=dev)
+        T = torch.empty(ncell, dtype=torch.float64, device=dev)
+        nv.init_state(ctx, prim, U, T)
+        t = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, None, None)
+        nv.check(ctx)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.nscbc_steps):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, None, None)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        nv.set_option(ctx, "profile", 1)
+        nv.rk_step(ctx, U, T, t, 0.0, case.cfl, None, None)
+        prof = nv.profile_read(ctx)
+        nv.set_option(ctx, "profile", 0)
+        nv.check(ctx)
+        out[name] = {"value": ncell * 3 * args.nscbc_steps / (ms * 1e-3), "unit": UNIT,
+                     "ms_per_step": ms / args.nscbc_steps, "other_ms_per_step": prof["other"][0],
+                     "other_launches_per_step": prof["other"][1]}
+        del ctx, U, T
+        torch.cuda.empty_cache()
+    out["boundary_kernels_ms_per_step"] = round(out["nscbc"]["other_ms_per_step"] - out["zero_gradient"]["other_ms_per_step"], 4)
+    out["step_time_ratio"] = round(out["nscbc"]["ms_per_step"] / out["zero_gradient"]["ms_per_step"], 4)
     return out
 
 
@@ -637,6 +698,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--teno-steps", type=int, default=4)
+    ap.add_argument("--nscbc-steps", type=int, default=10)
+    ap.add_argument("--nscbc-nx", type=int, default=256)
+    ap.add_argument("--nscbc-ny", type=int, default=128)
     ap.add_argument("--mie-members", type=int, default=8)
     ap.add_argument("--mie-n", type=int, default=48)
     ap.add_argument("--mie-steps", type=int, default=40)

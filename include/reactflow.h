@@ -63,7 +63,11 @@ enum rf_precision {
 
 enum rf_bc {
     RF_BC_PERIODIC = 0,
-    RF_BC_EXTRAPOLATE = 1 /* zero-gradient ghost cells (copies of the edge cell) */
+    RF_BC_EXTRAPOLATE = 1, /* zero-gradient ghost cells (copies of the edge cell) */
+    RF_BC_NSCBC = 2        /* Navier-Stokes characteristic boundaries at both ends of the axis
+                              (see rf_set_nscbc; the axis needs >= 3 cells).  Single-grid RHS
+                              and RK steps in both precisions and with either scheme; rejected
+                              by rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
 };
 
 enum rf_flags {           /* term switches for tests (0 = full method) and the scheme */
@@ -209,6 +213,43 @@ int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U
  *                  kernel launch of this context (read with rf_profile_read); 0: off
  * Errors: RF_EINVAL for an unknown key or a value out of range. */
 int rf_set_option(rf_ctx *c, const char *key, double value);
+
+/* One end of an NSCBC axis (paper: Application examples - the diffusion flame's left
+ * and right boundaries and the combustor's injector inlet and nozzle outlet use the
+ * Navier-Stokes characteristic boundary conditions for reacting flows, after Poinsot &
+ * Lele 1992 and Okong'o & Bellan 2002).  Along the axis the sweeps use zero-gradient
+ * ghost cells; in the first and last cell layer the inviscid normal term is replaced
+ * by its characteristic form: wave amplitudes from one-sided second-order normal
+ * derivatives of (rho, u_n, u_t1, u_t2, p, Y_s) with the frozen sound speed c, the
+ * amplitudes of waves entering the domain replaced as below, and the conserved
+ * rates formed with the multicomponent energy closure.  With ell = length,
+ * M = |u_n| / c and F = max(1 - M^2, 0):
+ *   outflow (target NULL): entering acoustic wave sigma c F (p - p_inf) / ell
+ *     (partially non-reflecting; sigma = 0 is perfectly non-reflecting), entering
+ *     entropy, shear and species waves 0;
+ *   inflow (target given): the entering waves relax u_n, T, u_t and Y_s towards the
+ *     target at rates eta_u c F / (2 ell), eta_T c / (gamma ell), eta_t c / ell and
+ *     eta_Y c / ell.
+ * Defaults at rf_create_ctx (both ends of every NSCBC axis): outflow, p_inf = 101325 Pa,
+ * sigma = 0.25, every eta 1, length the domain length along the axis. */
+typedef struct {
+    double p_inf;             /* outflow: far-field pressure, Pa (> 0) */
+    double sigma;             /* outflow: pressure relaxation coefficient (>= 0) */
+    double eta_u, eta_T, eta_t, eta_Y;  /* inflow: relaxation coefficients (>= 0) */
+    double length;            /* ell, m; <= 0: the number of cells along the axis times its spacing */
+    const double *target;     /* NULL: outflow.  Inflow: device array, FP64, [4 + Ns][plane] holding
+                                 (u, v, w, T, Y_1 .. Y_Ns) for each cell of the boundary plane;
+                                 plane index = i_t1 + n_t1 i_t2 with t1 < t2 the two other axes
+                                 (x axis: j + ny k; y axis: i + nx k; z axis: i + nx j).  Owned
+                                 by the caller and read at every evaluation: it must stay valid
+                                 (and may be changed between calls) while the side is set. */
+} rf_nscbc;
+
+/* Sets one end (side 0: low, the cells with index 0; side 1: high, index n - 1) of the
+ * NSCBC axis `axis` (0 x, 1 y, 2 z) of context c; takes effect from the next call.
+ * Errors: RF_EINVAL (null argument, axis or side out of range, the axis not NSCBC,
+ * a non-finite or negative coefficient, an outflow side with p_inf <= 0). */
+int rf_set_nscbc(rf_ctx *c, int axis, int side, const rf_nscbc *b);
 
 /* Kernel classes of rf_profile_read: cell state, x sweep, y sweep, z sweep, other. */
 enum { RF_PROF_CELL = 0, RF_PROF_SWEEP_X = 1, RF_PROF_SWEEP_Y = 2, RF_PROF_SWEEP_Z = 3, RF_PROF_OTHER = 4, RF_PROF_N = 5 };

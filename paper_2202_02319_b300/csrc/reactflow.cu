@@ -154,6 +154,8 @@ struct rf_ctx {
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
+    // characteristic boundaries of the axes whose bc is RF_BC_NSCBC (rf_set_nscbc)
+    NscbcAxis nscbc[3];
 };
 
 // record a start event before and a stop event after one launch of class k
@@ -436,8 +438,12 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(RF_EINVAL, "rf_create_ctx: grid %dx%dx%d has an empty axis", g->nx, g->ny, g->nz);
     if (g->nx > 1024) return fail(RF_EINVAL, "rf_create_ctx: nx = %d exceeds 1024", g->nx);
     if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return fail(RF_EINVAL, "rf_create_ctx: grid spacing must be > 0");
-    for (int a = 0; a < 3; ++a)
-        if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_create_ctx: bc[%d] = %d unknown", a, g->bc[a]);
+    for (int a = 0; a < 3; ++a) {
+        if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE && g->bc[a] != RF_BC_NSCBC)
+            return fail(RF_EINVAL, "rf_create_ctx: bc[%d] = %d unknown", a, g->bc[a]);
+        const int na = a == 0 ? g->nx : (a == 1 ? g->ny : g->nz);
+        if (g->bc[a] == RF_BC_NSCBC && na < 3) return fail(RF_EINVAL, "rf_create_ctx: NSCBC axis %d has %d cells (needs >= 3)", a, na);
+    }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_create_ctx: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
     int mslot = 0;
@@ -456,6 +462,10 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     c->nv = m->ns + 4;
     c->nq = Q_X0 + 3 * m->ns;
     c->rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);
+    for (int a = 0; a < 3; ++a) {
+        const double len = (a == 0 ? g->nx * g->dx : (a == 1 ? g->ny * g->dy : g->nz * g->dz));
+        for (int e = 0; e < 2; ++e) c->nscbc[a].s[e] = NscbcSide{101325.0, 0.25, 1.0, 1.0, 1.0, 1.0, len, nullptr};
+    }
     const size_t n = (size_t)c->n;
     struct A {
         void **p;
@@ -590,6 +600,29 @@ struct Path {
         return RF_OK;
     }
 
+    // characteristic boundary terms of every NSCBC axis, after the cell state has
+    // filled the RHS accumulator and before the sweeps add to it
+    template <int DIR, int SCHEME>
+    static void nscbc_axis(rf_ctx *c, const Member &m, cudaStream_t s) {
+        const int nn[3] = {c->g.nx, c->g.ny, c->g.nz};
+        const long long plane = (long long)nn[DIR == 0 ? 1 : 0] * nn[DIR == 2 ? 1 : 2];
+        nscbc_kernel<R, UT, NS, DIR, SCHEME><<<(unsigned)((2 * plane + 127) / 128), 128, 0, s>>>(c->mslot, m, c->nscbc[DIR]);
+    }
+
+    static int nscbc(rf_ctx *c, const Member &m, cudaStream_t s) {
+        if (m.flags & F_NO_INVISCID) return RF_OK;
+        const bool teno = (c->flags & RF_TENO6) != 0;
+        for (int d = 0; d < 3; ++d) {
+            if (c->g.bc[d] != RF_BC_NSCBC) continue;
+            ProfScope ps(c, PROF_OTHER, s);
+            if (d == 0) teno ? nscbc_axis<0, 1>(c, m, s) : nscbc_axis<0, 0>(c, m, s);
+            else if (d == 1) teno ? nscbc_axis<1, 1>(c, m, s) : nscbc_axis<1, 0>(c, m, s);
+            else teno ? nscbc_axis<2, 1>(c, m, s) : nscbc_axis<2, 0>(c, m, s);
+            LAUNCH_CHECK();
+        }
+        return RF_OK;
+    }
+
     // TENO6 sweeps: thread per face from global memory (six-cell stencils), both precisions
     template <int MODE>
     static int sweep_teno(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
@@ -718,6 +751,7 @@ struct Path {
         set_laser(m, L);
         int rc = cell_state(c, m, s);
         if (rc) return rc;
+        if ((rc = nscbc(c, m, s))) return rc;
         return sweeps<MODE_RHS>(c, m, s);
     }
 
@@ -761,6 +795,7 @@ struct Path {
                 return rc;
             }
             if (k == 2 && t_final_ev) CUDA_TRY(cudaEventRecord(t_final_ev, s));
+            if ((rc = nscbc(c, m, s))) return rc;
             if (k == 0) {
                 dt_kernel<<<1, 1, 0, s>>>(c->clock, c->rates, hmin, !(c->flags & RF_NO_VISCOUS),
                                           !(c->flags & RF_NO_CHEMISTRY) && c->mech->nr > 0, m.laser_on && !(c->flags & RF_NO_LASER),
@@ -921,6 +956,25 @@ extern "C" int rf_set_option(rf_ctx *c, const char *key, double value) {
     } else {
         return fail(RF_EINVAL, "rf_set_option: unknown key '%s'", key);
     }
+    return RF_OK;
+}
+
+extern "C" int rf_set_nscbc(rf_ctx *c, int axis, int side, const rf_nscbc *b) {
+    if (!c || !b) return fail(RF_EINVAL, "rf_set_nscbc: null argument");
+    if (axis < 0 || axis > 2) return fail(RF_EINVAL, "rf_set_nscbc: axis %d outside 0..2", axis);
+    if (side != 0 && side != 1) return fail(RF_EINVAL, "rf_set_nscbc: side %d is neither 0 (low) nor 1 (high)", side);
+    if (c->g.bc[axis] != RF_BC_NSCBC) return fail(RF_EINVAL, "rf_set_nscbc: axis %d is not an NSCBC axis (bc = %d)", axis, c->g.bc[axis]);
+    const double co[6] = {b->p_inf, b->sigma, b->eta_u, b->eta_T, b->eta_t, b->eta_Y};
+    for (int k = 0; k < 6; ++k)
+        if (!std::isfinite(co[k])) return fail(RF_EINVAL, "rf_set_nscbc: non-finite coefficient");
+    if (b->sigma < 0 || b->eta_u < 0 || b->eta_T < 0 || b->eta_t < 0 || b->eta_Y < 0)
+        return fail(RF_EINVAL, "rf_set_nscbc: relaxation coefficients must be >= 0");
+    if (!b->target && !(b->p_inf > 0)) return fail(RF_EINVAL, "rf_set_nscbc: an outflow side needs p_inf > 0");
+    if (!std::isfinite(b->length)) return fail(RF_EINVAL, "rf_set_nscbc: non-finite length");
+    const int na = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+    const double h = axis == 0 ? c->g.dx : (axis == 1 ? c->g.dy : c->g.dz);
+    c->nscbc[axis].s[side] = NscbcSide{b->p_inf, b->sigma, b->eta_u, b->eta_T, b->eta_t, b->eta_Y,
+                                       b->length > 0 ? b->length : na * h, b->target};
     return RF_OK;
 }
 
@@ -1211,6 +1265,10 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d has a null context or buffer", i);
         }
+        if (c->g.bc[0] == RF_BC_NSCBC || c->g.bc[1] == RF_BC_NSCBC || c->g.bc[2] == RF_BC_NSCBC) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d has an NSCBC axis; batched ensembles run periodic and zero-gradient axes", i);
+        }
         if (c->flags & RF_TENO6) {
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d uses TENO6; batched ensembles run WENO3-Z", i);
@@ -1447,6 +1505,8 @@ struct AdjWs {
 
 static int adj_ws(rf_ctx *c, AdjWs &w) {
     if (c->flags & RF_TENO6) return fail(RF_EINVAL, "the discrete adjoint is built for WENO3-Z, not TENO6");
+    for (int a = 0; a < 3; ++a)
+        if (c->g.bc[a] == RF_BC_NSCBC) return fail(RF_EINVAL, "the discrete adjoint is built for periodic and zero-gradient axes, not NSCBC (axis %d)", a);
     if (c->mech->npress > 0) return fail(RF_EINVAL, "the discrete adjoint is built for elementary reactions (the mechanism has %d pressure-dependent ones)", c->mech->npress);
     const size_t n = (size_t)c->n, nv = c->nv, nq = c->nq;
     const size_t tot = nq * n + 6 * nv * n + 3 * n;
@@ -1738,8 +1798,11 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
     if (g->nx < 1 || g->ny < 1 || g->nz < 1) return fail(RF_EINVAL, "rf_rhs_noalloc: grid %dx%dx%d has an empty axis", g->nx, g->ny, g->nz);
     if (g->nx > 1024) return fail(RF_EINVAL, "rf_rhs_noalloc: nx = %d exceeds 1024", g->nx);
     if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0)) return fail(RF_EINVAL, "rf_rhs_noalloc: grid spacing must be > 0");
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) {
+        if (g->bc[a] == RF_BC_NSCBC)
+            return fail(RF_EINVAL, "rf_rhs_noalloc: bc[%d] is NSCBC, whose side settings live in a context (rf_set_nscbc)", a);
         if (g->bc[a] != RF_BC_PERIODIC && g->bc[a] != RF_BC_EXTRAPOLATE) return fail(RF_EINVAL, "rf_rhs_noalloc: bc[%d] = %d unknown", a, g->bc[a]);
+    }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_rhs_noalloc: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_rhs_noalloc: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
     const long long n = (long long)g->nx * g->ny * g->nz;

@@ -1987,4 +1987,190 @@ __global__ void diag_fold_kernel(const double *partial, int nblocks, int nvals, 
     if (lane == 0) out[v] = acc;
 }
 
+// ----------------------------------------------------------------------------- characteristic boundaries
+
+// Navier-Stokes characteristic boundary conditions (NSCBC) for the reacting
+// equations (Application examples: the diffusion flame's and the combustor's inflow
+// and outflow boundaries, after Poinsot & Lele 1992 and Okong'o & Bellan 2002).
+// Along an NSCBC axis the sweeps run with zero-gradient ghost cells; in the first and
+// the last cell layer the scheme's inviscid normal term is then replaced by the
+// characteristic form -P(V) d of the local one-dimensional inviscid relations:
+//   wave amplitudes from one-sided second-order normal derivatives of
+//   V = (rho, u_n, u_t1, u_t2, p, Y_s), c the frozen sound speed,
+//     L1 = (u_n - c)(p' - rho c u_n'), L5 = (u_n + c)(p' + rho c u_n'),
+//     L2 = u_n (c^2 rho' - p'), L3 = u_n u_t1', L4 = u_n u_t2', LY_s = u_n Y_s';
+//   incoming amplitudes (speed pointing into the domain) replaced: at an outflow
+//   side the acoustic one by K (p - p_inf), K = sigma c max(1 - M^2, 0) / ell, the
+//   others by 0; at an inflow side by relaxations towards the target plane
+//   (s eta_u rho c^2 max(1 - M^2, 0)(u_n - u_n,t) / ell, s = +1 low / -1 high;
+//   -eta_T rho c Rbar (T - T_t) / ell; eta_t c (u_t - u_t,t) / ell;
+//   eta_Y c (Y_s - Y_s,t) / ell);
+//   d1 = (L2 + (L5 + L1) / 2) / c^2, d2 = (L5 + L1) / 2, d_n = (L5 - L1) / (2 rho c),
+//   d_t1 = L3, d_t2 = L4, dY_s = LY_s (the rates -drho/dt, -dp/dt, -du/dt, -dY/dt);
+//   conserved form with the multicomponent energy closure (e_s = h_s - R T / W_s,
+//   gamma = rho c^2 / p):  [rho Y_s] -(Y_s d1 + rho dY_s);  [rho u_k] -(u_k d1 + rho d_k);
+//   [E] -(|u|^2 d1 / 2 + rho u . d) + sum_s e_s [rho Y_s] + p / (gamma - 1)
+//   (d1 / rho - d2 / p + Wbar sum_s dY_s / W_s).
+// One thread per boundary cell (both ends of the axis); it recomputes the cell's two
+// inviscid face fluxes with the sweep's own face code and adds
+// (characteristic term - scheme term) to the RHS accumulator, before the sweeps add
+// the scheme term.  The characteristic term is formed in FP64 in both precisions
+// (a few planes of cells).
+struct NscbcSide {
+    double p_inf, sigma, eta_u, eta_T, eta_t, eta_Y, ell;
+    const double *target;        // [4 + NS][plane] (u, v, w, T, Y_s) or nullptr (outflow)
+};
+struct NscbcAxis {
+    NscbcSide s[2];              // low end, high end
+};
+
+template <typename R, typename UT, int NS, int DIR, int SCHEME>
+__global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_constant__ Member m,
+                                                    const __grid_constant__ NscbcAxis bx) {
+    constexpr int NV = NS + 4;
+    constexpr int T1 = DIR == 0 ? 1 : 0, T2 = DIR == 2 ? 1 : 2;   // tangential axes, increasing
+    const MechDev &M = c_mech[mslot];
+    const int nn[3] = {m.nx, m.ny, m.nz};
+    const int nd = nn[DIR], n1 = nn[T1];
+    const long long plane = (long long)n1 * nn[T2];
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 2 * plane) return;
+    const int side = id >= plane ? 1 : 0;
+    const long long pc = id - side * plane;       // index on the boundary plane, t1 fastest
+    int cc[3];
+    cc[T1] = (int)(pc % n1);
+    cc[T2] = (int)(pc / n1);
+    cc[DIR] = side ? nd - 1 : 0;
+    const long long st[3] = {1, m.nx, (long long)m.nx * m.ny};
+    const long long n = m.n;
+    const long long cell = (long long)cc[0] + (long long)cc[1] * st[1] + (long long)cc[2] * st[2];
+    const long long inw = side ? -st[DIR] : st[DIR];
+    const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
+    const R *Q = (const R *)m.Q;
+
+    // the scheme's inviscid normal term, G at the cell's low face and high face
+    R G0[NV], G1[NV];
+    {
+        R rl, rr;
+        int cf[3] = {cc[0], cc[1], cc[2]};
+        if (SCHEME == 1) {
+            const GlobalStencil6<R, UT, DIR> s0(m, U, Q, cf);
+            face_invisc_teno<R, NS, DIR>(m, s0, G0, rl, rr);
+            cf[DIR] += 1;
+            const GlobalStencil6<R, UT, DIR> s1(m, U, Q, cf);
+            face_invisc_teno<R, NS, DIR>(m, s1, G1, rl, rr);
+        } else {
+            const GlobalStencil<R, UT, DIR> s0(m, U, Q, cf);
+            face_invisc<R, NS, DIR>(m, s0, G0, rl, rr);
+            cf[DIR] += 1;
+            const GlobalStencil<R, UT, DIR> s1(m, U, Q, cf);
+            face_invisc<R, NS, DIR>(m, s1, G1, rl, rr);
+        }
+    }
+
+    // primitives of the boundary cell and its two inward neighbours
+    const double *__restrict__ Ud = m.U;
+    double rho[3], un[3], u1[3], u2[3], p[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const long long ck = cell + k * inw;
+        double r = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) r += Ud[s * n + ck];
+        rho[k] = r;
+        un[k] = wide(Q[(Q_U + DIR) * n + ck]);
+        u1[k] = wide(Q[(Q_U + T1) * n + ck]);
+        u2[k] = wide(Q[(Q_U + T2) * n + ck]);
+        p[k] = wide(Q[Q_P * n + ck]);
+    }
+    // d/dn = h2 (-3 f_0 + 4 f_1 - f_2), f_k k cells inward (h2 = -+1 / (2h) high / low)
+    const double h2 = (side ? -0.5 : 0.5) * m.invh[DIR];
+    auto ddn = [&](const double (&f)[3]) { return h2 * (fma(-3.0, f[0], 4.0 * f[1]) - f[2]); };
+    const double r0 = rho[0], u_n = un[0], p0 = p[0];
+    const double c = wide(Q[Q_C * n + cell]), T = wide(Q[Q_T * n + cell]);
+    const double ir[3] = {1.0 / rho[0], 1.0 / rho[1], 1.0 / rho[2]};
+    double Yb[NS], LY[NS];
+    double iWbar = 0.0;                           // sum_s Y_s / W_s
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const double y[3] = {Ud[s * n + cell] * ir[0], Ud[s * n + cell + inw] * ir[1], Ud[s * n + cell + 2 * inw] * ir[2]};
+        Yb[s] = y[0];
+        LY[s] = u_n * ddn(y);
+        iWbar = fma(y[0], M.invW[s], iWbar);
+    }
+    const double drho = ddn(rho), dun = ddn(un), dp = ddn(p);
+    double L1 = (u_n - c) * (dp - r0 * c * dun);
+    double L5 = (u_n + c) * (dp + r0 * c * dun);
+    double L2 = u_n * (c * c * drho - dp);
+    double L3 = u_n * ddn(u1), L4 = u_n * ddn(u2);
+
+    // incoming amplitudes
+    const NscbcSide &sd = bx.s[side];
+    const double F = fmax(1.0 - (u_n / c) * (u_n / c), 0.0);
+    const double cl = c / sd.ell;
+    const bool tgt = sd.target != nullptr;
+    double ac, ent = 0.0, sh1 = 0.0, sh2 = 0.0;
+    if (!tgt) {
+        ac = sd.sigma * cl * F * (p0 - sd.p_inf);
+    } else {
+        const double *__restrict__ tg = sd.target;
+        double tv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) tv[k] = tg[k * plane + pc];
+        ac = (side ? -1.0 : 1.0) * sd.eta_u * r0 * c * cl * F * (u_n - tv[DIR]);
+        double Rbar = 0.0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) Rbar = fma(Yb[s], M.RW[s], Rbar);
+        ent = -sd.eta_T * r0 * Rbar * cl * (T - tg[3 * plane + pc]);
+        sh1 = sd.eta_t * cl * (u1[0] - tv[T1]);
+        sh2 = sd.eta_t * cl * (u2[0] - tv[T2]);
+    }
+    const bool in_m = side ? (u_n - c < 0.0) : (u_n - c > 0.0);
+    const bool in_p = side ? (u_n + c < 0.0) : (u_n + c > 0.0);
+    const bool in_0 = side ? (u_n < 0.0) : (u_n > 0.0);
+    if (in_m) L1 = ac;
+    if (in_p) L5 = ac;
+    if (in_0) {
+        L2 = ent;
+        L3 = sh1;
+        L4 = sh2;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) LY[s] = tgt ? sd.eta_Y * cl * (Yb[s] - sd.target[(4 + s) * plane + pc]) : 0.0;
+    }
+
+    // -P(V) d
+    const double d1 = (L2 + 0.5 * (L5 + L1)) / (c * c);
+    const double d2 = 0.5 * (L5 + L1);
+    double dk[3], vel[3];
+    dk[DIR] = (L5 - L1) / (2.0 * r0 * c);
+    dk[T1] = L3;
+    dk[T2] = L4;
+    vel[DIR] = u_n;
+    vel[T1] = u1[0];
+    vel[T2] = u2[0];
+    double out[NV];
+    double eW = 0.0, sdY = 0.0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        out[s] = -fma(Yb[s], d1, r0 * LY[s]);
+        const double e_s = fma(-M.RW[s], T, wide(Q[(QL<NS>::H + s) * n + cell]));
+        eW = fma(e_s, out[s], eW);
+        sdY = fma(LY[s], M.invW[s], sdY);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) out[NS + k] = -fma(vel[k], d1, r0 * dk[k]);
+    const double ke = 0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    const double gm1 = r0 * c * c / p0 - 1.0;
+    const double dT = p0 / gm1 * (d1 / r0 - d2 / p0 + sdY / iWbar);
+    out[NS + 3] = -(ke * d1 + r0 * (vel[0] * dk[0] + vel[1] * dk[1] + vel[2] * dk[2])) + eW + dT;
+
+    R *__restrict__ rhs = (R *)m.rhs;
+    const R ih = (R)m.invh[DIR];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const double scheme = wide((G1[v] - G0[v]) * ih);
+        rhs[v * n + cell] = narrow<R>(wide(rhs[v * n + cell]) + (out[v] - scheme));
+    }
+}
+
 }  // namespace rf

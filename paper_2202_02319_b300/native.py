@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libr
 RF_OK, RF_EINVAL, RF_ENEWTON, RF_ENONFINITE, RF_ERANGE, RF_ECUDA, RF_ETIMEOUT, RF_ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 RF_FP64, RF_MIXED = 0, 1
 RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER, RF_TENO6 = 1, 2, 4, 8, 16
+RF_BC_PERIODIC, RF_BC_EXTRAPOLATE, RF_BC_NSCBC = 0, 1, 2
 CODE_NAMES = {0: "RF_OK", -1: "RF_EINVAL", -2: "RF_ENEWTON", -3: "RF_ENONFINITE", -4: "RF_ERANGE",
               -5: "RF_ECUDA", -6: "RF_ETIMEOUT", -7: "RF_ENOMEM"}
 
@@ -45,6 +46,11 @@ class Laser(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("E", "x0", "y0", "z0", "sigma_r", "t0", "sigma_t")]
 
 
+class NscbcDesc(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("p_inf", "sigma", "eta_u", "eta_T", "eta_t", "eta_Y", "length")] + \
+        [("target", ctypes.c_void_p)]
+
+
 class Diag(ctypes.Structure):
     _fields_ = [("total", ctypes.c_double * 32), ("heat_release", ctypes.c_double), ("max_T", ctypes.c_double),
                 ("nv", ctypes.c_int)]
@@ -64,6 +70,7 @@ _sigs = {
     "rf_rk_step_host": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(Laser), _vp, _vp]),
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
+    "rf_set_nscbc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(NscbcDesc)]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
     "rf_probe_math": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong, _vp]),
@@ -176,6 +183,7 @@ class Context:
         self.flags = flags
         self.n = grid.nx * grid.ny * grid.nz
         self.nv = mech.n_species + 4
+        self.nscbc_targets = {}          # (axis, side) -> inflow target tensor the library reads
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -236,6 +244,24 @@ def rk_step_host(ctx: Context, U_in, T_in, U_out, T_out, t_dev, dt_fixed: float 
 
 def set_option(ctx: Context, key: str, value: float):
     _check(_lib.rf_set_option(ctx.handle, key.encode(), float(value)), "rf_set_option")
+
+
+def set_nscbc(ctx: Context, axis: int, side: int, p_inf: float = 101325.0, sigma: float = 0.25, eta_u: float = 1.0,
+              eta_T: float = 1.0, eta_t: float = 1.0, eta_Y: float = 1.0, length: float = 0.0, target=None):
+    """One end of an NSCBC axis (rf_set_nscbc): an outflow when target is None, else an
+    inflow relaxing towards target, a contiguous float64 CUDA tensor [4 + Ns, plane]
+    (u, v, w, T, Y_s) that the context keeps a reference to while the side is set."""
+    if target is not None:
+        import torch
+        if not (target.is_cuda and target.dtype == torch.float64 and target.is_contiguous()):
+            raise ValueError("target must be a contiguous float64 CUDA tensor")
+    d = NscbcDesc(float(p_inf), float(sigma), float(eta_u), float(eta_T), float(eta_t), float(eta_Y), float(length),
+                  _ptr(target) if target is not None else None)
+    _check(_lib.rf_set_nscbc(ctx.handle, int(axis), int(side), ctypes.byref(d)), "rf_set_nscbc")
+    if target is not None:
+        ctx.nscbc_targets[(axis, side)] = target
+    else:
+        ctx.nscbc_targets.pop((axis, side), None)
 
 
 def probe_peak(kind: int, stream=None) -> float:

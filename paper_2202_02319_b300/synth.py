@@ -30,6 +30,7 @@ T_REF = 298.15           # K, reference temperature of formation data
 
 BC_PERIODIC = 0
 BC_EXTRAPOLATE = 1
+BC_NSCBC = 2
 
 
 def stream(seed: int, name: str) -> np.random.Generator:
@@ -342,6 +343,10 @@ class Case:
     laser: Laser = field(default_factory=Laser)
     steps: int = 10
     cfl: float = 0.5
+    # characteristic boundaries: (axis, side) -> {p_inf, sigma, eta_u, eta_T, eta_t,
+    # eta_Y, length, target}; target None (outflow) or [4 + Ns, plane] (u, v, w, T, Y_s)
+    # on the boundary plane, plane index t1 + n_t1 t2 over the two other axes
+    nscbc: dict = field(default_factory=dict)
 
 
 def _centres(n: int, d: float) -> np.ndarray:
@@ -443,6 +448,45 @@ def case_mixing_layer(seed: int = 0, n: int = 512) -> Case:
     prim = np.concatenate([np.full((1, 1, n, n), P_ATM), T[None], u[None], v[None],
                            np.zeros((1, 1, n, n)), Yf])
     return Case(f"mixing_layer_{n}x{n}", mech, grid, prim, Laser(), steps=200)
+
+
+def case_jet_inflow(seed: int = 0, nx: int = 64, ny: int = 48, nz: int = 1, u_jet: float = 100.0,
+                    u_co: float = 5.0, noise: float = 0.01) -> Case:
+    """Injection through characteristic boundaries, after the paper's diffusion flame
+    (an oxidiser jet from the centre of the left boundary into quiescent fuel, a slow
+    fuel co-flow from the rest of that boundary, NSCBC inflow on the left and outflow
+    on the right): nx x ny x nz cells of 1e-4 m, x an NSCBC axis, y and z zero-gradient.
+    The domain starts as fuel (X2) at 1 atm and 300 K moving at u_co, with white noise
+    of rms noise * u_jet on every velocity component (w only in 3-D).  Inflow target: air-like oxidiser in the jet (radius ny / 8
+    cells about the plane's centre, tanh edge one cell wide) at u_jet, fuel at u_co
+    elsewhere, 300 K; relaxation coefficients eta = 1.  Outflow: p_inf = 1 atm,
+    sigma = 0.25."""
+    mech = mechanism_9sp(seed)
+    dx = 1.0e-4
+    bcz = BC_EXTRAPOLATE if nz > 1 else BC_PERIODIC
+    grid = Grid(nx, ny, nz, dx, dx, dx, (BC_NSCBC, BC_EXTRAPOLATE, bcz))
+    g = stream(seed, f"jetin{nx}x{ny}x{nz}/noise")
+    shape = (nz, ny, nx)
+    fu, ox = _fuel(mech), _air(mech)
+    prim = np.zeros((5 + mech.n_species,) + shape)
+    prim[0] = P_ATM
+    prim[1] = 300.0
+    prim[2] = u_co + noise * u_jet * g.standard_normal(shape)
+    prim[3] = noise * u_jet * g.standard_normal(shape)
+    if nz > 1:
+        prim[4] = noise * u_jet * g.standard_normal(shape)
+    prim[5:] = fu[:, None, None, None]
+    yc = _centres(ny, dx) - ny * dx / 2
+    zc = _centres(nz, dx) - nz * dx / 2 if nz > 1 else np.zeros(1)
+    r = np.sqrt(yc[None, :] ** 2 + zc[:, None] ** 2)                        # [nz, ny]
+    phi = 0.5 * (1.0 - np.tanh((r - (ny / 8) * dx) / dx))                   # 1 in the jet
+    target = np.zeros((4 + mech.n_species, nz, ny))
+    target[0] = u_co + (u_jet - u_co) * phi
+    target[3] = 300.0
+    target[4:] = phi[None] * ox[:, None, None] + (1.0 - phi)[None] * fu[:, None, None]
+    sides = {(0, 0): dict(p_inf=P_ATM, target=target.reshape(4 + mech.n_species, nz * ny)),
+             (0, 1): dict(p_inf=P_ATM, sigma=0.25, target=None)}
+    return Case(f"jet_inflow_{nx}x{ny}x{nz}", mech, grid, prim, Laser(), steps=100, nscbc=sides)
 
 
 def _torch_gen(seed: int, name: str, device):

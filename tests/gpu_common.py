@@ -26,7 +26,33 @@ def gpu_setup(case, precision=0, flags=0, options=None):
     T = torch.empty(n, dtype=F64, device="cuda")
     nv.init_state(ctx, prim, U, T)
     nv.check(ctx)
+    nscbc_gpu(ctx, case)
     return mech, ctx, U, T
+
+
+def nscbc_gpu(ctx, case):
+    """Sets the case's characteristic-boundary sides on a context."""
+    from paper_2202_02319_b300 import native as nv
+    for (axis, side), spec in getattr(case, "nscbc", {}).items():
+        kw = {k: v for k, v in spec.items() if k != "target"}
+        tg = spec.get("target")
+        if tg is not None:
+            tg = torch.as_tensor(np.ascontiguousarray(tg), dtype=F64).cuda().contiguous()
+        nv.set_nscbc(ctx, axis, side, target=tg, **kw)
+
+
+def nscbc_oracle(case):
+    """The oracle's 'nscbc' flags entry ({axis: {side: Side}}) of the case's sides."""
+    g = case.grid
+    out = {}
+    for (axis, side), spec in getattr(case, "nscbc", {}).items():
+        kw = {k: v for k, v in spec.items() if k != "target"}
+        tg = spec.get("target")
+        if tg is not None:
+            plane = tuple(n for a, n in ((2, g.nz), (1, g.ny), (0, g.nx)) if a != axis)
+            tg = torch.as_tensor(np.asarray(tg), dtype=F64).reshape((tg.shape[0],) + plane)
+        out.setdefault(axis, {})[side] = oracle.nscbc.Side(target=tg, **kw)
+    return out
 
 
 def oracle_setup(case):
@@ -49,6 +75,18 @@ def rel_inf(a, b):
     num = (a - b).abs().amax(1)
     den = b.abs().amax(1)
     return torch.where(den > 0, num / torch.where(den > 0, den, torch.ones_like(den)), num).numpy()
+
+
+def rel_inf_group(a, b, ns):
+    """Per-variable ||a_v - b_v||_inf over the largest |b| of the variable's group
+    (species, momentum, energy), as a numpy vector: a variable whose values are all
+    tiny (a species nothing produces yet) is measured against its group's scale."""
+    a = a.reshape(a.shape[0], -1).double().cpu()
+    b = b.reshape(b.shape[0], -1).double().cpu()
+    num = (a - b).abs().amax(1)
+    m = b.abs().amax(1)
+    scale = torch.cat([m[:ns].max().repeat(ns), m[ns:ns + 3].max().repeat(3), m[ns + 3:]])
+    return (num / scale).numpy()
 
 
 def rel_l2(a, b):

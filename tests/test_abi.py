@@ -52,10 +52,22 @@ def test_host_argument_checks():
         nv.init_mechanism(five)
     # grid checks happen before any allocation
     for g in (synth.Grid(0, 4, 4, 1e-4, 1e-4, 1e-4), synth.Grid(2048, 1, 1, 1e-4, 1e-4, 1e-4),
-              synth.Grid(4, 4, 4, -1.0, 1e-4, 1e-4), synth.Grid(4, 4, 4, 1e-4, 1e-4, 1e-4, (0, 7, 0))):
+              synth.Grid(4, 4, 4, -1.0, 1e-4, 1e-4), synth.Grid(4, 4, 4, 1e-4, 1e-4, 1e-4, (0, 7, 0)),
+              synth.Grid(4, 2, 4, 1e-4, 1e-4, 1e-4, (0, synth.BC_NSCBC, 0))):
         with pytest.raises(nv.ReactFlowError) as e:
             nv.create_ctx(mech, g)
         assert e.value.code == nv.RF_EINVAL
+    # NSCBC: the allocation-free RHS has no context for the side settings; a null
+    # context is refused before any device call
+    f = ctypes.CDLL(nv.LIB_PATH).rf_rhs_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.POINTER(nv.GridDesc), ctypes.c_int, ctypes.c_uint32, ctypes.c_void_p,
+                  ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    gd = nv.GridDesc(8, 8, 1, 1e-4, 1e-4, 1e-4, (ctypes.c_int * 3)(synth.BC_NSCBC, 0, 0))
+    assert f(mech.handle, ctypes.byref(gd), 0, 0, 16, 16, 0.0, None, 16, None) == nv.RF_EINVAL
+    assert "NSCBC" in nv.last_error()
+    d = nv.NscbcDesc(101325.0, 0.25, 1.0, 1.0, 1.0, 1.0, 0.0, None)
+    assert nv._lib.rf_set_nscbc(None, 0, 0, ctypes.byref(d)) == nv.RF_EINVAL
     # more than three molecules on one side of a reaction
     m2 = synth.mechanism_4sp(0)
     m2.nu_f = m2.nu_f.copy()
