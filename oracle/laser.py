@@ -6,7 +6,8 @@ with E_L an energy per unit depth of a two-dimensional domain.  Reading for
 three-dimensional grids: the normalisation becomes (2 pi)^2 sigma_r^3 sigma_t,
 so that the space-time integral of q_L equals E_L [J].  A grid with nz = 1 uses
 the paper's two-dimensional form with r measured in the x-y plane.  Cell
-centres sit at ((i + 1/2) dx, (j + 1/2) dy, (k + 1/2) dz); no periodic images.
+centres sit at ((i + 1/2) dx, (j + 1/2) dy, (k + 1/2) dz) (on a mapped grid: the
+mean of each cell's eight corners); no periodic images.
 """
 from __future__ import annotations
 
@@ -27,7 +28,11 @@ def laser_source(grid, t: float, las) -> torch.Tensor:
     """q_L [W/m^3] on the grid; `las` = (E, x0, y0, z0, sigma_r, t0, sigma_t),
     numbers or 0-d tensors."""
     E, x0, y0, z0, sr, t0, st = las
-    X, Y, Z = cell_centres(grid)
+    if getattr(grid, "nodes", None) is not None:      # mapped grid: the cells' corner means
+        from .mapped import cached_geometry
+        X, Y, Z = cached_geometry(grid)["C"]
+    else:
+        X, Y, Z = cell_centres(grid)
     if grid.nz == 1:
         r2 = (X - x0) ** 2 + (Y - y0) ** 2
         norm = E / ((2.0 * math.pi) ** 1.5 * sr ** 2 * st)

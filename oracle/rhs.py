@@ -10,13 +10,15 @@ variable-major [nv, nz, ny, nx].  The RHS is
 `flags` switches terms off for tests: keys 'inviscid', 'viscous', 'chemistry',
 'laser' (all default True); 'scheme' picks the inviscid reconstruction
 ('weno3z' or 'teno6'); 'nscbc' maps an axis whose bc is 2 to its {side: Side}
-(oracle.nscbc; a missing side is an outflow with the defaults).
+(oracle.nscbc; a missing side is an outflow with the defaults).  A grid with
+node coordinates (oracle.mapped.MappedGridT) runs the mapped form: face fluxes
+through the faces' area vectors, divided by the cell volumes.
 """
 from __future__ import annotations
 
 import torch
 
-from . import chemistry, fluxes, laser as laser_mod, nscbc, thermo, transport
+from . import chemistry, fluxes, laser as laser_mod, mapped, nscbc, thermo, transport
 from .mech import R_U, MechT
 
 
@@ -104,6 +106,20 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
         mup = fluxes.pad(st["mu"], grid)
         lamp = fluxes.pad(st["lam"], grid)
     scheme = (flags or {}).get("scheme", "weno3z")
+    if getattr(grid, "nodes", None) is not None:
+        geo = mapped.cached_geometry(grid)
+        Vp = fluxes.pad(geo["V"], grid)
+        Mp = fluxes.pad(geo["M"], grid)
+        for d in range(3):
+            if _flag(flags, "inviscid"):
+                Fa = mapped.inviscid_flux(Up, velp, pp, cp, Vp, geo["S"][d], grid, d, ns, scheme)
+                out = out - mapped.divergence(Fa, grid, d, geo["V"])
+            if _flag(flags, "viscous"):
+                Fd = mapped.diffusive_flux(velp, Tp, Xp, Yp, Dcp, hp, mup, lamp, Mp, geo["S"][d], grid, d, ns)
+                out = out + mapped.divergence(Fd, grid, d, geo["V"])
+        if return_state:
+            return out, T, st
+        return out, T
     for d in range(3):
         if _flag(flags, "inviscid"):
             Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns, scheme)

@@ -23,7 +23,7 @@ from __future__ import annotations
 
 import torch
 
-from . import chemistry, rhs as rhs_mod
+from . import chemistry, mapped, rhs as rhs_mod
 from .rhs import _flag
 
 
@@ -35,16 +35,22 @@ def ssp_rk3(L, U, t: float, dt: float):
 
 
 def rate_limits(mech, grid, U, T0, flags=None):
-    """Per-grid maxima (acoustic rate, diffusive coefficient, chemical rate)."""
+    """Per-grid maxima (acoustic rate, diffusive coefficient, chemical rate).  On a
+    mapped grid the acoustic rate is sum_e (|u . grad xi_e| + c |grad xi_e|) per cell
+    and the diffusive entry is max over cells of the coefficient times
+    max_e |grad xi_e|^2 (so the limit is 0.25 / that)."""
     st = rhs_mod.cell_state(mech, U, T0)
-    ac = torch.zeros_like(st["T"])
-    for d in range(3):
-        if grid.n[d] > 1:
-            ac = ac + (st["vel"][d].abs() + st["c"]) / grid.h[d]
     nu = st["mu"] / st["rho"]
     alpha = st["lam"] / (st["rho"] * st["cp"])
     dmax = torch.maximum(torch.maximum(nu, alpha), st["D"].max(0).values)
     ch = chemistry.chemical_rate(mech, st["rho_s"], st["T"])
+    if getattr(grid, "nodes", None) is not None:
+        ac, g2 = mapped.rate_limits(grid, st)
+        return float(ac.max()), float((dmax * g2).max()), float(ch.max())
+    ac = torch.zeros_like(st["T"])
+    for d in range(3):
+        if grid.n[d] > 1:
+            ac = ac + (st["vel"][d].abs() + st["c"]) / grid.h[d]
     return float(ac.max()), float(dmax.max()), float(ch.max())
 
 
@@ -52,7 +58,10 @@ def time_step(mech, grid, U, T0, t: float, las, cfl: float, flags=None) -> float
     ac, dmax, ch = rate_limits(mech, grid, U, T0, flags)
     dt = cfl / ac if ac > 0.0 else 1.0e300
     active = [grid.h[d] for d in range(3) if grid.n[d] > 1]
-    if _flag(flags, "viscous") and active and dmax > 0.0:
+    if getattr(grid, "nodes", None) is not None:
+        if _flag(flags, "viscous") and active and dmax > 0.0:
+            dt = min(dt, 0.25 / dmax)
+    elif _flag(flags, "viscous") and active and dmax > 0.0:
         hmin = min(active)
         dt = min(dt, 0.25 * hmin * hmin / dmax)
     if _flag(flags, "chemistry") and ch > 0.0:
