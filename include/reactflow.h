@@ -82,7 +82,17 @@ enum rf_flags {           /* term switches for tests (0 = full method) and the s
                              where their smoothness share chi_k >= 1e-7, LLF alpha over the
                              six cells.  Single-grid RHS and RK steps in both precisions;
                              rejected by rf_ensemble_create and the adjoint entry points */
-    RF_FLAGS_ALL = 31
+    RF_MAPPED = 32,       /* curvilinear grid given by its node coordinates (rf_set_nodes; Methods,
+                             Numerical method: the equations mapped onto a uniform computational
+                             grid, U~ = U / J, F~ = (xi_x F + xi_y G + xi_z H) / J).  Face metrics
+                             are the faces' area vectors (the six of a cell sum to zero, so a
+                             uniform flow stays uniform), frozen over each face's stencil;
+                             volumes, cell metrics and centres from the nodes.  dx, dy, dz of
+                             the grid descriptor are then unused (they must still be > 0).
+                             Single-grid RHS and RK steps in both precisions and with either
+                             scheme (global-memory sweeps); rejected with NSCBC axes and by
+                             rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
+    RF_FLAGS_ALL = 63
 };
 
 /* Mechanism description (host arrays, copied by rf_init_mechanism).
@@ -213,6 +223,20 @@ int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U
  *                  kernel launch of this context (read with rf_profile_read); 0: off
  * Errors: RF_EINVAL for an unknown key or a value out of range. */
 int rf_set_option(rf_ctx *c, const char *key, double value);
+
+/* Node (cell corner) coordinates of an RF_MAPPED context: device array, FP64,
+ * [3][nz+1][ny+1][nx+1] (x, y, z of node (i, j, k) at ((k (ny+1) + j)(nx+1) + i) within
+ * each component; a two-dimensional grid, nz = 1, gives its two node planes, one
+ * cell deep).  Cell (i, j, k) has the corners (i..i+1, j..j+1, k..k+1), ordered so
+ * that the cell's volume is positive.  Computes the face area vectors, cell volumes,
+ * metrics (inverse of the mean edge Jacobian) and centres into the context
+ * (synchronous on s); the nodes are not kept.  Periodic axes connect cells by index;
+ * each cell's faces take its own nodes, so a mapping that is not periodic stays
+ * freestream-preserving, and one that is translation-periodic is also conservative.
+ * Must be called before rf_rhs / rf_rk_step / rf_rk_step_host / rf_diagnostics.
+ * Errors: RF_EINVAL (null argument, context without RF_MAPPED, a cell with a
+ * non-positive volume or a left-handed metric), RF_ECUDA. */
+int rf_set_nodes(rf_ctx *c, const double *nodes, rf_stream s);
 
 /* One end of an NSCBC axis (paper: Application examples - the diffusion flame's left
  * and right boundaries and the combustor's injector inlet and nozzle outlet use the

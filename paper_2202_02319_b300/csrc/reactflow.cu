@@ -156,6 +156,13 @@ struct rf_ctx {
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
     // characteristic boundaries of the axes whose bc is RF_BC_NSCBC (rf_set_nscbc)
     NscbcAxis nscbc[3];
+    // mapped grids (RF_MAPPED): face area vectors, cell metric, volume, 1/volume (bulk
+    // type) and cell centres (FP64), filled by rf_set_nodes
+    int nodes_set = 0;
+    void *geo = nullptr;
+    void *gS[3] = {nullptr, nullptr, nullptr};
+    void *gM = nullptr, *giV = nullptr;
+    double *gV = nullptr, *gC = nullptr;
 };
 
 // record a start event before and a stop event after one launch of class k
@@ -405,7 +412,7 @@ extern "C" void rf_free_mechanism(rf_mech *m) {
 
 static void free_ctx_buffers(rf_ctx *c) {
     void *ptrs[] = {c->Q, c->rhs, c->U32, c->U1, c->U2, c->clock, c->rates, c->status, c->bad_cell, c->diag, c->adj,
-                    c->hU, c->hT};
+                    c->hU, c->hT, c->geo};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->hev)
@@ -432,6 +439,32 @@ extern "C" size_t rf_ctx_workspace_bytes(const rf_ctx *c) { return c ? c->bytes 
 
 static int prepare_ctx(rf_ctx *c);
 
+// mapped-grid workspace: face area vectors of the three axes, cell metric, volume and
+// its reciprocal in the bulk type, cell centres and a bad-cell counter in FP64 / u64
+static size_t geo_faces(const rf_grid_desc &g, int a) {
+    return a == 0 ? (size_t)(g.nx + 1) * g.ny * g.nz : (a == 1 ? (size_t)g.nx * (g.ny + 1) * g.nz : (size_t)g.nx * g.ny * (g.nz + 1));
+}
+static size_t geo_bytes(const rf_grid_desc &g, size_t rsize) {
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t r = 3 * (geo_faces(g, 0) + geo_faces(g, 1) + geo_faces(g, 2)) + 10 * n;
+    return ((r * rsize + 15) / 16) * 16 + 4 * n * sizeof(double) + 16;
+}
+static void geo_layout(rf_ctx *c) {
+    const size_t n = (size_t)c->n;
+    char *p = (char *)c->geo;
+    for (int a = 0; a < 3; ++a) {
+        c->gS[a] = p;
+        p += 3 * geo_faces(c->g, a) * c->rsize;
+    }
+    c->gM = p;
+    p += 9 * n * c->rsize;
+    c->giV = p;
+    p += n * c->rsize;
+    p = (char *)c->geo + ((size_t)(p - (char *)c->geo + 15) / 16) * 16;
+    c->gV = (double *)p;
+    c->gC = c->gV + n;                         // then 3n centres and the bad-cell counter
+}
+
 extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precision, uint32_t flags, rf_ctx **out) {
     if (!m || !g || !out) return fail(RF_EINVAL, "rf_create_ctx: null argument");
     *out = nullptr;
@@ -446,6 +479,8 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_create_ctx: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
+    if ((flags & RF_MAPPED) && (g->bc[0] == RF_BC_NSCBC || g->bc[1] == RF_BC_NSCBC || g->bc[2] == RF_BC_NSCBC))
+        return fail(RF_EINVAL, "rf_create_ctx: NSCBC axes are built for Cartesian grids, not RF_MAPPED ones");
     int mslot = 0;
     {
         int rc = mech_slot(m, &mslot);
@@ -480,6 +515,7 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
         {(void **)&c->rates, 4 * sizeof(unsigned long long)},
         {(void **)&c->status, sizeof(int) * 2},
         {(void **)&c->bad_cell, sizeof(long long)},
+        {&c->geo, (flags & RF_MAPPED) ? geo_bytes(*g, c->rsize) : 0},
     };
     for (auto &a : allocs) {
         if (!a.bytes) continue;
@@ -498,6 +534,7 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
         delete c;
         return fail(RF_ENOMEM, "rf_create_ctx: diagnostics buffer: %s", cudaGetErrorString(e));
     }
+    if (c->geo) geo_layout(c);
     cudaMemset(c->status, 0, sizeof(int) * 2);
     cudaMemset(c->bad_cell, 0xff, sizeof(long long));
     cudaMemset(c->clock, 0, 8 * sizeof(double));
@@ -542,6 +579,14 @@ static Member base_member(rf_ctx *c) {
     m.flags = (int)c->flags;
     m.c_lo = 0;
     m.c_hi = c->n;
+    if (c->flags & RF_MAPPED) {
+        m.mapped = 1;
+        for (int a = 0; a < 3; ++a) m.gS[a] = c->gS[a];
+        m.gM = c->gM;
+        m.gV = c->gV;
+        m.giV = c->giV;
+        m.gC = c->gC;
+    }
     return m;
 }
 
@@ -626,6 +671,13 @@ struct Path {
     // TENO6 sweeps: thread per face from global memory (six-cell stencils), both precisions
     template <int MODE>
     static int sweep_teno(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
+        return sweep_global<MODE, 1, 0>(c, m, dir, s);
+    }
+
+    // global-memory sweeps (thread per face) of scheme SCHEME on a Cartesian (GEOM 0) or
+    // mapped (GEOM 1) grid, both precisions
+    template <int MODE, int SCHEME, int GEOM>
+    static int sweep_global(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
         if (dir == 0) {
             const int nx = c->g.nx;
@@ -642,16 +694,16 @@ struct Path {
             const int blocks = (nrows + rpb - 1) / rpb;
             const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
             ProfScope ps(c, PROF_SWEEP_X, s);
-            sweep_x_kernel<R, UT, NS, MODE, 1><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+            sweep_x_kernel<R, UT, NS, MODE, SCHEME, GEOM><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
         } else {
             const int nd = dir == 1 ? c->g.ny : c->g.nz;
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             dim3 grid((unsigned)((lines + c->walk_block - 1) / c->walk_block), (unsigned)((nd + c->walk_seg - 1) / c->walk_seg));
             ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
             if (dir == 1)
-                sweep_walk_kernel<R, UT, NS, 1, MODE, 1><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+                sweep_walk_kernel<R, UT, NS, 1, MODE, SCHEME, GEOM><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
             else
-                sweep_walk_kernel<R, UT, NS, 2, MODE, 1><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+                sweep_walk_kernel<R, UT, NS, 2, MODE, SCHEME, GEOM><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
         }
         LAUNCH_CHECK();
         return RF_OK;
@@ -660,6 +712,8 @@ struct Path {
     template <int MODE>
     static int sweep(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
+        if (c->flags & RF_MAPPED)
+            return (c->flags & RF_TENO6) ? sweep_global<MODE, 1, 1>(c, m, dir, s) : sweep_global<MODE, 0, 1>(c, m, dir, s);
         if (c->flags & RF_TENO6) return sweep_teno<MODE>(c, m, dir, s);
         if (dir == 0 && sizeof(R) == 4) {
             // staged x sweep: a row per warp, four rows per block
@@ -773,8 +827,10 @@ struct Path {
         const double a[3] = {0.0, 0.75, 1.0 / 3.0}, b[3] = {1.0, 0.25, 2.0 / 3.0}, cc[3] = {0.0, 1.0, 0.5};
         const double *in[3] = {U, c->U1, c->U2};
         double *outp[3] = {c->U1, c->U2, U};
-        const double hmin = std::min(c->g.nx > 1 ? c->g.dx : 1e300,
-                                     std::min(c->g.ny > 1 ? c->g.dy : 1e300, c->g.nz > 1 ? c->g.dz : 1e300));
+        // a mapped grid's diffusive rate already carries max_e |grad xi_e|^2
+        const double hmin = (c->flags & RF_MAPPED) ? 1.0
+                                                   : std::min(c->g.nx > 1 ? c->g.dx : 1e300,
+                                                              std::min(c->g.ny > 1 ? c->g.dy : 1e300, c->g.nz > 1 ? c->g.dz : 1e300));
         for (int k = 0; k < 3; ++k) {
             m.U = in[k];
             m.Uout = outp[k];
@@ -869,8 +925,15 @@ extern "C" int rf_init_state(rf_ctx *c, const double *prim, double *U, double *T
     DISPATCH(c, init_state(c, prim, U, T, (cudaStream_t)s));
 }
 
+#define NODES_READY(c, where)                                                                     \
+    do {                                                                                          \
+        if (((c)->flags & RF_MAPPED) && !(c)->nodes_set)                                          \
+            return fail(RF_EINVAL, "%s: mapped context without node coordinates (rf_set_nodes)", where); \
+    } while (0)
+
 extern "C" int rf_rhs(rf_ctx *c, const double *U, double *T, double t, const rf_laser *L, double *dUdt, rf_stream s) {
     if (!c || !U || !T || !dUdt) return fail(RF_EINVAL, "rf_rhs: null argument");
+    NODES_READY(c, "rf_rhs");
     DISPATCH(c, rhs(c, U, T, t, L, dUdt, (cudaStream_t)s));
 }
 
@@ -878,6 +941,7 @@ extern "C" int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double
                           double *dt_dev, rf_stream s) {
     if (!c || !U || !T || !t_dev) return fail(RF_EINVAL, "rf_rk_step: null argument");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_rk_step: need dt_fixed > 0 or cfl > 0");
+    NODES_READY(c, "rf_rk_step");
     DISPATCH(c, rk_step(c, U, T, t_dev, dt_fixed, cfl, L, dt_dev, (cudaStream_t)s));
 }
 
@@ -891,6 +955,7 @@ extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in
                                rf_stream s) {
     if (!c || !U_in || !T_in || !U_out || !t_dev) return fail(RF_EINVAL, "rf_rk_step_host: null argument");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_rk_step_host: need dt_fixed > 0 or cfl > 0");
+    NODES_READY(c, "rf_rk_step_host");
     const long long n = c->n;
     const int nv = c->nv;
     if (!c->hU) {
@@ -931,6 +996,7 @@ extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in
 extern "C" int rf_diagnostics(rf_ctx *c, const double *U, double *T, rf_diag *out, rf_stream s) {
     if (!c || !U || !T || !out) return fail(RF_EINVAL, "rf_diagnostics: null argument");
     if (c->nv + 2 > 32) return fail(RF_EINVAL, "rf_diagnostics: too many variables");
+    NODES_READY(c, "rf_diagnostics");
     DISPATCH(c, diagnostics(c, U, T, out, (cudaStream_t)s));
 }
 
@@ -957,6 +1023,33 @@ extern "C" int rf_set_option(rf_ctx *c, const char *key, double value) {
         return fail(RF_EINVAL, "rf_set_option: unknown key '%s'", key);
     }
     return RF_OK;
+}
+
+template <typename R>
+static int set_nodes_impl(rf_ctx *c, const double *nodes, cudaStream_t s) {
+    const Nodes N{nodes, c->g.nx, c->g.ny, c->g.nz, (long long)(c->g.nx + 1) * (c->g.ny + 1) * (c->g.nz + 1)};
+    unsigned long long *bad = (unsigned long long *)(c->gC + 3 * c->n);
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+    const long long nf0 = (long long)geo_faces(c->g, 0), nf1 = (long long)geo_faces(c->g, 1), nf2 = (long long)geo_faces(c->g, 2);
+    geometry_face_kernel<R, 0><<<(unsigned)((nf0 + 127) / 128), 128, 0, s>>>(N, (R *)c->gS[0]);
+    geometry_face_kernel<R, 1><<<(unsigned)((nf1 + 127) / 128), 128, 0, s>>>(N, (R *)c->gS[1]);
+    geometry_face_kernel<R, 2><<<(unsigned)((nf2 + 127) / 128), 128, 0, s>>>(N, (R *)c->gS[2]);
+    geometry_cell_kernel<R><<<(unsigned)((c->n + 127) / 128), 128, 0, s>>>(N, (R *)c->gM, c->gV, (R *)c->giV, c->gC, bad);
+    LAUNCH_CHECK();
+    unsigned long long nbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&nbad, bad, sizeof nbad, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (nbad) return fail(RF_EINVAL, "rf_set_nodes: %llu cells with a non-positive volume or a left-handed metric", nbad);
+    c->nodes_set = 1;
+    return RF_OK;
+}
+
+extern "C" int rf_set_nodes(rf_ctx *c, const double *nodes, rf_stream s) {
+    if (!c || !nodes) return fail(RF_EINVAL, "rf_set_nodes: null argument");
+    if (!(c->flags & RF_MAPPED)) return fail(RF_EINVAL, "rf_set_nodes: the context was not created with RF_MAPPED");
+    c->nodes_set = 0;
+    return c->precision == RF_FP64 ? set_nodes_impl<double>(c, nodes, (cudaStream_t)s)
+                                   : set_nodes_impl<float>(c, nodes, (cudaStream_t)s);
 }
 
 extern "C" int rf_set_nscbc(rf_ctx *c, int axis, int side, const rf_nscbc *b) {
@@ -1265,6 +1358,10 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d has a null context or buffer", i);
         }
+        if (c->flags & RF_MAPPED) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d is a mapped grid; batched ensembles run Cartesian grids", i);
+        }
         if (c->g.bc[0] == RF_BC_NSCBC || c->g.bc[1] == RF_BC_NSCBC || c->g.bc[2] == RF_BC_NSCBC) {
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d has an NSCBC axis; batched ensembles run periodic and zero-gradient axes", i);
@@ -1505,6 +1602,7 @@ struct AdjWs {
 
 static int adj_ws(rf_ctx *c, AdjWs &w) {
     if (c->flags & RF_TENO6) return fail(RF_EINVAL, "the discrete adjoint is built for WENO3-Z, not TENO6");
+    if (c->flags & RF_MAPPED) return fail(RF_EINVAL, "the discrete adjoint is built for Cartesian grids, not RF_MAPPED ones");
     for (int a = 0; a < 3; ++a)
         if (c->g.bc[a] == RF_BC_NSCBC) return fail(RF_EINVAL, "the discrete adjoint is built for periodic and zero-gradient axes, not NSCBC (axis %d)", a);
     if (c->mech->npress > 0) return fail(RF_EINVAL, "the discrete adjoint is built for elementary reactions (the mechanism has %d pressure-dependent ones)", c->mech->npress);
@@ -1805,6 +1903,7 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
     }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_rhs_noalloc: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_rhs_noalloc: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
+    if (flags & RF_MAPPED) return fail(RF_EINVAL, "rf_rhs_noalloc: RF_MAPPED needs a context (rf_set_nodes)");
     const long long n = (long long)g->nx * g->ny * g->nz;
     const int ns = m->ns, nv = ns + 4, nq = Q_X0 + 3 * ns;
     const size_t rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);

@@ -110,6 +110,13 @@ struct Member {
     double t_host;
     int xW, xrpb;                // x sweep row chunk width and rows per block (ensemble launches)
     long long c_lo, c_hi;        // cells [c_lo, c_hi) of a cell-state launch
+    // mapped grids (null on Cartesian ones): face area vectors per axis [3][faces of
+    // the axis], cell metric d xi_e / d x_k [9][n] and 1/volume [n] (all of type R),
+    // cell volume [n] and centres [3][n] (FP64)
+    int mapped;
+    const void *gS[3];
+    const void *gM, *giV;
+    const double *gV, *gC;
 };
 
 // Q field order (each field n values of type R).

@@ -625,10 +625,18 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             const int k = (int)(cell / nxy);
             const long long rem = cell - (long long)k * nxy;
             const int j = (int)(rem / m.nx), i = (int)(rem - (long long)j * m.nx);
-            // cell indices are below 2^24, so they convert exactly through FP32
-            const double dx = fma(f2d((float)i), m.h[0], s_laser[2]);
-            const double dy = fma(f2d((float)j), m.h[1], s_laser[3]);
-            const double dz = m.nz > 1 ? fma(f2d((float)k), m.h[2], s_laser[4]) : 0.0;
+            // cell indices are below 2^24, so they convert exactly through FP32; a mapped
+            // grid takes the stored cell centre
+            double dx, dy, dz;
+            if (m.mapped) {
+                dx = m.gC[cell] - m.las[1];
+                dy = m.gC[m.n + cell] - m.las[2];
+                dz = m.nz > 1 ? m.gC[2 * m.n + cell] - m.las[3] : 0.0;
+            } else {
+                dx = fma(f2d((float)i), m.h[0], s_laser[2]);
+                dy = fma(f2d((float)j), m.h[1], s_laser[3]);
+                dz = m.nz > 1 ? fma(f2d((float)k), m.h[2], s_laser[4]) : 0.0;
+            }
             if (sizeof(R) == 8) {
                 double r2 = fma(dx, dx, dy * dy);
                 if (m.nz > 1) r2 = fma(dz, dz, r2);
@@ -646,10 +654,26 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
             for (int v2 = 0; v2 < NV; ++v2) m.U32[v2 * n + cell] = d2f(U[v2 * n + cell]);
         }
         if (m.want_rates) {
-            R ac = 0;
-            if (m.nx > 1) ac += (fabs(ub) + c) * narrow<R>(m.invh[0]);
-            if (m.ny > 1) ac += (fabs(vb) + c) * narrow<R>(m.invh[1]);
-            if (m.nz > 1) ac += (fabs(wb) + c) * narrow<R>(m.invh[2]);
+            R ac = 0, g2 = 1;
+            if (m.mapped) {
+                // sum_e |u . grad xi_e| + c |grad xi_e|; the diffusive coefficient is scaled
+                // by max_e |grad xi_e|^2 (the step's rule then takes unit spacing)
+                const R *__restrict__ gM = (const R *)m.gM;
+                const int ne[3] = {m.nx, m.ny, m.nz};
+                g2 = 0;
+#pragma unroll
+                for (int e = 0; e < 3; ++e) {
+                    if (ne[e] <= 1) continue;
+                    const R a0 = gM[(3 * e) * n + cell], a1 = gM[(3 * e + 1) * n + cell], a2 = gM[(3 * e + 2) * n + cell];
+                    const R m2 = a0 * a0 + a1 * a1 + a2 * a2;
+                    ac += fabs(a0 * ub + a1 * vb + a2 * wb) + c * sqrt(m2);
+                    g2 = m2 > g2 ? m2 : g2;
+                }
+            } else {
+                if (m.nx > 1) ac += (fabs(ub) + c) * narrow<R>(m.invh[0]);
+                if (m.ny > 1) ac += (fabs(vb) + c) * narrow<R>(m.invh[1]);
+                if (m.nz > 1) ac += (fabs(wb) + c) * narrow<R>(m.invh[2]);
+            }
             r_ac = ac;
             if (!(m.flags & F_NO_VISCOUS)) {
                 const R rhob = narrow<R>(rho);
@@ -657,6 +681,7 @@ __device__ __forceinline__ void cell_state_block(const MechDev &M, const Member 
                 const R al = lam / (rhob * cpb);
                 R d = nu > al ? nu : al;
                 r_df = Dmax > d ? Dmax : d;
+                if (m.mapped) r_df *= g2;
             }
         }
     }
@@ -1166,6 +1191,232 @@ __device__ __forceinline__ void face_flux(const Member &m, const UT *__restrict_
     face_flux_core<R, NS, DIR>(m, st, G);
 }
 
+// ----------------------------------------------------------------------------- mapped grids
+
+// Mapped (curvilinear) grids (Methods, Numerical method: the equations mapped onto a
+// uniform computational grid, U~ = U / J, F~ = (xi_x F + xi_y G + xi_z H) / J, the
+// Cartesian scheme applied to the mapped fluxes).  The metric of a face is its area
+// vector S (from its corners; the six of a cell sum to zero), frozen over the face's
+// stencil: contravariant velocity theta = S . u, LLF speed max |theta| + c |S|,
+// f+- = (theta U + p (0, S, theta) +- alpha U) / 2 reconstructed as on a Cartesian grid,
+// the WENO3-Z eps with h = (V_L + V_R) / (2 |S|).  A uniform flow therefore gives every
+// face exactly S . F and stays uniform.  Diffusive fluxes take physical gradients
+// sum_e (d / d xi_e) grad xi_e with the mean of the two cells' metrics, dotted with S.
+// Cells divide the flux difference by their volume.
+
+// Index of face f (between cells f-1 and f along DIR) of the line through cc.
+template <int DIR>
+__device__ __forceinline__ long long face_index(const Member &m, const int (&cc)[3]) {
+    if (DIR == 0) return (long long)cc[0] + (long long)(m.nx + 1) * (cc[1] + (long long)m.ny * cc[2]);
+    if (DIR == 1) return (long long)cc[0] + (long long)m.nx * (cc[1] + (long long)(m.ny + 1) * cc[2]);
+    return (long long)cc[0] + (long long)m.nx * (cc[1] + (long long)m.ny * cc[2]);
+}
+template <int DIR>
+__device__ __forceinline__ long long face_count(const Member &m) {
+    return DIR == 0 ? (long long)(m.nx + 1) * m.ny * m.nz
+                    : (DIR == 1 ? (long long)m.nx * (m.ny + 1) * m.nz : (long long)m.nx * m.ny * (m.nz + 1));
+}
+
+// Inviscid part through a mapped face (four-cell stencil, WENO3-Z).
+template <typename R, int NS, int DIR, class ST>
+__device__ __forceinline__ void face_invisc_mapped(const Member &m, const ST &st, const R (&S)[3], R e2, R (&G)[NS + 4],
+                                                   R &rhoL, R &rhoR) {
+    constexpr int NV = NS + 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    rhoL = 0;
+    rhoR = 0;
+    if (m.flags & F_NO_INVISCID) return;
+    const R Sm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    R th[4], hp[4];
+    R alpha = 0;
+#pragma unroll
+    for (int o = 0; o < 4; ++o) {
+        th[o] = S[0] * st.q(Q_U, o) + S[1] * st.q(Q_U + 1, o) + S[2] * st.q(Q_U + 2, o);
+        hp[o] = R(0.5) * st.q(Q_P, o);
+        const R lam = fabs(th[o]) + st.q(Q_C, o) * Sm;
+        alpha = lam > alpha ? lam : alpha;
+    }
+    const R ha = R(0.5) * alpha;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        R fp[4], fm[4];
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+            const R Uv = st.u(v, o);
+            if (v < NS) {
+                if (o == 1) rhoL += Uv;
+                if (o == 2) rhoR += Uv;
+            }
+            R extra = 0;
+            if (v >= NS && v < NS + 3) extra = hp[o] * S[v - NS];
+            if (v == NS + 3) extra = hp[o] * th[o];
+            const R h = R(0.5) * th[o];
+            fp[o] = fma(h + ha, Uv, extra);
+            fm[o] = fma(h - ha, Uv, extra);
+        }
+        G[v] = -(weno3z<R>(fp[0], fp[1], fp[2], e2) + weno3z<R>(fm[3], fm[2], fm[1], e2));
+    }
+}
+
+// Inviscid part through a mapped face with TENO6 (six-cell stencil, L = 2, R = 3).
+template <typename R, int NS, int DIR, class ST>
+__device__ __forceinline__ void face_invisc_teno_mapped(const Member &m, const ST &st, const R (&S)[3], R (&G)[NS + 4],
+                                                        R &rhoL, R &rhoR) {
+    constexpr int NV = NS + 4;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    rhoL = 0;
+    rhoR = 0;
+    if (m.flags & F_NO_INVISCID) return;
+    const R Sm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+    R th[6], hp[6];
+    R alpha = 0;
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+        th[o] = S[0] * st.q(Q_U, o) + S[1] * st.q(Q_U + 1, o) + S[2] * st.q(Q_U + 2, o);
+        hp[o] = R(0.5) * st.q(Q_P, o);
+        const R lam = fabs(th[o]) + st.q(Q_C, o) * Sm;
+        alpha = lam > alpha ? lam : alpha;
+    }
+    const R ha = R(0.5) * alpha;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        R fp[6], fm[6];
+#pragma unroll
+        for (int o = 0; o < 6; ++o) {
+            const R Uv = st.u(v, o);
+            if (v < NS) {
+                if (o == 2) rhoL += Uv;
+                if (o == 3) rhoR += Uv;
+            }
+            R extra = 0;
+            if (v >= NS && v < NS + 3) extra = hp[o] * S[v - NS];
+            if (v == NS + 3) extra = hp[o] * th[o];
+            const R h = R(0.5) * th[o];
+            fp[o] = fma(h + ha, Uv, extra);
+            fm[o] = fma(h - ha, Uv, extra);
+        }
+        G[v] = -(teno6<R>(fp[0], fp[1], fp[2], fp[3], fp[4], fp[5]) + teno6<R>(fm[5], fm[4], fm[3], fm[2], fm[1], fm[0]));
+    }
+}
+
+// Viscous part through a mapped face, added to G (the four-cell view: L = 1, R = 2);
+// Mf the face metric (d xi_e / d x_k at 3 e + k).
+template <typename R, int NS, int DIR, class ST>
+__device__ __forceinline__ void face_visc_mapped(const Member &m, const ST &st, const R (&S)[3], const R (&Mf)[9],
+                                                 R (&G)[NS + 4], R rhoL, R rhoR, bool have_rho) {
+    if (m.flags & F_NO_VISCOUS) return;
+    if (!have_rho) {
+        rhoL = 0;
+        rhoR = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            rhoL += st.u(s, 1);
+            rhoR += st.u(s, 2);
+        }
+    }
+    // d f / d xi_e at the face: two-point along DIR, mean of the two cells' central
+    // differences along the other axes; physical gradient through Mf
+    auto dxi = [&](int f, int e) -> R {
+        if (e == DIR) return st.q(f, 2) - st.q(f, 1);
+        return R(0.25) * ((st.qt(f, 1, e, true) - st.qt(f, 1, e, false)) + (st.qt(f, 2, e, true) - st.qt(f, 2, e, false)));
+    };
+    auto grad = [&](int f, R (&g)[3]) {
+        const R d0 = dxi(f, 0), d1 = dxi(f, 1), d2 = dxi(f, 2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) g[k] = d0 * Mf[k] + d1 * Mf[3 + k] + d2 * Mf[6 + k];
+    };
+    const R mu = R(0.5) * (st.q(Q_MU, 1) + st.q(Q_MU, 2));
+    const R lam = R(0.5) * (st.q(Q_LAM, 1) + st.q(Q_LAM, 2));
+    R gu[3][3];                                  // gu[l][k] = d u_l / d x_k
+#pragma unroll
+    for (int l = 0; l < 3; ++l) grad(Q_U + l, gu[l]);
+    const R div = gu[0][0] + gu[1][1] + gu[2][2];
+    R uf[3];
+#pragma unroll
+    for (int l = 0; l < 3; ++l) uf[l] = R(0.5) * (st.q(Q_U + l, 1) + st.q(Q_U + l, 2));
+    // tau . S (momentum) and (tau . u) . S (work)
+    R tS[3], work = 0;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+        R a = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            R t = mu * (gu[l][k] + gu[k][l]);
+            if (k == l) t -= R(2.0 / 3.0) * mu * div;
+            a = fma(S[k], t, a);
+        }
+        tS[l] = a;
+        work = fma(a, uf[l], work);
+    }
+    // species diffusion: J_s = -Dc_s grad X_s + Y_s sum_k Dc_k grad X_k; first pass the sum
+    R corr[3] = {0, 0, 0};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        R g[3];
+        grad(QL<NS>::X + s, g);
+        const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
+#pragma unroll
+        for (int k = 0; k < 3; ++k) corr[k] = fma(Dcf, g[k], corr[k]);
+    }
+    const R corrS = corr[0] * S[0] + corr[1] * S[1] + corr[2] * S[2];
+    const R irL = rcp_face(rhoL), irR = rcp_face(rhoR);
+    R qhS = 0;                                   // sum_s (J_s . S) h_s
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        R g[3];
+        grad(QL<NS>::X + s, g);
+        const R Dcf = R(0.5) * (st.q(QL<NS>::DC + s, 1) + st.q(QL<NS>::DC + s, 2));
+        const R Yf = R(0.5) * (st.u(s, 1) * irL + st.u(s, 2) * irR);
+        const R JS = fma(Yf, corrS, -Dcf * (g[0] * S[0] + g[1] * S[1] + g[2] * S[2]));
+        const R hf = R(0.5) * (st.q(QL<NS>::H + s, 1) + st.q(QL<NS>::H + s, 2));
+        qhS = fma(JS, hf, qhS);
+        G[s] -= JS;
+    }
+    R gT[3];
+    grad(Q_T, gT);
+    const R qS = fma(-lam, gT[0] * S[0] + gT[1] * S[1] + gT[2] * S[2], qhS);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) G[NS + l] += tS[l];
+    G[NS + 3] += work - qS;
+}
+
+// Face flux through a mapped face from global memory (cc[DIR] = f).
+template <typename R, typename UT, int NS, int DIR, int SCHEME>
+__device__ __forceinline__ void face_flux_mapped(const Member &m, const UT *__restrict__ U, const R *__restrict__ Q,
+                                                 const int (&cc)[3], R (&G)[NS + 4]) {
+    const long long fi = face_index<DIR>(m, cc), nf = face_count<DIR>(m);
+    const R *__restrict__ gS = (const R *)m.gS[DIR];
+    const R S[3] = {gS[fi], gS[nf + fi], gS[2 * nf + fi]};
+    const R *__restrict__ gM = (const R *)m.gM;
+    const double *__restrict__ gV = m.gV;
+    R rhoL, rhoR;
+    long long iL, iR;
+    if (SCHEME == 1) {
+        const GlobalStencil6<R, UT, DIR> st(m, U, Q, cc);
+        face_invisc_teno_mapped<R, NS, DIR>(m, st, S, G, rhoL, rhoR);
+        iL = st.id[2];
+        iR = st.id[3];
+        R Mf[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Mf[q] = R(0.5) * (gM[q * m.n + iL] + gM[q * m.n + iR]);
+        const InnerFour<GlobalStencil6<R, UT, DIR>> in{st};
+        face_visc_mapped<R, NS, DIR>(m, in, S, Mf, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
+    } else {
+        const GlobalStencil<R, UT, DIR> st(m, U, Q, cc);
+        iL = st.id[1];
+        iR = st.id[2];
+        const R Sm = sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+        const R hf = narrow<R>(0.5 * (gV[iL] + gV[iR])) / Sm;
+        face_invisc_mapped<R, NS, DIR>(m, st, S, hf * hf * R(1.0 / 3.0), G, rhoL, rhoR);
+        R Mf[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Mf[q] = R(0.5) * (gM[q * m.n + iL] + gM[q * m.n + iR]);
+        face_visc_mapped<R, NS, DIR>(m, st, S, Mf, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
+    }
+}
+
 // Stage value of one conserved variable, U_out = a U^n + b (U^(k) + dt L), in FP64.
 // FP64 bulk: as written.  FP32 bulk: L carries FP32 precision, so the increment
 // b dt L is formed in FP32 (and widened exactly) and joined to a U^n + b U^(k) by two
@@ -1218,7 +1469,7 @@ __device__ __forceinline__ void cell_update(const Member &m, long long cell, con
 
 // x sweep: each block row group processes its rows in chunks of W faces; face
 // f = c W + lx goes to slot lx+1, slot 0 carries the previous chunk's last face.
-template <typename R, typename UT, int NS, int MODE, int SCHEME = 0>
+template <typename R, typename UT, int NS, int MODE, int SCHEME = 0, int GEOM = 0>
 __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m, int blk, int W, int rpb,
                                               unsigned char *smem_raw) {
     constexpr int NV = NS + 4;
@@ -1239,10 +1490,12 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
     auto slot = [&](int v, int s) -> R & { return sG[((size_t)v * rpb + r) * (W + 1) + s]; };
     for (int c = 0; c < nchunks; ++c) {
         const int f = c * W + lx;
-        if (active && (f < nx || (f == nx && !periodic))) {
+        // a mapped periodic row computes face nx too (its area vector is its own)
+        if (active && (f < nx || (f == nx && (!periodic || GEOM)))) {
             R G[NV];
             const int cc[3] = {f, j, k};
-            if (SCHEME == 1) face_flux_teno<R, UT, NS, 0>(m, U, Q, cc, G);
+            if (GEOM) face_flux_mapped<R, UT, NS, 0, SCHEME>(m, U, Q, cc, G);
+            else if (SCHEME == 1) face_flux_teno<R, UT, NS, 0>(m, U, Q, cc, G);
             else face_flux<R, UT, NS, 0>(m, U, Q, cc, G);
 #pragma unroll
             for (int v = 0; v < NV; ++v) slot(v, lx + 1) = G[v];
@@ -1254,11 +1507,11 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
         __syncthreads();
         if (active && f >= 1 && f <= nx) {
             R dG[NV];
-            const bool wrap = (f == nx && periodic);
+            const bool wrap = (f == nx && periodic && !GEOM);
 #pragma unroll
             for (int v = 0; v < NV; ++v) dG[v] = (wrap ? s0[v * rpb + r] : slot(v, lx + 1)) - slot(v, lx);
             const long long cell = ((long long)k * m.ny + j) * nx + (f - 1);
-            cell_update<R, NS, MODE>(m, cell, dG, ih);
+            cell_update<R, NS, MODE>(m, cell, dG, GEOM ? ((const R *)m.giV)[cell] : ih);
         }
         __syncthreads();
         if (active) {
@@ -1268,17 +1521,17 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
     }
 }
 
-// SCHEME 0: WENO3-Z, 1: TENO6
-template <typename R, typename UT, int NS, int MODE, int SCHEME = 0>
+// SCHEME 0: WENO3-Z, 1: TENO6; GEOM 1: mapped grid
+template <typename R, typename UT, int NS, int MODE, int SCHEME = 0, int GEOM = 0>
 __global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_constant__ Member m,
                                                       int W, int rpb) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_x_block<R, UT, NS, MODE, SCHEME>(M, m, blockIdx.x, W, rpb, smem_raw);
+    sweep_x_block<R, UT, NS, MODE, SCHEME, GEOM>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
 
 // y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
-template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0>
+template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0, int GEOM = 0>
 __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member &m, long long lblk, int sblk, int seg) {
     constexpr int NV = NS + 4;
     const long long line = lblk * blockDim.x + threadIdx.x;
@@ -1303,24 +1556,26 @@ __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member 
     // whichever segment computes it (bitwise independence of the segmentation)
     for (int c = c0 - 1; c < c1; ++c) {
         cc[DIR] = c + 1;
-        if (SCHEME == 1) face_flux_teno<R, UT, NS, DIR>(m, U, Q, cc, Gn);
+        if (GEOM) face_flux_mapped<R, UT, NS, DIR, SCHEME>(m, U, Q, cc, Gn);
+        else if (SCHEME == 1) face_flux_teno<R, UT, NS, DIR>(m, U, Q, cc, Gn);
         else face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
         if (c >= c0) {
             R dG[NV];
 #pragma unroll
             for (int v = 0; v < NV; ++v) dG[v] = Gn[v] - Gp[v];
-            cell_update<R, NS, MODE>(m, cbase + (long long)c * sd, dG, ih);
+            const long long cell = cbase + (long long)c * sd;
+            cell_update<R, NS, MODE>(m, cell, dG, GEOM ? ((const R *)m.giV)[cell] : ih);
         }
 #pragma unroll
         for (int v = 0; v < NV; ++v) Gp[v] = Gn[v];
     }
 }
 
-template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0>
+template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0, int GEOM = 0>
 __global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid_constant__ Member m,
                                                          int seg) {
     const MechDev &M = c_mech[mslot];
-    sweep_walk_block<R, UT, NS, DIR, MODE, SCHEME>(M, m, blockIdx.x, blockIdx.y, seg);
+    sweep_walk_block<R, UT, NS, DIR, MODE, SCHEME, GEOM>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
 // ----------------------------------------------------------------------------- staged y / z sweep (FP32 bulk)
@@ -1917,7 +2172,7 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
     double *sD = sW + NS * B;
     __shared__ double red[NV + 2][64];
     const long long n = m.n, cell = (long long)blockIdx.x * B + tid;
-    const double dV = m.h[0] * m.h[1] * m.h[2];
+    const double dV0 = m.h[0] * m.h[1] * m.h[2];
     double vals[NV + 2];
 #pragma unroll
     for (int v = 0; v < NV + 2; ++v) vals[v] = 0.0;
@@ -1950,6 +2205,7 @@ __global__ void __launch_bounds__(64) diag_kernel(int mslot, const __grid_consta
 #pragma unroll
             for (int s = 0; s < NS; ++s) hrr -= hs[s] * sW[s * B + tid] * M.W[s];
         }
+        const double dV = m.mapped ? m.gV[cell] : dV0;
 #pragma unroll
         for (int v2 = 0; v2 < NV; ++v2) vals[v2] = m.U[v2 * n + cell] * dV;
         vals[NV] = hrr * dV;
@@ -2171,6 +2427,139 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
         const double scheme = wide((G1[v] - G0[v]) * ih);
         rhs[v * n + cell] = narrow<R>(wide(rhs[v * n + cell]) + (out[v] - scheme));
     }
+}
+
+// ----------------------------------------------------------------------------- mapped-grid geometry
+
+// Node (cell corner) coordinates X[3][nz+1][ny+1][nx+1] (FP64) -> the metric terms the
+// mapped sweeps and cell state read.  Face area vector: half the cross product of the
+// face's diagonals, oriented towards increasing index; cell volume: one third of the
+// sum over its faces of the outward area vector dotted with the face centre; cell
+// metric: the inverse of the matrix of dx/dxi_e, each column the mean of the cell's
+// four edges along e; cell centre: the mean of its corners.  Computed in FP64.
+struct Nodes {
+    const double *X;
+    int nx, ny, nz;
+    long long nn;                 // (nx+1)(ny+1)(nz+1)
+    __device__ __forceinline__ void at(int i, int j, int k, double (&p)[3]) const {
+        const long long o = ((long long)k * (ny + 1) + j) * (nx + 1) + i;
+        p[0] = X[o];
+        p[1] = X[nn + o];
+        p[2] = X[2 * nn + o];
+    }
+};
+
+__device__ __forceinline__ void cross3(const double (&a)[3], const double (&b)[3], double (&c)[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// area vector and centre of face f of axis DIR at the other two indices (i, j, k with
+// the DIR entry = f)
+template <int DIR>
+__device__ __forceinline__ void face_geom(const Nodes &N, int i, int j, int k, double (&S)[3], double (&c)[3]) {
+    double p00[3], p11[3], pa[3], pb[3];
+    if (DIR == 0) {
+        N.at(i, j, k, p00); N.at(i, j + 1, k + 1, p11); N.at(i, j, k + 1, pa); N.at(i, j + 1, k, pb);
+    } else if (DIR == 1) {
+        N.at(i, j, k, p00); N.at(i + 1, j, k + 1, p11); N.at(i + 1, j, k, pa); N.at(i, j, k + 1, pb);
+    } else {
+        N.at(i, j, k, p00); N.at(i + 1, j + 1, k, p11); N.at(i, j + 1, k, pa); N.at(i + 1, j, k, pb);
+    }
+    double d1[3], d2[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        d1[q] = p11[q] - p00[q];
+        d2[q] = pa[q] - pb[q];
+        c[q] = 0.25 * (p00[q] + p11[q] + pa[q] + pb[q]);
+    }
+    cross3(d1, d2, S);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[q] *= 0.5;
+}
+
+template <typename R, int DIR>
+__global__ void geometry_face_kernel(const Nodes N, R *__restrict__ S) {
+    const long long nf = DIR == 0 ? (long long)(N.nx + 1) * N.ny * N.nz
+                                  : (DIR == 1 ? (long long)N.nx * (N.ny + 1) * N.nz : (long long)N.nx * N.ny * (N.nz + 1));
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nf) return;
+    const int ax = DIR == 0 ? N.nx + 1 : N.nx, ay = DIR == 1 ? N.ny + 1 : N.ny;
+    const int i = (int)(id % ax);
+    const long long r = id / ax;
+    const int j = (int)(r % ay), k = (int)(r / ay);
+    double Sv[3], c[3];
+    face_geom<DIR>(N, i, j, k, Sv, c);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) S[q * nf + id] = narrow<R>(Sv[q]);
+}
+
+// cell volume, metric and centre; bad (if given) counts cells whose volume or metric
+// determinant is not positive
+template <typename R>
+__global__ void geometry_cell_kernel(const Nodes N, R *__restrict__ Mo, double *__restrict__ Vo, R *__restrict__ iVo,
+                                     double *__restrict__ C, unsigned long long *bad) {
+    const long long n = (long long)N.nx * N.ny * N.nz;
+    const long long id = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= n) return;
+    const int i = (int)(id % N.nx);
+    const long long r = id / N.nx;
+    const int j = (int)(r % N.ny), k = (int)(r / N.ny);
+    double vol = 0.0, S[3], c[3];
+    face_geom<0>(N, i + 1, j, k, S, c);
+    vol += S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    face_geom<0>(N, i, j, k, S, c);
+    vol -= S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    face_geom<1>(N, i, j + 1, k, S, c);
+    vol += S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    face_geom<1>(N, i, j, k, S, c);
+    vol -= S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    face_geom<2>(N, i, j, k + 1, S, c);
+    vol += S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    face_geom<2>(N, i, j, k, S, c);
+    vol -= S[0] * c[0] + S[1] * c[1] + S[2] * c[2];
+    vol *= (1.0 / 3.0);
+    double P[8][3];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) N.at(i + (q & 1), j + ((q >> 1) & 1), k + (q >> 2), P[q]);
+    double A[3][3];                               // A[k][e] = d x_k / d xi_e
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        A[kk][0] = 0.25 * ((P[1][kk] - P[0][kk]) + (P[3][kk] - P[2][kk]) + (P[5][kk] - P[4][kk]) + (P[7][kk] - P[6][kk]));
+        A[kk][1] = 0.25 * ((P[2][kk] - P[0][kk]) + (P[3][kk] - P[1][kk]) + (P[6][kk] - P[4][kk]) + (P[7][kk] - P[5][kk]));
+        A[kk][2] = 0.25 * ((P[4][kk] - P[0][kk]) + (P[5][kk] - P[1][kk]) + (P[6][kk] - P[2][kk]) + (P[7][kk] - P[3][kk]));
+    }
+    // inverse by cofactors: Minv[e][k] = cof(A)[k][e] / det
+    const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+    const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+    const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+    const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+    const double id_ = 1.0 / det;
+    double Mi[3][3];
+    Mi[0][0] = c00 * id_;
+    Mi[1][0] = c01 * id_;
+    Mi[2][0] = c02 * id_;
+    Mi[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id_;
+    Mi[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id_;
+    Mi[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id_;
+    Mi[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id_;
+    Mi[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id_;
+    Mi[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id_;
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) Mo[(3 * e + kk) * n + id] = narrow<R>(Mi[e][kk]);
+    Vo[id] = vol;
+    iVo[id] = narrow<R>(1.0 / vol);
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) sum += P[q][kk];
+        C[kk * n + id] = 0.125 * sum;
+    }
+    if (bad && !(vol > 0.0 && det > 0.0)) atomicAdd(bad, 1ull);
 }
 
 }  // namespace rf

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libr
 
 RF_OK, RF_EINVAL, RF_ENEWTON, RF_ENONFINITE, RF_ERANGE, RF_ECUDA, RF_ETIMEOUT, RF_ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 RF_FP64, RF_MIXED = 0, 1
-RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER, RF_TENO6 = 1, 2, 4, 8, 16
+RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER, RF_TENO6, RF_MAPPED = 1, 2, 4, 8, 16, 32
 RF_BC_PERIODIC, RF_BC_EXTRAPOLATE, RF_BC_NSCBC = 0, 1, 2
 CODE_NAMES = {0: "RF_OK", -1: "RF_EINVAL", -2: "RF_ENEWTON", -3: "RF_ENONFINITE", -4: "RF_ERANGE",
               -5: "RF_ECUDA", -6: "RF_ETIMEOUT", -7: "RF_ENOMEM"}
@@ -71,6 +71,7 @@ _sigs = {
                                        ctypes.POINTER(Laser), _vp, _vp]),
     "rf_set_option": (ctypes.c_int, [_vp, ctypes.c_char_p, ctypes.c_double]),
     "rf_set_nscbc": (ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(NscbcDesc)]),
+    "rf_set_nodes": (ctypes.c_int, [_vp, _vp, _vp]),
     "rf_profile_read": (ctypes.c_int, [_vp, _dp, _ip, ctypes.c_int]),
     "rf_probe_peak": (ctypes.c_int, [ctypes.c_int, _dp, _vp]),
     "rf_probe_math": (ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, ctypes.c_longlong, _vp]),
@@ -244,6 +245,15 @@ def rk_step_host(ctx: Context, U_in, T_in, U_out, T_out, t_dev, dt_fixed: float 
 
 def set_option(ctx: Context, key: str, value: float):
     _check(_lib.rf_set_option(ctx.handle, key.encode(), float(value)), "rf_set_option")
+
+
+def set_nodes(ctx: Context, nodes, stream=None):
+    """Node coordinates of an RF_MAPPED context (rf_set_nodes): a contiguous float64
+    CUDA tensor [3, nz + 1, ny + 1, nx + 1]; synchronous."""
+    g = ctx.grid
+    if tuple(nodes.shape) != (3, g.nz + 1, g.ny + 1, g.nx + 1):
+        raise ValueError(f"nodes must have shape (3, {g.nz + 1}, {g.ny + 1}, {g.nx + 1})")
+    _check(_lib.rf_set_nodes(ctx.handle, _ptr(nodes), _stream(stream)), "rf_set_nodes")
 
 
 def set_nscbc(ctx: Context, axis: int, side: int, p_inf: float = 101325.0, sigma: float = 0.25, eta_u: float = 1.0,

@@ -347,6 +347,8 @@ class Case:
     # eta_Y, length, target}; target None (outflow) or [4 + Ns, plane] (u, v, w, T, Y_s)
     # on the boundary plane, plane index t1 + n_t1 t2 over the two other axes
     nscbc: dict = field(default_factory=dict)
+    # mapped grids: node (cell corner) coordinates [3, nz + 1, ny + 1, nx + 1], else None
+    nodes: Optional[np.ndarray] = None
 
 
 def _centres(n: int, d: float) -> np.ndarray:
@@ -487,6 +489,46 @@ def case_jet_inflow(seed: int = 0, nx: int = 64, ny: int = 48, nz: int = 1, u_je
     sides = {(0, 0): dict(p_inf=P_ATM, target=target.reshape(4 + mech.n_species, nz * ny)),
              (0, 1): dict(p_inf=P_ATM, sigma=0.25, target=None)}
     return Case(f"jet_inflow_{nx}x{ny}x{nz}", mech, grid, prim, Laser(), steps=100, nscbc=sides)
+
+
+def skewed_nodes(N: int, L: float = 10.0, beta: float = 0.2, dz: Optional[float] = None) -> np.ndarray:
+    """The skewed grid of the paper's convergence tests (Solver Performance
+    Analysis, Accuracy): the uniform N x N nodes (xi, eta) of [-L/2, L/2]^2 placed at
+    x = xi (1 + beta sin(2 pi eta / L)), y = eta (1 + beta sin(2 pi xi / L)), one cell
+    deep (z nodes 0 and dz, default L / N).  Shape [3, 2, N + 1, N + 1]."""
+    h = L / N
+    s_ = -L / 2 + np.arange(N + 1) * h
+    E, Xi = np.meshgrid(s_, s_, indexing="ij")
+    x = Xi * (1.0 + beta * np.sin(2 * np.pi * E / L))
+    y = E * (1.0 + beta * np.sin(2 * np.pi * Xi / L))
+    dz = h if dz is None else dz
+    return np.stack([np.stack([x, x]), np.stack([y, y]),
+                     np.stack([np.zeros_like(x), np.full_like(x, dz)])])
+
+
+def wavy_nodes(nx: int, ny: int, nz: int, h: float, amp: float = 0.2) -> np.ndarray:
+    """A translation-periodic curved grid: the uniform nodes of spacing h moved by
+    amp h times products of sines of period (nx, ny, nz) cells in the other two
+    indices, so that every cell is curved and sheared and the grid tiles space
+    periodically.  Shape [3, nz + 1, ny + 1, nx + 1]."""
+    k, j, i = np.meshgrid(np.arange(nz + 1), np.arange(ny + 1), np.arange(nx + 1), indexing="ij")
+    a, b, c = 2 * np.pi * i / nx, 2 * np.pi * j / ny, 2 * np.pi * k / max(nz, 1)
+    X = np.stack([i * h, j * h, k * h]).astype(np.float64)
+    X[0] += amp * h * np.sin(b) * (np.cos(c) if nz > 1 else 1.0)
+    X[1] += amp * h * np.sin(a) * (np.cos(c) if nz > 1 else 1.0)
+    if nz > 1:
+        X[2] += amp * h * np.sin(a) * np.sin(b)
+    return X
+
+
+def case_jet_mapped(seed: int = 0, n: int = 64, amp: float = 0.2, device=None) -> Case:
+    """The jet in a periodic box (case_jet's fields, n^3 cells) on a curved,
+    translation-periodic grid (wavy_nodes, amplitude amp cells): the curvilinear
+    workload."""
+    c = case_jet(seed, n, device=device)
+    c.name = f"jet_mapped_{n}^3"
+    c.nodes = wavy_nodes(n, n, n, c.grid.dx, amp)
+    return c
 
 
 def _torch_gen(seed: int, name: str, device):

@@ -1,5 +1,7 @@
 """Shared helpers of the GPU parity tests: run the CUDA path and the oracle on
 the same seeded inputs and compare."""
+import gc
+
 import numpy as np
 import torch
 
@@ -15,8 +17,14 @@ def prim_tensor(case):
 
 def gpu_setup(case, precision=0, flags=0, options=None):
     from paper_2202_02319_b300 import native as nv
+    gc.collect()            # release the constant-memory slots of mechanisms no longer referenced
     mech = nv.init_mechanism(case.mech)
+    nodes = getattr(case, "nodes", None)
+    if nodes is not None:
+        flags |= nv.RF_MAPPED
     ctx = nv.create_ctx(mech, case.grid, precision, flags)
+    if nodes is not None:
+        nv.set_nodes(ctx, torch.as_tensor(np.ascontiguousarray(nodes), dtype=F64).cuda())
     for k, v in (options or {}).items():
         nv.set_option(ctx, k, v)
     ns = case.mech.n_species
@@ -58,6 +66,9 @@ def nscbc_oracle(case):
 def oracle_setup(case):
     mt = from_synth(case.mech)
     g = grid_from_synth(case.grid)
+    nodes = getattr(case, "nodes", None)
+    if nodes is not None:
+        g = oracle.mapped.MappedGridT(g.nx, g.ny, g.nz, torch.as_tensor(np.asarray(nodes), dtype=F64), g.bc)
     U, T = oracle.rhs.init_state(mt, prim_tensor(case))
     return mt, g, U, T
 
