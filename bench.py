@@ -261,6 +261,9 @@ def run_ours(args):
     # --- characteristic inflow / outflow boundaries: injection case, mixed
     nscbc = run_nscbc_leg(args, dev) if args.nscbc_steps > 0 else None
 
+    # --- curvilinear grid: the jet on a curved periodic grid, mixed and FP64
+    mapd = run_mapped_leg(args, dev) if args.mapped_steps > 0 else None
+
     # --- batched ensemble (64 members of uneven size): members/s per launch mode
     ens = run_ensemble_leg(args, dev) if args.ensemble_members > 0 else None
 
@@ -343,6 +346,7 @@ def run_ours(args):
         "roofline": roofline,
         "teno6": teno,
         "nscbc": nscbc,
+        "mapped": mapd,
         "min_ignition_energy": mie,
         "ensemble": ens,
         "adjoint": adj,
@@ -460,6 +464,53 @@ def run_nscbc_leg(args, dev):
         torch.cuda.empty_cache()
     out["boundary_kernels_ms_per_step"] = round(out["nscbc"]["other_ms_per_step"] - out["zero_gradient"]["other_ms_per_step"], 4)
     out["step_time_ratio"] = round(out["nscbc"]["ms_per_step"] / out["zero_gradient"]["ms_per_step"], 4)
+    return out
+
+
+# ----------------------------------------------------------------------------- mapped-grid leg
+
+def run_mapped_leg(args, dev):
+    """The jet in a box on a curved periodic grid (synth.case_jet_mapped, n^3), mixed
+    and FP64: cell-updates/s with CUDA events on the launching stream, per-kernel
+    times from the library's profile events."""
+    import torch
+    from paper_2202_02319_b300 import native as nv, synth
+    case = synth.case_jet_mapped(0, args.mapped_n)
+    ns = case.mech.n_species
+    ncell = case.grid.ncells
+    mech = nv.init_mechanism(case.mech)
+    prim = torch.as_tensor(case.prim, dtype=torch.float64).reshape(5 + ns, ncell).to(dev)
+    nodes = torch.as_tensor(case.nodes, dtype=torch.float64).to(dev).contiguous()
+    las = case.laser.as_tuple()
+    out = {"grid": [args.mapped_n] * 3, "cells": ncell, "amplitude_cells": 0.2}
+    for name, prec, steps in (("mixed", nv.RF_MIXED, args.mapped_steps), ("fp64", nv.RF_FP64, max(1, args.mapped_steps // 2))):
+        ctx = nv.create_ctx(mech, case.grid, prec, nv.RF_MAPPED)
+        nv.set_nodes(ctx, nodes)
+        U = torch.empty((ns + 4, ncell), dtype=torch.float64, device=dev)
+        T = torch.empty(ncell, dtype=torch.float64, device=dev)
+        nv.init_state(ctx, prim, U, T)
+        t = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(2):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        nv.check(ctx)
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(steps):
+            nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        nv.set_option(ctx, "profile", 1)
+        nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+        prof = nv.profile_read(ctx)
+        nv.set_option(ctx, "profile", 0)
+        nv.check(ctx)
+        out[name] = {"value": ncell * 3 * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+                     "kernels_ms_per_launch": {k: round(v[0] / v[1], 4) for k, v in prof.items() if v[1]}}
+        del ctx, U, T
+        torch.cuda.empty_cache()
     return out
 
 
@@ -698,6 +749,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--teno-steps", type=int, default=4)
+    ap.add_argument("--mapped-steps", type=int, default=4)
+    ap.add_argument("--mapped-n", type=int, default=192)
     ap.add_argument("--nscbc-steps", type=int, default=10)
     ap.add_argument("--nscbc-nx", type=int, default=256)
     ap.add_argument("--nscbc-ny", type=int, default=128)
