@@ -206,8 +206,12 @@ int rf_rk_step(rf_ctx *c, double *U, double *T, double *t_dev, double dt_fixed, 
  * chunks of cells on a copy stream of the context, and the first stage's
  * cell-state kernel of each chunk starts once that chunk has arrived, so that the
  * transfer overlaps computation; the temperature is copied out on the copy stream
- * as soon as the last stage's cell state has written it, during that stage's sweeps
- * (with pinned host memory; pageable memory works but copies synchronously).  t_dev, dt_fixed, cfl, laser, dt_dev as rf_rk_step.
+ * as soon as the last stage's cell state has written it, during that stage's sweeps;
+ * the state is copied out by eight chunks on a second copy stream once the last stage
+ * is done, and s waits for them.  A following call's copy in of chunk q waits only for
+ * this step's last stage and its copy out of chunk q, so the copies out of one step and
+ * in of the next run in both directions at once (with pinned host memory; pageable
+ * memory works but copies synchronously).  t_dev, dt_fixed, cfl, laser, dt_dev as rf_rk_step.
  * Asynchronous on s: the host buffers must stay valid, and U_out unread, until s
  * has completed.  Errors: RF_EINVAL, RF_ENOMEM, RF_ECUDA. */
 int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in, double *U_out, double *T_out, double *t_dev,

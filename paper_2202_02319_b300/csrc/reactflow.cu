@@ -151,6 +151,12 @@ struct rf_ctx {
     // host-buffer step: [0, 8) chunk copies in, [8] queued work before them, [9] the last
     // stage's cell state (T final), [10] T copied out
     cudaEvent_t hev[11] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // host-buffer step, copy out: a second copy stream (so copies out of one step and
+    // in of the next run in both directions at once), [0, 8) chunk copies out done,
+    // [8] the last stage done; out_pending: a step's copies out may still be in flight
+    cudaStream_t copy_out = nullptr;
+    cudaEvent_t oev[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int out_pending = 0;
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
@@ -417,7 +423,10 @@ static void free_ctx_buffers(rf_ctx *c) {
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->hev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->oev)
+        if (e) cudaEventDestroy(e);
     if (c->copy) cudaStreamDestroy(c->copy);
+    if (c->copy_out) cudaStreamDestroy(c->copy_out);
 }
 
 static void clear_profile(rf_ctx *c) {
@@ -965,15 +974,26 @@ extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in
     }
     if (!c->copy) {
         CUDA_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+        CUDA_TRY(cudaStreamCreateWithFlags(&c->copy_out, cudaStreamNonBlocking));
         for (cudaEvent_t &e : c->hev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        for (cudaEvent_t &e : c->oev) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     cudaStream_t st = (cudaStream_t)s;
     const int chunks = (int)std::min<long long>(8, n);
-    // the copy stream follows the work already queued on s (an earlier read of hU / hT)
-    CUDA_TRY(cudaEventRecord(c->hev[8], st));
-    CUDA_TRY(cudaStreamWaitEvent(c->copy, c->hev[8], 0));
+    // The copies in overwrite hU / hT.  The first call's follow the work already queued on
+    // s; a later call's follow the previous step's last stage (its last read of hU / hT on
+    // s) and, chunk by chunk, that step's copy out of the same chunk (the host buffers may
+    // be the same, and hU is that copy's source), so that the copies in of this step run
+    // beside the remaining copies out of the previous one
+    if (c->out_pending) {
+        CUDA_TRY(cudaStreamWaitEvent(c->copy, c->oev[8], 0));
+    } else {
+        CUDA_TRY(cudaEventRecord(c->hev[8], st));
+        CUDA_TRY(cudaStreamWaitEvent(c->copy, c->hev[8], 0));
+    }
     for (int q = 0; q < chunks; ++q) {
         const long long lo = n * q / chunks, hi = n * (q + 1) / chunks;
+        if (c->out_pending) CUDA_TRY(cudaStreamWaitEvent(c->copy, c->oev[q], 0));
         for (int v = 0; v < nv; ++v)
             CUDA_TRY(cudaMemcpyAsync(c->hU + (size_t)v * n + lo, U_in + (size_t)v * n + lo, (size_t)(hi - lo) * sizeof(double),
                                      cudaMemcpyHostToDevice, c->copy));
@@ -988,7 +1008,19 @@ extern "C" int rf_rk_step_host(rf_ctx *c, const double *U_in, const double *T_in
         CUDA_TRY(cudaMemcpyAsync(T_out, c->hT, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, c->copy));
         CUDA_TRY(cudaEventRecord(c->hev[10], c->copy));
     }
-    CUDA_TRY(cudaMemcpyAsync(U_out, c->hU, (size_t)n * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // U out by chunks on the second copy stream once the last stage is done; s waits for
+    // the last chunk, so completion of s covers the copies
+    CUDA_TRY(cudaEventRecord(c->oev[8], st));
+    CUDA_TRY(cudaStreamWaitEvent(c->copy_out, c->oev[8], 0));
+    for (int q = 0; q < chunks; ++q) {
+        const long long lo = n * q / chunks, hi = n * (q + 1) / chunks;
+        for (int v = 0; v < nv; ++v)
+            CUDA_TRY(cudaMemcpyAsync(U_out + (size_t)v * n + lo, c->hU + (size_t)v * n + lo, (size_t)(hi - lo) * sizeof(double),
+                                     cudaMemcpyDeviceToHost, c->copy_out));
+        CUDA_TRY(cudaEventRecord(c->oev[q], c->copy_out));
+    }
+    c->out_pending = 1;
+    CUDA_TRY(cudaStreamWaitEvent(st, c->oev[chunks - 1], 0));
     if (T_out) CUDA_TRY(cudaStreamWaitEvent(st, c->hev[10], 0));
     return RF_OK;
 }

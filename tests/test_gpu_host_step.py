@@ -44,3 +44,27 @@ def test_host_step_equals_device_step(precision, in_place):
     nv.check(ctx)
     if in_place:
         assert torch.equal(T.cpu(), Th)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_back_to_back_host_steps_equal_device_steps(precision):
+    """Five in-place host-buffer steps queued without synchronising (each step's
+    copies in wait, chunk by chunk, for the previous step's copies out of the same
+    buffer) give bitwise the state of five device-buffer steps."""
+    from paper_2202_02319_b300 import native as nv
+    case = _jet()
+    las = laser_tuple(case)
+    mech, ctx, U, T = gpu_setup(case, precision=precision)
+    Uh = U.cpu().pin_memory()
+    Th = T.cpu().pin_memory()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    th = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        nv.rk_step(ctx, U, T, t, 0.0, case.cfl, las, None)
+    for _ in range(5):
+        nv.rk_step_host(ctx, Uh, Th, Uh, Th, th, 0.0, case.cfl, las, None)
+    torch.cuda.synchronize()
+    nv.check(ctx)
+    assert torch.equal(U.cpu(), Uh)
+    assert torch.equal(T.cpu(), Th)
+    assert float(t) == float(th)
