@@ -764,8 +764,15 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=20)
     ap.add_argument("--adjoint-members", type=int, default=1)
     ap.add_argument("--adjoint-ck", type=int, default=0, help="checkpoint interval (0: half the steps)")
+    ap.add_argument("--leg", default=None, choices=["mapped", "nscbc"],
+                    help="run only this leg and print its result (for profiling its kernels)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.leg is not None:
+        import torch
+        dev = torch.device("cuda")
+        leg = run_mapped_leg(args, dev) if args.leg == "mapped" else run_nscbc_leg(args, dev)
+        print(json.dumps({"leg": args.leg, **leg}))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -350,9 +350,11 @@ int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value);
  * mode 0: per-member launch loop (each member's own rf_rk_step launches);
  * mode 1: one launch per phase over all members' work items;
  * mode 2: mode 1 captured once as a CUDA graph of one step, replayed;
- * mode 3: one persistent cooperative launch per RK stage (grid barriers between
- *         the phases, each bounded: a wait that runs out returns RF_ETIMEOUT);
- *         the three launches of a step are issued directly, not captured.
+ * mode 3: per RK stage, the cell state and the x sweep as launches over all members'
+ *         work items, the y and z sweeps in one persistent cooperative launch (a grid
+ *         barrier between them, bounded: a wait that runs out returns RF_ETIMEOUT),
+ *         and (mixed precision) the stage update as a launch over the cells; one
+ *         step is captured as a CUDA graph, as in mode 2, and replayed.
  * Modes 1-3 need every member with nx, ny, nz > 1.  A member whose state fails
  * (Newton, non-finite, range) is frozen at its last good step and the others
  * continue; member_status (host, n ints, may be NULL) receives each member's

@@ -1290,13 +1290,13 @@ struct EnsPath {
             CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
             CUDA_TRY(cudaFuncSetAttribute(ens_walk_kernel<R, UT, NS, 2, MODE_ACCUM>, cudaFuncAttributeMaxDynamicSharedMemorySize, sw));
         }
-        const size_t sm_stage = std::max(std::max(e->smem_cell, e->smem_x), walk_smem<R, NS>());
-        CUDA_TRY(cudaFuncSetAttribute(ens_stage_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_stage));
+        const size_t sm_sweep = walk_smem<R, NS>();
+        CUDA_TRY(cudaFuncSetAttribute(ens_sweep_stage_kernel<R, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sweep));
         int dev = 0, sms = 0, per = 0;
         CUDA_TRY(cudaGetDevice(&dev));
         CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_stage_kernel<R, NS>, 128, sm_stage));
-        if (per < 1) return fail(RF_ECUDA, "ensemble: persistent stage kernel does not fit on an SM");
+        CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, ens_sweep_stage_kernel<R, NS>, 128, sm_sweep));
+        if (per < 1) return fail(RF_ECUDA, "ensemble: persistent sweep kernel does not fit on an SM");
         e->coop_blocks = per * sms;
         return RF_OK;
     }
@@ -1331,24 +1331,42 @@ struct EnsPath {
         return RF_OK;
     }
 
-    // one step as one cooperative launch per RK stage (mode 3)
+    // one step as, per RK stage, work-list launches of the cell state (and, in the first
+    // stage, the time step) and the x sweep, one cooperative launch of the y and z sweeps,
+    // and (FP32 bulk) the stage update (mode 3)
     static int step_persistent(rf_ensemble *e, cudaStream_t s) {
-        const size_t sm_stage = std::max(std::max(e->smem_cell, e->smem_x), walk_smem<R, NS>());
+        const size_t sm_sweep = walk_smem<R, NS>();
+        const int M = e->mslot;
         for (int k = 0; k < 3; ++k) {
+            EnsDev E0 = ens_dev(e, e->nitems[0]);
+            ens_cell_kernel<R, NS><<<e->nitems[0], 128, cell_state_smem<R, NS>(128, k == 0, e->mech->nr), s>>>(M, E0, k);
+            LAUNCH_CHECK();
+            if (k == 0) {
+                ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);
+                LAUNCH_CHECK();
+            }
+            ens_x_kernel<R, UT, NS, MODE_ACCUM><<<e->nitems[1], 128, e->smem_x, s>>>(M, ens_dev(e, e->nitems[1]), k);
+            LAUNCH_CHECK();
             EnsDev E = ens_dev(e, e->coop_blocks);
             cudaLaunchConfig_t cfg;
             std::memset(&cfg, 0, sizeof cfg);
             cfg.gridDim = dim3(e->coop_blocks);
             cfg.blockDim = dim3(128);
-            cfg.dynamicSmemBytes = sm_stage;
+            cfg.dynamicSmemBytes = sm_sweep;
             cfg.stream = s;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeCooperative;
             attr[0].val.cooperative = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            CUDA_TRY(cudaLaunchKernelEx(&cfg, ens_stage_kernel<R, NS>, e->mslot, E, k));
+            CUDA_TRY(cudaLaunchKernelEx(&cfg, ens_sweep_stage_kernel<R, NS>, e->mslot, E, k));
+            if constexpr (sizeof(R) == 4) {
+                ens_final_kernel<R, NS><<<e->nitems[0], 128, 0, s>>>(ens_dev(e, e->nitems[0]), k);
+                LAUNCH_CHECK();
+            }
         }
+        ens_end_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(ens_dev(e, 1));
+        LAUNCH_CHECK();
         return RF_OK;
     }
 };
@@ -1505,7 +1523,9 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
         EnsDev E = ens_dev(e, 1);
         ens_begin_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(E, e->t_dev, cfl, dt_fixed);
         LAUNCH_CHECK();
-        const bool graph = mode == 2;
+        // modes 2 and 3 replay one step captured as a CUDA graph (mode 3's graph holds its
+        // cooperative launches)
+        const bool graph = mode == 2 || mode == 3;
         if (graph && nsteps > 0 && !e->graph[mode]) {
             // captured on the ensemble's own stream: capture records, it does not run anything
             cudaGraph_t g;

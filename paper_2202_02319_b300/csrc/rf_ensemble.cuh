@@ -1,10 +1,11 @@
 // Batched ensembles: many members (grids of uneven size, each with its own laser
 // and workspace) advanced together.  Every phase of an RK stage (cell state, x,
 // y, z sweeps, time step) becomes one launch over a work list of (member, tile)
-// items spanning all members; the "persistent" form runs a whole RK stage in one
-// cooperative launch whose blocks stride over the work lists and meet at grid
-// barriers between phases.  Results of a member are bitwise those of running it
-// alone: every cell sees the same arithmetic whatever block processes it.
+// items spanning all members; the "persistent" form runs the y and z sweeps of a stage
+// in one cooperative launch whose blocks stride over the work lists and meet at a grid
+// barrier between the phases, the other phases as such launches.  Results of a
+// member are bitwise those of running it alone: every cell sees the same arithmetic
+// whatever block processes it.
 #pragma once
 
 #include "rf_kernels.cuh"
@@ -134,6 +135,9 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 5) ens_cell_kernel(i
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok;
+    // after a persistent sweep launch gave up, the stage states of this step were never
+    // written: run nothing (the temperature warm start must not be overwritten)
+    if (*(volatile int *)E.timeout) return;
     ens_cell_phase<R, NS>(M, E, stage, smem_raw, sm, s_ok);
 }
 
@@ -161,6 +165,7 @@ template <typename R, int NS>
 __global__ void __launch_bounds__(128) ens_final_kernel(const __grid_constant__ EnsDev E, int stage) {
     __shared__ Member sm;
     __shared__ int s_ok;
+    if (*(volatile int *)E.timeout) return;     // a persistent sweep launch of this step gave up
     ens_final_phase<R, NS>(E, stage, sm, s_ok);
 }
 
@@ -185,7 +190,7 @@ __global__ void ens_dt_kernel(int mslot, const __grid_constant__ EnsDev E) {
 // Step epilogue: advance the clock of members that did not fail, clear maxima.
 __global__ void ens_end_kernel(const __grid_constant__ EnsDev E) {
     const int mi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (mi >= E.nmembers) return;
+    if (mi >= E.nmembers || *(volatile int *)E.timeout) return;
     const Member &m = E.tab[0][mi];
     if (*m.status == 0) m.clock[0] += m.clock[1];
     m.rates[0] = m.rates[1] = m.rates[2] = 0ull;
@@ -235,42 +240,27 @@ __device__ __forceinline__ bool grid_barrier(const EnsDev &E, int &s_flag) {
     return s_flag != 0;
 }
 
-// One RK stage of every member in one cooperative launch: cell state, (stage 1:
-// time step), x, y and z sweeps, (stage 3: clock advance), separated by grid
-// barriers.  Members must have nx, ny, nz > 1 (the z sweep performs the update:
-// a separate elementwise phase would add a grid barrier and a pass at this
-// launch's occupancy, which the staged walk's shared memory holds at two blocks
-// per SM).
+// The y and z sweeps of one RK stage of every member in one cooperative launch,
+// separated by a grid barrier.  The stage's cell state and x sweep run before it, and
+// in the FP32-bulk path the stage update after it, as work-list launches of their own
+// (the x sweep's blocks fit three to an SM alone, two beside the walk's rings): the cell state is bound by FP64 latency and needs the 24 warps per SM that
+// its own 80-register, 33 KB blocks give, which no launch that also holds the staged
+// sweeps' registers and 75 KB rings can offer (a launch running every phase held the
+// cell state at 8 warps per SM).
 template <typename R, int NS>
-__global__ void __launch_bounds__(128) ens_stage_kernel(int mslot, const __grid_constant__ EnsDev E,
-                                                        int stage) {
+__global__ void __launch_bounds__(128) ens_sweep_stage_kernel(int mslot, const __grid_constant__ EnsDev E,
+                                                              int stage) {
     const MechDev &M = c_mech[mslot];
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
     __shared__ int s_ok, s_flag;
     if (*(volatile int *)E.timeout) return;     // an earlier stage of this step gave up: run nothing
-    ens_cell_phase<R, NS>(M, E, stage, smem_raw, sm, s_ok);
-    if (!grid_barrier(E, s_flag)) return;
-    if (stage == 0) {
-        if (blockIdx.x == 0)
-            for (int mi = threadIdx.x; mi < E.nmembers; mi += blockDim.x) member_dt(M, E.tab[0][mi]);
-        if (!grid_barrier(E, s_flag)) return;
-    }
-    ens_x_phase<R, UT, NS, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok);
-    if (!grid_barrier(E, s_flag)) return;
     ens_walk_phase<R, UT, NS, 1, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok);
     if (!grid_barrier(E, s_flag)) return;
-    ens_walk_phase<R, UT, NS, 2, MODE_STAGE>(M, E, stage, smem_raw, sm, s_ok);
-    if (stage == 2) {
-        if (!grid_barrier(E, s_flag)) return;
-        if (blockIdx.x == 0)
-            for (int mi = threadIdx.x; mi < E.nmembers; mi += blockDim.x) {
-                const Member &m = E.tab[0][mi];
-                if (*m.status == 0) m.clock[0] += m.clock[1];
-                m.rates[0] = m.rates[1] = m.rates[2] = 0ull;
-            }
-    }
+    // FP32 bulk: the z sweep accumulates and an elementwise launch applies the stage (the
+    // stage's FP64 operations would hold this launch's few warps); FP64: fused
+    ens_walk_phase<R, UT, NS, 2, sizeof(R) == 4 ? MODE_ACCUM : MODE_STAGE>(M, E, stage, smem_raw, sm, s_ok);
 }
 
 }  // namespace rf
