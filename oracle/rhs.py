@@ -114,6 +114,8 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
             if _flag(flags, "inviscid"):
                 Fa = mapped.inviscid_flux(Up, velp, pp, cp, Vp, geo["S"][d], grid, d, ns, scheme)
                 out = out - mapped.divergence(Fa, grid, d, geo["V"])
+                if grid.bc[d] == nscbc.BC_NSCBC:
+                    out = nscbc.correct_mapped(mech, grid, geo, st, U, Fa, out, d, (flags or {}).get("nscbc", {}).get(d))
             if _flag(flags, "viscous"):
                 Fd = mapped.diffusive_flux(velp, Tp, Xp, Yp, Dcp, hp, mup, lamp, Mp, geo["S"][d], grid, d, ns)
                 out = out + mapped.divergence(Fd, grid, d, geo["V"])

@@ -394,3 +394,93 @@ def test_supersonic_outflow_gives_the_exact_flux_derivative(mech, direction):
     scale = want.abs().max()
     assert float(((got - want).abs() / scale).max()) < 1e-7
     assert float((R[:, 0, 0, up].abs() / scale).max()) < 1e-13
+
+
+def _mapped_nodes_uniform(nx, ny, nz, dx, dy, dz):
+    i = torch.arange(nx + 1, dtype=torch.float64) * dx
+    j = torch.arange(ny + 1, dtype=torch.float64) * dy
+    k = torch.arange(nz + 1, dtype=torch.float64) * dz
+    Z, Yy, X = torch.meshgrid(k, j, i, indexing="ij")
+    return torch.stack([X, Yy, Z])
+
+
+def test_mapped_uniform_nodes_reproduce_the_cartesian_boundaries(mech):
+    """Characteristic boundaries on a uniform grid given by its nodes (the mapped
+    form: normal from the area vectors, d/dn from |S| / V) give the Cartesian RHS,
+    with an inflow target on one end and a relaxing outflow on the other."""
+    from oracle import mapped
+    m = synth.mechanism_4sp(0)
+    nz, ny, nx = 3, 4, 9
+    dx, dy, dz = 1.1e-4, 0.9e-4, 1.3e-4
+    prim = tensor(random_prim(m, (nz, ny, nx), 8, smooth=True))
+    U, T = rhs.init_state(mech, prim)
+    target = torch.empty((8, nz, ny), dtype=torch.float64)
+    target[0], target[1], target[2], target[3] = 30.0, 5.0, -4.0, 900.0
+    target[4:] = tensor(np.array([0.2, 0.3, 0.1, 0.4]))[:, None, None]
+    sides = {0: nscbc.Side(p_inf=1.0e5, eta_u=0.7, eta_T=0.9, eta_t=0.5, eta_Y=0.8, target=target),
+             1: nscbc.Side(p_inf=1.01e5, sigma=0.3)}
+    flags = {"laser": False, "nscbc": {0: sides}}
+    gc = GridT(nx, ny, nz, dx, dy, dz, (2, 0, 1))
+    gm = mapped.MappedGridT(nx, ny, nz, _mapped_nodes_uniform(nx, ny, nz, dx, dy, dz), (2, 0, 1))
+    rc, _ = rhs.rhs(mech, gc, U, T, flags=flags)
+    rm, _ = rhs.rhs(mech, gm, U, T, flags=flags)
+    num = (rm - rc).reshape(rc.shape[0], -1).abs().amax(1)
+    den = rc.reshape(rc.shape[0], -1).abs().amax(1)
+    assert float((num / den).max()) < 1e-12
+
+
+def test_mapped_boundaries_on_a_rotated_grid_match_the_one_dimensional_ones(mech):
+    """A uniform grid rotated by 30 degrees, characteristic ends on its first axis,
+    data varying along that axis only and the velocity along it: the RHS is the
+    one-dimensional Cartesian RHS with the momentum rotated."""
+    from oracle import mapped
+    m = synth.mechanism_4sp(0)
+    nx, ny, h = 16, 3, 1e-4
+    prim1 = tensor(random_prim(m, (1, 1, nx), 9, smooth=True))
+    prim1[3] = 0.0
+    prim1[4] = 0.0
+    th = np.radians(30.0)
+    cs, sn = float(np.cos(th)), float(np.sin(th))
+    X = _mapped_nodes_uniform(nx, ny, 1, h, h, h)
+    Xr = X.clone()
+    Xr[0] = cs * X[0] - sn * X[1]
+    Xr[1] = sn * X[0] + cs * X[1]
+    prim2 = prim1.expand(prim1.shape[0], 1, ny, nx).clone()
+    prim2[2] = cs * prim1[2]
+    prim2[3] = sn * prim1[2]
+    U1, T1 = rhs.init_state(mech, prim1)
+    U2, T2 = rhs.init_state(mech, prim2)
+    s1 = {0: nscbc.Side(p_inf=1.0e5, sigma=0.4), 1: nscbc.Side(p_inf=1.02e5, sigma=0.2)}
+    fl = dict(NO_SRC, viscous=True, nscbc={0: s1})
+    R1, _ = rhs.rhs(mech, GridT(nx, 1, 1, h, h, h, (2, 0, 0)), U1, T1, flags=fl)
+    R2, _ = rhs.rhs(mech, mapped.MappedGridT(nx, ny, 1, Xr, (2, 0, 0)), U2, T2, flags=fl)
+    want = R1.expand(R1.shape[0], 1, ny, nx).clone()
+    want[4] = cs * R1[4]
+    want[5] = sn * R1[4]
+    scale = R1.reshape(R1.shape[0], -1).abs().amax(1)
+    scale[5] = scale[4]
+    scale[6] = scale[4]
+    err = (R2 - want).reshape(R2.shape[0], -1).abs().amax(1) / scale
+    assert float(err.max()) < 1e-10
+
+
+def test_mapped_uniform_state_at_its_targets_is_at_rest(mech):
+    """A uniform flow on the paper's skewed grid with a characteristic inflow at its
+    targets and an outflow at p_inf on the first axis: the RHS vanishes to rounding."""
+    from oracle import mapped
+    N = 12
+    nodes = tensor(synth.skewed_nodes(N, L=N * 1e-4))
+    Y = np.array([0.1, 0.2, 0.3, 0.4])
+    p0, u0, v0, T0 = 1.0e5, 25.0, 7.0, 450.0
+    U, T = _uniform(mech, (1, N, N), p0, T0, (u0, v0, 0.0), Y)
+    target = torch.empty((8, 1, N), dtype=torch.float64)
+    target[0], target[1], target[2], target[3] = u0, v0, 0.0, T0
+    target[4:] = tensor(Y)[:, None, None]
+    flags = {"chemistry": False, "laser": False,
+             "nscbc": {0: {0: nscbc.Side(p_inf=p0, target=target), 1: nscbc.Side(p_inf=p0)}}}
+    R, _ = rhs.rhs(mech, mapped.MappedGridT(N, N, 1, nodes, (2, 0, 0)), U, T, flags=flags)
+    st = rhs.primitives(mech, U, T)
+    rho, c = float(st["rho"].max()), float(st["c"].max())
+    E = float(U[-1].abs().max())
+    scale = torch.tensor([rho] * 4 + [rho * c] * 3 + [E], dtype=torch.float64)[:, None, None, None] * c / 1e-4
+    assert float((R.abs() / scale).max()) < 1e-12
