@@ -66,7 +66,9 @@ enum rf_bc {
     RF_BC_EXTRAPOLATE = 1, /* zero-gradient ghost cells (copies of the edge cell) */
     RF_BC_NSCBC = 2        /* Navier-Stokes characteristic boundaries at both ends of the axis
                               (see rf_set_nscbc; the axis needs >= 3 cells).  Single-grid RHS
-                              and RK steps in both precisions and with either scheme; rejected
+                              and RK steps in both precisions, with either scheme, on Cartesian
+                              and RF_MAPPED grids (normal: the boundary cell's mean area vector
+                              of the axis; the metric part of the normal term kept); rejected
                               by rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
 };
 
@@ -90,7 +92,7 @@ enum rf_flags {           /* term switches for tests (0 = full method) and the s
                              volumes, cell metrics and centres from the nodes.  dx, dy, dz of
                              the grid descriptor are then unused (they must still be > 0).
                              Single-grid RHS and RK steps in both precisions and with either
-                             scheme (global-memory sweeps); rejected with NSCBC axes and by
+                             scheme (global-memory sweeps), NSCBC axes included; rejected by
                              rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
     RF_FLAGS_ALL = 63
 };
@@ -264,7 +266,9 @@ typedef struct {
     double p_inf;             /* outflow: far-field pressure, Pa (> 0) */
     double sigma;             /* outflow: pressure relaxation coefficient (>= 0) */
     double eta_u, eta_T, eta_t, eta_Y;  /* inflow: relaxation coefficients (>= 0) */
-    double length;            /* ell, m; <= 0: the number of cells along the axis times its spacing */
+    double length;            /* ell, m; <= 0: the number of cells along the axis times its spacing
+                                 (on an RF_MAPPED grid: times V / |S| of the boundary cell, S its
+                                 mean area vector of the axis) */
     const double *target;     /* NULL: outflow.  Inflow: device array, FP64, [4 + Ns][plane] holding
                                  (u, v, w, T, Y_1 .. Y_Ns) for each cell of the boundary plane;
                                  plane index = i_t1 + n_t1 i_t2 with t1 < t2 the two other axes

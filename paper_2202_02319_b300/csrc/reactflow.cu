@@ -488,8 +488,6 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_create_ctx: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
-    if ((flags & RF_MAPPED) && (g->bc[0] == RF_BC_NSCBC || g->bc[1] == RF_BC_NSCBC || g->bc[2] == RF_BC_NSCBC))
-        return fail(RF_EINVAL, "rf_create_ctx: NSCBC axes are built for Cartesian grids, not RF_MAPPED ones");
     int mslot = 0;
     {
         int rc = mech_slot(m, &mslot);
@@ -506,10 +504,10 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     c->nv = m->ns + 4;
     c->nq = Q_X0 + 3 * m->ns;
     c->rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);
-    for (int a = 0; a < 3; ++a) {
-        const double len = (a == 0 ? g->nx * g->dx : (a == 1 ? g->ny * g->dy : g->nz * g->dz));
-        for (int e = 0; e < 2; ++e) c->nscbc[a].s[e] = NscbcSide{101325.0, 0.25, 1.0, 1.0, 1.0, 1.0, len, nullptr};
-    }
+    // ell = 0: the kernel takes the domain length along the axis (n h; n / (|S| / V) of
+    // the boundary cell on a mapped grid)
+    for (int a = 0; a < 3; ++a)
+        for (int e = 0; e < 2; ++e) c->nscbc[a].s[e] = NscbcSide{101325.0, 0.25, 1.0, 1.0, 1.0, 1.0, 0.0, nullptr};
     const size_t n = (size_t)c->n;
     struct A {
         void **p;
@@ -660,7 +658,11 @@ struct Path {
     static void nscbc_axis(rf_ctx *c, const Member &m, cudaStream_t s) {
         const int nn[3] = {c->g.nx, c->g.ny, c->g.nz};
         const long long plane = (long long)nn[DIR == 0 ? 1 : 0] * nn[DIR == 2 ? 1 : 2];
-        nscbc_kernel<R, UT, NS, DIR, SCHEME><<<(unsigned)((2 * plane + 127) / 128), 128, 0, s>>>(c->mslot, m, c->nscbc[DIR]);
+        const unsigned blocks = (unsigned)((2 * plane + 127) / 128);
+        if (c->flags & RF_MAPPED)
+            nscbc_kernel<R, UT, NS, DIR, SCHEME, 1><<<blocks, 128, 0, s>>>(c->mslot, m, c->nscbc[DIR]);
+        else
+            nscbc_kernel<R, UT, NS, DIR, SCHEME, 0><<<blocks, 128, 0, s>>>(c->mslot, m, c->nscbc[DIR]);
     }
 
     static int nscbc(rf_ctx *c, const Member &m, cudaStream_t s) {
@@ -1096,10 +1098,8 @@ extern "C" int rf_set_nscbc(rf_ctx *c, int axis, int side, const rf_nscbc *b) {
         return fail(RF_EINVAL, "rf_set_nscbc: relaxation coefficients must be >= 0");
     if (!b->target && !(b->p_inf > 0)) return fail(RF_EINVAL, "rf_set_nscbc: an outflow side needs p_inf > 0");
     if (!std::isfinite(b->length)) return fail(RF_EINVAL, "rf_set_nscbc: non-finite length");
-    const int na = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
-    const double h = axis == 0 ? c->g.dx : (axis == 1 ? c->g.dy : c->g.dz);
     c->nscbc[axis].s[side] = NscbcSide{b->p_inf, b->sigma, b->eta_u, b->eta_T, b->eta_t, b->eta_Y,
-                                       b->length > 0 ? b->length : na * h, b->target};
+                                       b->length > 0 ? b->length : 0.0, b->target};
     return RF_OK;
 }
 

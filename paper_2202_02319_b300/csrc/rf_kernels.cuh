@@ -2267,20 +2267,24 @@ __global__ void diag_fold_kernel(const double *partial, int nblocks, int nvals, 
 //   gamma = rho c^2 / p):  [rho Y_s] -(Y_s d1 + rho dY_s);  [rho u_k] -(u_k d1 + rho d_k);
 //   [E] -(|u|^2 d1 / 2 + rho u . d) + sum_s e_s [rho Y_s] + p / (gamma - 1)
 //   (d1 / rho - d2 / p + Wbar sum_s dY_s / W_s).
+// On a mapped grid the normal n is the boundary cell's mean area vector of the axis,
+// S = (S_low + S_high) / 2, normalised, d/dn = (|S| / V) d/d(index), the shear amplitude
+// is the vector u_n d(u - u_n n)/dn, and the metric part of the normal term,
+// -(S_high - S_low) . F(U_b) / V, stays (a uniform flow stays at rest).
 // One thread per boundary cell (both ends of the axis); it recomputes the cell's two
 // inviscid face fluxes with the sweep's own face code and adds
 // (characteristic term - scheme term) to the RHS accumulator, before the sweeps add
 // the scheme term.  The characteristic term is formed in FP64 in both precisions
 // (a few planes of cells).
 struct NscbcSide {
-    double p_inf, sigma, eta_u, eta_T, eta_t, eta_Y, ell;
+    double p_inf, sigma, eta_u, eta_T, eta_t, eta_Y, ell;   // ell <= 0: the domain length
     const double *target;        // [4 + NS][plane] (u, v, w, T, Y_s) or nullptr (outflow)
 };
 struct NscbcAxis {
     NscbcSide s[2];              // low end, high end
 };
 
-template <typename R, typename UT, int NS, int DIR, int SCHEME>
+template <typename R, typename UT, int NS, int DIR, int SCHEME, int GEOM>
 __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_constant__ Member m,
                                                     const __grid_constant__ NscbcAxis bx) {
     constexpr int NV = NS + 4;
@@ -2304,12 +2308,61 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
     const UT *U = (sizeof(UT) == 4) ? (const UT *)m.U32 : (const UT *)m.U;
     const R *Q = (const R *)m.Q;
 
+    // boundary normal n and d/dn = kappa d/d(index): the axis and 1/h on a Cartesian
+    // grid; on a mapped grid the cell's mean area vector of the axis, normalised, and
+    // |S| / V, with dS = S_high - S_low for the metric part of the normal term
+    double nv[3] = {0.0, 0.0, 0.0}, dS[3] = {0.0, 0.0, 0.0}, kappa;
+    R Slo[3], Shi[3];
+    if (GEOM) {
+        int cf[3] = {cc[0], cc[1], cc[2]};
+        const R *__restrict__ gS = (const R *)m.gS[DIR];
+        const long long nf = face_count<DIR>(m);
+        const long long f0 = face_index<DIR>(m, cf);
+        cf[DIR] += 1;
+        const long long f1 = face_index<DIR>(m, cf);
+        double Sm2 = 0.0, Sb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            Slo[k] = gS[k * nf + f0];
+            Shi[k] = gS[k * nf + f1];
+            Sb[k] = 0.5 * (wide(Slo[k]) + wide(Shi[k]));
+            dS[k] = wide(Shi[k]) - wide(Slo[k]);
+            Sm2 = fma(Sb[k], Sb[k], Sm2);
+        }
+        const double Sm = sqrt(Sm2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) nv[k] = Sb[k] / Sm;
+        kappa = Sm / m.gV[cell];
+    } else {
+        nv[DIR] = 1.0;
+        kappa = m.invh[DIR];
+    }
+
     // the scheme's inviscid normal term, G at the cell's low face and high face
     R G0[NV], G1[NV];
     {
         R rl, rr;
         int cf[3] = {cc[0], cc[1], cc[2]};
-        if (SCHEME == 1) {
+        if (GEOM) {
+            const double *__restrict__ gV = m.gV;
+            if (SCHEME == 1) {
+                const GlobalStencil6<R, UT, DIR> s0(m, U, Q, cf);
+                face_invisc_teno_mapped<R, NS, DIR>(m, s0, Slo, G0, rl, rr);
+                cf[DIR] += 1;
+                const GlobalStencil6<R, UT, DIR> s1(m, U, Q, cf);
+                face_invisc_teno_mapped<R, NS, DIR>(m, s1, Shi, G1, rl, rr);
+            } else {
+                const GlobalStencil<R, UT, DIR> s0(m, U, Q, cf);
+                const R S0 = sqrt(Slo[0] * Slo[0] + Slo[1] * Slo[1] + Slo[2] * Slo[2]);
+                const R h0 = narrow<R>(0.5 * (gV[s0.id[1]] + gV[s0.id[2]])) / S0;
+                face_invisc_mapped<R, NS, DIR>(m, s0, Slo, h0 * h0 * R(1.0 / 3.0), G0, rl, rr);
+                cf[DIR] += 1;
+                const GlobalStencil<R, UT, DIR> s1(m, U, Q, cf);
+                const R S1 = sqrt(Shi[0] * Shi[0] + Shi[1] * Shi[1] + Shi[2] * Shi[2]);
+                const R h1 = narrow<R>(0.5 * (gV[s1.id[1]] + gV[s1.id[2]])) / S1;
+                face_invisc_mapped<R, NS, DIR>(m, s1, Shi, h1 * h1 * R(1.0 / 3.0), G1, rl, rr);
+            }
+        } else if (SCHEME == 1) {
             const GlobalStencil6<R, UT, DIR> s0(m, U, Q, cf);
             face_invisc_teno<R, NS, DIR>(m, s0, G0, rl, rr);
             cf[DIR] += 1;
@@ -2326,23 +2379,24 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
 
     // primitives of the boundary cell and its two inward neighbours
     const double *__restrict__ Ud = m.U;
-    double rho[3], un[3], u1[3], u2[3], p[3];
+    double rho[3], u[3][3], p[3];                 // u[k][j]: component k, j cells inward
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const long long ck = cell + k * inw;
+    for (int j = 0; j < 3; ++j) {
+        const long long cj = cell + j * inw;
         double r = 0.0;
 #pragma unroll
-        for (int s = 0; s < NS; ++s) r += Ud[s * n + ck];
-        rho[k] = r;
-        un[k] = wide(Q[(Q_U + DIR) * n + ck]);
-        u1[k] = wide(Q[(Q_U + T1) * n + ck]);
-        u2[k] = wide(Q[(Q_U + T2) * n + ck]);
-        p[k] = wide(Q[Q_P * n + ck]);
+        for (int s = 0; s < NS; ++s) r += Ud[s * n + cj];
+        rho[j] = r;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[k][j] = wide(Q[(Q_U + k) * n + cj]);
+        p[j] = wide(Q[Q_P * n + cj]);
     }
-    // d/dn = h2 (-3 f_0 + 4 f_1 - f_2), f_k k cells inward (h2 = -+1 / (2h) high / low)
-    const double h2 = (side ? -0.5 : 0.5) * m.invh[DIR];
+    // d/dn = h2 (-3 f_0 + 4 f_1 - f_2), f_j j cells inward (h2 = -+kappa / 2 high / low)
+    const double h2 = (side ? -0.5 : 0.5) * kappa;
     auto ddn = [&](const double (&f)[3]) { return h2 * (fma(-3.0, f[0], 4.0 * f[1]) - f[2]); };
-    const double r0 = rho[0], u_n = un[0], p0 = p[0];
+    const double r0 = rho[0], p0 = p[0];
+    const double ub[3] = {u[0][0], u[1][0], u[2][0]};
+    const double u_n = nv[0] * ub[0] + nv[1] * ub[1] + nv[2] * ub[2];
     const double c = wide(Q[Q_C * n + cell]), T = wide(Q[Q_T * n + cell]);
     const double ir[3] = {1.0 / rho[0], 1.0 / rho[1], 1.0 / rho[2]};
     double Yb[NS], LY[NS];
@@ -2354,18 +2408,25 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
         LY[s] = u_n * ddn(y);
         iWbar = fma(y[0], M.invW[s], iWbar);
     }
-    const double drho = ddn(rho), dun = ddn(un), dp = ddn(p);
+    const double drho = ddn(rho), dp = ddn(p);
+    double du[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) du[k] = ddn(u[k]);
+    const double dun = nv[0] * du[0] + nv[1] * du[1] + nv[2] * du[2];
     double L1 = (u_n - c) * (dp - r0 * c * dun);
     double L5 = (u_n + c) * (dp + r0 * c * dun);
     double L2 = u_n * (c * c * drho - dp);
-    double L3 = u_n * ddn(u1), L4 = u_n * ddn(u2);
+    double Lt[3];                                 // shear amplitude vector u_n d(u - u_n n)/dn
+#pragma unroll
+    for (int k = 0; k < 3; ++k) Lt[k] = u_n * fma(-dun, nv[k], du[k]);
 
     // incoming amplitudes
     const NscbcSide &sd = bx.s[side];
+    const double ell = sd.ell > 0.0 ? sd.ell : (GEOM ? nd / kappa : nd * m.h[DIR]);
     const double F = fmax(1.0 - (u_n / c) * (u_n / c), 0.0);
-    const double cl = c / sd.ell;
+    const double cl = c / ell;
     const bool tgt = sd.target != nullptr;
-    double ac, ent = 0.0, sh1 = 0.0, sh2 = 0.0;
+    double ac, ent = 0.0, sh[3] = {0.0, 0.0, 0.0};
     if (!tgt) {
         ac = sd.sigma * cl * F * (p0 - sd.p_inf);
     } else {
@@ -2373,13 +2434,14 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
         double tv[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) tv[k] = tg[k * plane + pc];
-        ac = (side ? -1.0 : 1.0) * sd.eta_u * r0 * c * cl * F * (u_n - tv[DIR]);
+        const double utn = nv[0] * tv[0] + nv[1] * tv[1] + nv[2] * tv[2];
+        ac = (side ? -1.0 : 1.0) * sd.eta_u * r0 * c * cl * F * (u_n - utn);
         double Rbar = 0.0;
 #pragma unroll
         for (int s = 0; s < NS; ++s) Rbar = fma(Yb[s], M.RW[s], Rbar);
         ent = -sd.eta_T * r0 * Rbar * cl * (T - tg[3 * plane + pc]);
-        sh1 = sd.eta_t * cl * (u1[0] - tv[T1]);
-        sh2 = sd.eta_t * cl * (u2[0] - tv[T2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) sh[k] = sd.eta_t * cl * (fma(-u_n, nv[k], ub[k]) - fma(-utn, nv[k], tv[k]));
     }
     const bool in_m = side ? (u_n - c < 0.0) : (u_n - c > 0.0);
     const bool in_p = side ? (u_n + c < 0.0) : (u_n + c > 0.0);
@@ -2388,22 +2450,19 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
     if (in_p) L5 = ac;
     if (in_0) {
         L2 = ent;
-        L3 = sh1;
-        L4 = sh2;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Lt[k] = sh[k];
 #pragma unroll
         for (int s = 0; s < NS; ++s) LY[s] = tgt ? sd.eta_Y * cl * (Yb[s] - sd.target[(4 + s) * plane + pc]) : 0.0;
     }
 
-    // -P(V) d
+    // -P(V) d (velocity rate d_n n + Lt)
     const double d1 = (L2 + 0.5 * (L5 + L1)) / (c * c);
     const double d2 = 0.5 * (L5 + L1);
-    double dk[3], vel[3];
-    dk[DIR] = (L5 - L1) / (2.0 * r0 * c);
-    dk[T1] = L3;
-    dk[T2] = L4;
-    vel[DIR] = u_n;
-    vel[T1] = u1[0];
-    vel[T2] = u2[0];
+    const double dn = (L5 - L1) / (2.0 * r0 * c);
+    double dv[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) dv[k] = fma(dn, nv[k], Lt[k]);
     double out[NV];
     double eW = 0.0, sdY = 0.0;
 #pragma unroll
@@ -2414,14 +2473,26 @@ __global__ void __launch_bounds__(128) nscbc_kernel(int mslot, const __grid_cons
         sdY = fma(LY[s], M.invW[s], sdY);
     }
 #pragma unroll
-    for (int k = 0; k < 3; ++k) out[NS + k] = -fma(vel[k], d1, r0 * dk[k]);
-    const double ke = 0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]);
+    for (int k = 0; k < 3; ++k) out[NS + k] = -fma(ub[k], d1, r0 * dv[k]);
+    const double ke = 0.5 * (ub[0] * ub[0] + ub[1] * ub[1] + ub[2] * ub[2]);
     const double gm1 = r0 * c * c / p0 - 1.0;
     const double dT = p0 / gm1 * (d1 / r0 - d2 / p0 + sdY / iWbar);
-    out[NS + 3] = -(ke * d1 + r0 * (vel[0] * dk[0] + vel[1] * dk[1] + vel[2] * dk[2])) + eW + dT;
+    out[NS + 3] = -(ke * d1 + r0 * (ub[0] * dv[0] + ub[1] * dv[1] + ub[2] * dv[2])) + eW + dT;
+    if (GEOM) {
+        // metric part of the normal term: -dS . F(U_b) / V
+        const double iV = 1.0 / m.gV[cell];
+        const double th = dS[0] * ub[0] + dS[1] * ub[1] + dS[2] * ub[2];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double f = th * Ud[v * n + cell];
+            if (v >= NS && v < NS + 3) f = fma(p0, dS[v - NS], f);
+            if (v == NS + 3) f = fma(p0, th, f);
+            out[v] = fma(-f, iV, out[v]);
+        }
+    }
 
     R *__restrict__ rhs = (R *)m.rhs;
-    const R ih = (R)m.invh[DIR];
+    const R ih = GEOM ? ((const R *)m.giV)[cell] : (R)m.invh[DIR];
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const double scheme = wide((G1[v] - G0[v]) * ih);

@@ -6,8 +6,9 @@ scale p / h, see _err_mapped) with WENO3-Z and TENO6 on the paper's skewed grid,
 curved periodic and non-periodic 3-D grids and a uniform grid given by its nodes;
 FP64 RK steps at the time-step rule likewise; the mixed path within 1e-4 of those
 scales per RHS and 1e-5 after a run of steps; a uniform flow stays uniform; the
-skewed-grid vortex converges at third order on the GPU; the entry points that do
-not support mapped grids reject them."""
+skewed-grid vortex converges at third order on the GPU; characteristic (NSCBC)
+ends on curved grids match the oracle likewise; the entry points that do not support
+mapped grids reject them."""
 import math
 
 import numpy as np
@@ -259,9 +260,6 @@ def test_mapped_is_rejected_where_unsupported():
     grads = torch.zeros(5 + case.mech.n_reactions, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError, match="RF_MAPPED"):
         nv.adjoint_rhs(ctx, U, T, 0.0, None, lam, 0.0, lam.clone(), grads)
-    nscbc_grid = synth.Grid(8, 8, 8, 1e-4, 1e-4, 1e-4, (synth.BC_NSCBC, 0, 0))
-    with pytest.raises(RuntimeError, match="NSCBC"):
-        nv.create_ctx(mech, nscbc_grid, nv.RF_FP64, nv.RF_MAPPED)
     fresh = nv.create_ctx(mech, case.grid, nv.RF_FP64, nv.RF_MAPPED)
     out = torch.empty_like(U)
     with pytest.raises(RuntimeError, match="rf_set_nodes"):
@@ -272,3 +270,82 @@ def test_mapped_is_rejected_where_unsupported():
         nv.set_nodes(fresh, torch.as_tensor(mirrored, dtype=torch.float64).cuda())
     with pytest.raises(RuntimeError, match="RF_MAPPED"):
         nv.set_nodes(nv.create_ctx(mech, case.grid, nv.RF_FP64), torch.as_tensor(case.nodes).cuda())
+
+
+def _mapped_nscbc_cases():
+    """Characteristic ends on curved grids: the paper's skewed grid with an inflow
+    target on the low x end and an outflow on the high end; a curved 3-D grid with
+    outflows on x and an inflow / outflow pair on y."""
+    N = 20
+    skew = _case("skewed_nscbc_20x20", (1, N, N), synth.skewed_nodes(N, L=N * 1e-4), (2, 0, 0), 6, laser=False)
+    g = np.random.default_rng(6)
+    ns = skew.mech.n_species
+    tg = np.empty((4 + ns, N))
+    tg[0] = 40.0 + 10.0 * g.standard_normal(N)
+    tg[1] = 5.0 * g.standard_normal(N)
+    tg[2] = 0.0
+    tg[3] = 900.0
+    Y = g.dirichlet(np.ones(ns), size=N).T
+    tg[4:] = Y
+    skew.nscbc = {(0, 0): dict(p_inf=101325.0, eta_u=0.8, eta_T=1.2, eta_t=0.6, eta_Y=0.9, target=tg),
+                  (0, 1): dict(p_inf=100000.0, sigma=0.3, target=None)}
+    wavy = _case("wavy_nscbc_10x9x8", (8, 9, 10), synth.wavy_nodes(10, 9, 8, 1e-4), (2, 2, 0), 7, laser=False)
+    tgy = np.empty((4 + ns, 10 * 8))
+    tgy[0], tgy[1], tgy[2], tgy[3] = 10.0, 30.0, -5.0, 800.0
+    tgy[4:] = (np.ones(ns) / ns)[:, None]
+    wavy.nscbc = {(0, 0): dict(p_inf=101325.0, sigma=0.25, target=None),
+                  (0, 1): dict(p_inf=101325.0, sigma=0.5, target=None),
+                  (1, 0): dict(p_inf=101325.0, eta_u=1.5, eta_T=0.5, eta_t=1.0, eta_Y=0.7, length=2e-3, target=tgy),
+                  (1, 1): dict(p_inf=99000.0, sigma=0.1, target=None)}
+    return [skew, wavy]
+
+
+NSCBC_CASES = _mapped_nscbc_cases()
+
+
+def _oracle_rhs_nscbc(case, flags=None):
+    from tests.gpu_common import nscbc_oracle
+    return _oracle_rhs(case, dict(flags or {}, nscbc=nscbc_oracle(case)))
+
+
+@pytest.mark.parametrize("teno", [False, True], ids=["weno3z", "teno6"])
+@pytest.mark.parametrize("case", NSCBC_CASES, ids=[c.name for c in NSCBC_CASES])
+def test_mapped_nscbc_rhs_parity_fp64(case, teno):
+    nv = _nv()
+    mech, ctx, U, T = gpu_setup(case, flags=nv.RF_TENO6 if teno else 0)
+    out = torch.empty_like(U)
+    nv.rhs(ctx, U, T, 0.0, None, out)
+    nv.check(ctx)
+    err = _err_mapped(out, _oracle_rhs_nscbc(case, {"scheme": "teno6"} if teno else None), case)
+    assert err.max() < TOL64, err
+
+
+@pytest.mark.parametrize("case", NSCBC_CASES, ids=[c.name for c in NSCBC_CASES])
+def test_mapped_nscbc_rhs_parity_mixed(case):
+    nv = _nv()
+    mech, ctx, U, T = gpu_setup(case, precision=nv.RF_MIXED)
+    out = torch.empty_like(U)
+    nv.rhs(ctx, U, T, 0.0, None, out)
+    nv.check(ctx)
+    err = _err_mapped(out, _oracle_rhs_nscbc(case), case)
+    assert err.max() < 1e-4, err
+
+
+def test_mapped_nscbc_rk_step_parity_fp64():
+    """Three FP64 steps at the CFL rule with characteristic ends on the skewed grid."""
+    from tests.gpu_common import nscbc_oracle
+    nv = _nv()
+    case = NSCBC_CASES[0]
+    mech, ctx, U, T = gpu_setup(case)
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+    mt, g, Uo, To = oracle_setup(case)
+    fl = {"nscbc": nscbc_oracle(case)}
+    to = 0.0
+    for _ in range(3):
+        nv.rk_step(ctx, U, T, t, 0.0, 0.5, None, dt)
+        nv.check(ctx)
+        Uo, To, dto = oracle.rk.rk_step(mt, g, Uo, To, to, 0.0, None, 0.5, fl)
+        to += dto
+        assert abs(float(dt) - dto) <= 1e-12 * dto
+    assert rel_inf(U, Uo.reshape(U.shape)).max() < TOL64
