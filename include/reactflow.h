@@ -68,8 +68,10 @@ enum rf_bc {
                               (see rf_set_nscbc; the axis needs >= 3 cells).  Single-grid RHS
                               and RK steps in both precisions, with either scheme, on Cartesian
                               and RF_MAPPED grids (normal: the boundary cell's mean area vector
-                              of the axis; the metric part of the normal term kept); rejected
-                              by rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
+                              of the axis; the metric part of the normal term kept) and in
+                              batched ensembles (the boundary kernels run per member after
+                              the cell state); rejected by rf_rhs_noalloc and the adjoint
+                              entry points */
 };
 
 enum rf_flags {           /* term switches for tests (0 = full method) and the scheme */

@@ -160,8 +160,10 @@ struct rf_ctx {
     // optional per-kernel timing: CUDA events recorded on the launching stream
     int profile = 0;
     std::vector<cudaEvent_t> ev[RF_NPROF][2];
-    // characteristic boundaries of the axes whose bc is RF_BC_NSCBC (rf_set_nscbc)
+    // characteristic boundaries of the axes whose bc is RF_BC_NSCBC (rf_set_nscbc) and a
+    // counter of their changes (ensembles re-capture their graphs when it moves)
     NscbcAxis nscbc[3];
+    long long nscbc_version = 0;
     // mapped grids (RF_MAPPED): face area vectors, cell metric, volume, 1/volume (bulk
     // type) and cell centres (FP64), filled by rf_set_nodes
     int nodes_set = 0;
@@ -1100,6 +1102,7 @@ extern "C" int rf_set_nscbc(rf_ctx *c, int axis, int side, const rf_nscbc *b) {
     if (!std::isfinite(b->length)) return fail(RF_EINVAL, "rf_set_nscbc: non-finite length");
     c->nscbc[axis].s[side] = NscbcSide{b->p_inf, b->sigma, b->eta_u, b->eta_T, b->eta_t, b->eta_Y,
                                        b->length > 0 ? b->length : 0.0, b->target};
+    ++c->nscbc_version;
     return RF_OK;
 }
 
@@ -1148,6 +1151,8 @@ struct rf_ensemble {
     std::vector<rf_laser> las;
     double *t_dev = nullptr;
     Member *d_tab[3] = {nullptr, nullptr, nullptr};
+    std::vector<Member> h_tab[3];             // host copies (launches of members' own kernels)
+    long long nscbc_stamp = -1;               // members' NSCBC settings when the graphs were captured
     EnsItem *d_items[4] = {nullptr, nullptr, nullptr, nullptr};
     int nitems[4] = {0, 0, 0, 0};
     unsigned int *d_bar = nullptr;
@@ -1248,6 +1253,7 @@ static int ens_build(rf_ensemble *e) {
     for (int k = 0; k < 3; ++k) {
         CUDA_TRY(cudaMalloc((void **)&e->d_tab[k], sizeof(Member) * e->n));
         CUDA_TRY(cudaMemcpy(e->d_tab[k], tab[k].data(), sizeof(Member) * e->n, cudaMemcpyHostToDevice));
+        e->h_tab[k] = tab[k];
     }
     for (int k = 0; k < 4; ++k) {
         e->nitems[k] = (int)items[k].size();
@@ -1279,6 +1285,17 @@ static EnsDev ens_dev(rf_ensemble *e, unsigned int grid) {
 template <typename R, int NS>
 struct EnsPath {
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
+
+    // characteristic boundaries of the members that have NSCBC axes, each by its own
+    // launches (a few planes of cells), after the stage's cell state
+    static int members_nscbc(rf_ensemble *e, int k, cudaStream_t s) {
+        for (int mi = 0; mi < e->n; ++mi) {
+            rf_ctx *c = e->ctx[mi];
+            if (c->g.bc[0] != RF_BC_NSCBC && c->g.bc[1] != RF_BC_NSCBC && c->g.bc[2] != RF_BC_NSCBC) continue;
+            if (int rc = Path<R, NS>::nscbc(c, e->h_tab[k][mi], s)) return rc;
+        }
+        return RF_OK;
+    }
 
     static int setup(rf_ensemble *e) {
         e->smem_cell = cell_state_smem_max<R, NS>(128, e->mech->nr);
@@ -1312,6 +1329,7 @@ struct EnsPath {
                 ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);
                 LAUNCH_CHECK();
             }
+            if (int rc = members_nscbc(e, k, s)) return rc;
             ens_x_kernel<R, UT, NS, MODE_ACCUM><<<e->nitems[1], 128, e->smem_x, s>>>(M, ens_dev(e, e->nitems[1]), k);
             LAUNCH_CHECK();
             ens_walk_kernel<R, UT, NS, 1, MODE_ACCUM><<<e->nitems[2], 128, walk_smem<R, NS>(), s>>>(M, ens_dev(e, e->nitems[2]), k);
@@ -1345,6 +1363,7 @@ struct EnsPath {
                 ens_dt_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(M, E0);
                 LAUNCH_CHECK();
             }
+            if (int rc = members_nscbc(e, k, s)) return rc;
             ens_x_kernel<R, UT, NS, MODE_ACCUM><<<e->nitems[1], 128, e->smem_x, s>>>(M, ens_dev(e, e->nitems[1]), k);
             LAUNCH_CHECK();
             EnsDev E = ens_dev(e, e->coop_blocks);
@@ -1411,10 +1430,6 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
         if (c->flags & RF_MAPPED) {
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d is a mapped grid; batched ensembles run Cartesian grids", i);
-        }
-        if (c->g.bc[0] == RF_BC_NSCBC || c->g.bc[1] == RF_BC_NSCBC || c->g.bc[2] == RF_BC_NSCBC) {
-            delete e;
-            return fail(RF_EINVAL, "rf_ensemble_create: member %d has an NSCBC axis; batched ensembles run periodic and zero-gradient axes", i);
         }
         if (c->flags & RF_TENO6) {
             delete e;
@@ -1526,6 +1541,14 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
         // modes 2 and 3 replay one step captured as a CUDA graph (mode 3's graph holds its
         // cooperative launches)
         const bool graph = mode == 2 || mode == 3;
+        long long stamp = 0;
+        for (rf_ctx *c : e->ctx) stamp += c->nscbc_version;
+        if (stamp != e->nscbc_stamp) {
+            // a member's boundary settings (captured as launch parameters) changed
+            for (int q = 0; q < 4; ++q)
+                if (e->graph[q]) cudaGraphExecDestroy(e->graph[q]), e->graph[q] = nullptr;
+            e->nscbc_stamp = stamp;
+        }
         if (graph && nsteps > 0 && !e->graph[mode]) {
             // captured on the ensemble's own stream: capture records, it does not run anything
             cudaGraph_t g;

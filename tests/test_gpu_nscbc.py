@@ -4,9 +4,10 @@ the FP64 oracle on the same seeded inputs: the FP64 RHS within 1e-12 per conserv
 variable with WENO3-Z and TENO6, over subsonic and partly supersonic states, inflow
 targets and outflow relaxation on every axis; FP64 RK steps likewise; the mixed
 RHS within 1e-4 of each group's scale; the mixed state after a run of steps within
-1e-5 (WENO3-Z) or within the oracle's own sensitivity (TENO6); the entry points
-that do not support NSCBC reject it; and a longer injection run on the GPU alone
-holds the inflow plane at its target."""
+1e-5 (WENO3-Z) or within the oracle's own sensitivity (TENO6); batched ensembles with
+NSCBC members match the member loop bitwise; the entry points that do not support
+NSCBC reject it; and a longer injection run on the GPU alone holds the inflow plane
+at its target."""
 import numpy as np
 import pytest
 import torch
@@ -214,8 +215,6 @@ def test_nscbc_is_rejected_where_unsupported():
     case = CASES[0]
     mech, ctx, U, T = gpu_setup(case)
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(RuntimeError, match="NSCBC"):
-        nv.ensemble_create([ctx], [U], [T], [case.laser.as_tuple()], t)
     lam = torch.zeros_like(U)
     grads = torch.zeros(5 + case.mech.n_reactions, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError, match="NSCBC"):
@@ -229,3 +228,39 @@ def test_nscbc_is_rejected_where_unsupported():
     small = synth.Grid(2, 8, 1, 1e-4, 1e-4, 1e-4, (synth.BC_NSCBC, synth.BC_PERIODIC, synth.BC_PERIODIC))
     with pytest.raises(RuntimeError, match="needs >= 3"):
         nv.create_ctx(mech, small, nv.RF_FP64)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_nscbc_members_in_batched_ensembles_equal_the_member_loop(precision):
+    """Members with characteristic ends (injection cases of uneven sizes, inflow
+    targets of their own) beside a periodic member: every batched mode advances each
+    member bitwise as the per-member loop does."""
+    from tests.gpu_common import nscbc_gpu
+    nv = _nv()
+    cases = [synth.case_jet_inflow(3, 16, 12, 10), synth.case_jet_inflow(4, 12, 10, 8, u_jet=60.0),
+             synth.ensemble_members(seed=2, n_members=1, lo=8, hi=12)[0]]
+    res = {}
+    for mode in (0, 1, 2, 3):
+        mech = nv.init_mechanism(cases[0].mech)
+        ctxs, Us, Ts = [], [], []
+        for c in cases:
+            ns, n = c.mech.n_species, c.grid.ncells
+            ctx = nv.create_ctx(mech, c.grid, precision)
+            U = torch.empty((ns + 4, n), dtype=torch.float64, device="cuda")
+            T = torch.empty(n, dtype=torch.float64, device="cuda")
+            nv.init_state(ctx, torch.as_tensor(c.prim, dtype=torch.float64).reshape(5 + ns, n).cuda(), U, T)
+            nscbc_gpu(ctx, c)
+            ctxs.append(ctx)
+            Us.append(U)
+            Ts.append(T)
+        t = torch.zeros(len(cases), dtype=torch.float64, device="cuda")
+        e = nv.ensemble_create(ctxs, Us, Ts, [c.laser.as_tuple() for c in cases], t)
+        code, st = nv.run_ensemble(e, 3, mode, 0.5)
+        assert code == 0 and st == [0] * len(cases)
+        res[mode] = ([u.cpu() for u in Us], t.cpu())
+        del e
+    for mode in (1, 2, 3):
+        for m in range(len(cases)):
+            assert torch.equal(res[mode][0][m], res[0][0][m]), (mode, m)
+        assert torch.equal(res[mode][1], res[0][1])
+    assert float(res[0][1].min()) > 0.0
