@@ -23,18 +23,19 @@ from . import rk, rhs as rhs_mod
 from .adjoint import heat_release
 
 
-def member_window(mech, grid, prim, las, nsteps: int, dt: float):
+def member_window(mech, grid, prim, las, nsteps: int, dt: float, flags=None):
     """Runs one member over the window; returns (peak T at the end, total HRR at
-    the middle, total HRR at the end)."""
+    the middle, total HRR at the end).  flags as for oracle.rhs.rhs (for example the
+    case's characteristic ends)."""
     U, T = rhs_mod.init_state(mech, prim)
     half = nsteps // 2
     t = 0.0
     for _ in range(half):
-        U, T, _ = rk.rk_step(mech, grid, U, T, t, dt, las)
+        U, T, _ = rk.rk_step(mech, grid, U, T, t, dt, las, flags=flags)
         t += dt
     h_mid, T = heat_release(mech, grid, U, T)
     for _ in range(nsteps - half):
-        U, T, _ = rk.rk_step(mech, grid, U, T, t, dt, las)
+        U, T, _ = rk.rk_step(mech, grid, U, T, t, dt, las, flags=flags)
         t += dt
     h_end, T = heat_release(mech, grid, U, T)
     return float(T.max()), float(h_mid), float(h_end)
@@ -65,12 +66,12 @@ def bisect(outcome_of, lo: float, hi: float, members: int, rounds: int):
 
 
 def minimum_ignition_energy(mech, grid, prim, las_template, E_lo: float, E_hi: float, members: int,
-                            rounds: int, nsteps: int, dt: float, T_fail: float = 600.0):
+                            rounds: int, nsteps: int, dt: float, T_fail: float = 600.0, flags=None):
     """The oracle's bisection: every probe is one member run on the oracle."""
     def outcome_of(energies):
         out = []
         for E in energies:
             las = (E,) + tuple(las_template[1:])
-            out.append(is_ignited(*member_window(mech, grid, prim, las, nsteps, dt), T_fail=T_fail))
+            out.append(is_ignited(*member_window(mech, grid, prim, las, nsteps, dt, flags), T_fail=T_fail))
         return out
     return bisect(outcome_of, E_lo, E_hi, members, rounds)

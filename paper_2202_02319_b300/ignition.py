@@ -80,6 +80,16 @@ class EnsembleIgnition:
         self.prim = torch.as_tensor(case.prim, dtype=torch.float64).reshape(5 + ns, n).to(self.dev)
         self.mech = nv.init_mechanism(case.mech)
         self.ctxs = [nv.create_ctx(self.mech, case.grid, precision) for _ in range(self.members)]
+        # characteristic ends of the case (inflow targets shared by the members)
+        self.targets = {}
+        for (axis, side), spec in getattr(case, "nscbc", {}).items():
+            kw = {k: v for k, v in spec.items() if k != "target"}
+            tg = spec.get("target")
+            if tg is not None:
+                tg = torch.as_tensor(tg, dtype=torch.float64).to(self.dev).contiguous()
+                self.targets[(axis, side)] = tg
+            for ctx in self.ctxs:
+                nv.set_nscbc(ctx, axis, side, target=tg, **kw)
         self.Us = [torch.empty((ns + 4, n), dtype=torch.float64, device=self.dev) for _ in range(self.members)]
         self.Ts = [torch.empty(n, dtype=torch.float64, device=self.dev) for _ in range(self.members)]
 

@@ -41,3 +41,26 @@ def test_minimum_ignition_energy_matches_the_oracle(mode):
             peak, h_mid, h_end = oig.member_window(mt, g, prim, (E,) + case.laser.as_tuple()[1:], nsteps, dt)
             assert abs(mT - peak) <= 1e-11 * peak
             assert abs(he - h_end) <= 1e-9 * abs(h_end) + 1e-20
+
+
+def test_minimum_ignition_energy_with_characteristic_ends_matches_the_oracle():
+    """The same search with NSCBC outflow ends on the jet's axis (the paper's
+    diffusion-flame ensembles run between characteristic boundaries): bracket and
+    every member decision equal the oracle's."""
+    from paper_2202_02319_b300 import ignition, native as nv
+    case = _case()
+    case.grid.bc = (synth.BC_NSCBC, 0, 0)
+    case.nscbc = {(0, 0): dict(p_inf=synth.P_ATM, sigma=0.25, target=None),
+                  (0, 1): dict(p_inf=synth.P_ATM, sigma=0.25, target=None)}
+    members, rounds, nsteps, dt = 3, 2, 30, 2e-9
+    runner = ignition.EnsembleIgnition(case, members, nsteps, dt, precision=nv.RF_FP64, mode=nv.ENS_GRAPH)
+    res = ignition.minimum_ignition_energy(runner, 0.02e-3, 3e-3, rounds=rounds)
+    from oracle import nscbc
+    mt, g = from_synth(case.mech), grid_from_synth(case.grid)
+    prim = torch.as_tensor(case.prim, dtype=torch.float64)
+    fl = {"nscbc": {0: {0: nscbc.Side(p_inf=synth.P_ATM, sigma=0.25), 1: nscbc.Side(p_inf=synth.P_ATM, sigma=0.25)}}}
+    (lo, hi), hist = oig.minimum_ignition_energy(mt, g, prim, case.laser.as_tuple(), 0.02e-3, 3e-3, members,
+                                                 rounds, nsteps, dt, flags=fl)
+    assert res.bracket == pytest.approx((lo, hi), rel=1e-14)
+    for r, (probes, outcomes, _) in zip(res.rounds, hist):
+        assert r.ignited == outcomes
