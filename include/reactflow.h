@@ -94,8 +94,9 @@ enum rf_flags {           /* term switches for tests (0 = full method) and the s
                              volumes, cell metrics and centres from the nodes.  dx, dy, dz of
                              the grid descriptor are then unused (they must still be > 0).
                              Single-grid RHS and RK steps in both precisions and with either
-                             scheme (global-memory sweeps), NSCBC axes included; rejected by
-                             rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
+                             scheme (global-memory sweeps), NSCBC axes included; ensembles run
+                             mapped members in the member loop (mode 0) only; rejected by
+                             rf_rhs_noalloc and the adjoint entry points */
     RF_FLAGS_ALL = 63
 };
 
@@ -361,7 +362,8 @@ int rf_ensemble_set_option(rf_ensemble *e, const char *key, double value);
  *         barrier between them, bounded: a wait that runs out returns RF_ETIMEOUT),
  *         and (mixed precision) the stage update as a launch over the cells; one
  *         step is captured as a CUDA graph, as in mode 2, and replayed.
- * Modes 1-3 need every member with nx, ny, nz > 1.  A member whose state fails
+ * Modes 1-3 need every member with nx, ny, nz > 1 and Cartesian (an ensemble with
+ * RF_MAPPED members runs mode 0).  A member whose state fails
  * (Newton, non-finite, range) is frozen at its last good step and the others
  * continue; member_status (host, n ints, may be NULL) receives each member's
  * RF_E* code.  Synchronous.  Returns RF_ETIMEOUT if a barrier gave up, a member's

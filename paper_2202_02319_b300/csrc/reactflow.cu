@@ -1146,6 +1146,7 @@ struct rf_ensemble {
     const rf_mech *mech = nullptr;
     int n = 0, precision = 0, ns = 0;
     bool all3d = true;
+    bool any_mapped = false;                  // a mapped member: only the member loop (mode 0)
     std::vector<rf_ctx *> ctx;
     std::vector<double *> U, T;
     std::vector<rf_laser> las;
@@ -1427,9 +1428,9 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d has a null context or buffer", i);
         }
-        if (c->flags & RF_MAPPED) {
+        if ((c->flags & RF_MAPPED) && !c->nodes_set) {
             delete e;
-            return fail(RF_EINVAL, "rf_ensemble_create: member %d is a mapped grid; batched ensembles run Cartesian grids", i);
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d is a mapped grid without node coordinates (rf_set_nodes)", i);
         }
         if (c->flags & RF_TENO6) {
             delete e;
@@ -1445,6 +1446,7 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             return fail(RF_EINVAL, "rf_ensemble_create: member %d differs in mechanism or precision", i);
         }
         e->all3d = e->all3d && c->g.nx > 1 && c->g.ny > 1 && c->g.nz > 1;
+        e->any_mapped = e->any_mapped || (c->flags & RF_MAPPED);
         e->ctx.push_back(c);
         e->U.push_back(U[i]);
         e->T.push_back(T[i]);
@@ -1526,6 +1528,8 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
     if (!e || nsteps < 0 || mode < 0 || mode > 3) return fail(RF_EINVAL, "rf_run_ensemble: bad argument");
     if (!(dt_fixed > 0.0) && !(cfl > 0.0)) return fail(RF_EINVAL, "rf_run_ensemble: need dt_fixed > 0 or cfl > 0");
     if (mode > 0 && !e->all3d) return fail(RF_EINVAL, "rf_run_ensemble: batched modes need every member with nx, ny, nz > 1");
+    if (mode > 0 && e->any_mapped)
+        return fail(RF_EINVAL, "rf_run_ensemble: batched modes run Cartesian members; an ensemble with mapped members runs mode 0");
     cudaStream_t s = (cudaStream_t)stream;
     if (mode == 0) {
         for (int k = 0; k < nsteps; ++k) {
@@ -1616,6 +1620,7 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
 extern "C" int rf_ensemble_autotune(rf_ensemble *e, int mode, double cfl, int *seg_out, rf_stream stream) {
     if (!e || mode < 1 || mode > 3) return fail(RF_EINVAL, "rf_ensemble_autotune: bad argument");
     if (!e->all3d) return fail(RF_EINVAL, "rf_ensemble_autotune: batched modes need 3-D members");
+    if (e->any_mapped) return fail(RF_EINVAL, "rf_ensemble_autotune: batched modes run Cartesian members");
     cudaStream_t s = (cudaStream_t)stream;
     // keep the states: trial steps run on them and are rolled back
     size_t tot = 0;

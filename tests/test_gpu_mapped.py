@@ -254,8 +254,12 @@ def test_mapped_is_rejected_where_unsupported():
     case = CASES[1]
     mech, ctx, U, T = gpu_setup(case)
     t = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(RuntimeError, match="mapped"):
-        nv.ensemble_create([ctx], [U], [T], [case.laser.as_tuple()], t)
+    ens = nv.ensemble_create([ctx], [U], [T], [case.laser.as_tuple()], t)
+    with pytest.raises(RuntimeError, match="Cartesian members"):
+        nv.run_ensemble(ens, 1, nv.ENS_GRAPH, 0.5)
+    code, st = nv.run_ensemble(ens, 1, nv.ENS_LOOP, 0.5)
+    assert code == 0 and float(t[0]) > 0.0
+    del ens
     lam = torch.zeros_like(U)
     grads = torch.zeros(5 + case.mech.n_reactions, dtype=torch.float64, device="cuda")
     with pytest.raises(RuntimeError, match="RF_MAPPED"):
