@@ -17,6 +17,7 @@ vectorised over cells, in the order the paper states each step:
   fluxes      WENO3-Z with local Lax-Friedrichs splitting; 2nd-order central
               viscous, heat and species-diffusion fluxes
   rhs         cell state, source terms, flux divergence
+  charwise    characteristic-wise flux splitting (the optional scheme variant)
   mapped      curvilinear grids: face area vectors, volumes, metrics, mapped fluxes
   nscbc       characteristic (NSCBC) inflow / outflow boundaries
   rk          SSP-RK3 (Shu-Osher form) and the time-step rule
@@ -26,5 +27,5 @@ vectorised over cells, in the order the paper states each step:
 Where the paper is silent the oracle takes one stated reading; each module's
 docstring lists the readings it implements.
 """
-from . import thermo, transport, chemistry, laser, fluxes, mapped, nscbc, rhs, rk  # noqa: F401
+from . import thermo, transport, chemistry, laser, fluxes, charwise, mapped, nscbc, rhs, rk  # noqa: F401
 from .mech import MechT, GridT, from_synth  # noqa: F401

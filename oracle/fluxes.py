@@ -98,11 +98,15 @@ def weno3z(a, b, c, h):
     same value since omega0 + omega1 = 1, with q0 - q1 = ((b - a) - (c - b)) / 2:
     reverse-mode derivatives of the weights then multiply differences of f, not
     values of f, and stay accurate where f varies by far less than its size."""
+    return weno3z_eps(a, b, c, h * h * (a * a + b * b + c * c) / 3.0 + EPS_WENO)
+
+
+def weno3z_eps(a, b, c, eps):
+    """WENO3-Z value at i+1/2 with a given eps (see weno3z)."""
     q1 = 0.5 * b + 0.5 * c
     beta0 = (b - a) ** 2
     beta1 = (c - b) ** 2
     tau = (beta1 - beta0).abs()
-    eps = h * h * (a * a + b * b + c * c) / 3.0 + EPS_WENO
     alpha0 = (1.0 / 3.0) * (1.0 + tau / (beta0 + eps))
     alpha1 = (2.0 / 3.0) * (1.0 + tau / (beta1 + eps))
     omega0 = alpha0 / (alpha0 + alpha1)

@@ -9,7 +9,8 @@ variable-major [nv, nz, ny, nx].  The RHS is
 
 `flags` switches terms off for tests: keys 'inviscid', 'viscous', 'chemistry',
 'laser' (all default True); 'scheme' picks the inviscid reconstruction
-('weno3z' or 'teno6'); 'nscbc' maps an axis whose bc is 2 to its {side: Side}
+('weno3z' or 'teno6'); 'splitting' 'component' (default) or 'characteristic'
+(oracle.charwise, Cartesian grids); 'nscbc' maps an axis whose bc is 2 to its {side: Side}
 (oracle.nscbc; a missing side is an outflow with the defaults).  A grid with
 node coordinates (oracle.mapped.MappedGridT) runs the mapped form: face fluxes
 through the faces' area vectors, divided by the cell volumes.
@@ -18,7 +19,7 @@ from __future__ import annotations
 
 import torch
 
-from . import chemistry, fluxes, laser as laser_mod, mapped, nscbc, thermo, transport
+from . import charwise, chemistry, fluxes, laser as laser_mod, mapped, nscbc, thermo, transport
 from .mech import R_U, MechT
 
 
@@ -106,7 +107,10 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
         mup = fluxes.pad(st["mu"], grid)
         lamp = fluxes.pad(st["lam"], grid)
     scheme = (flags or {}).get("scheme", "weno3z")
+    charw = (flags or {}).get("splitting", "component") == "characteristic"
     if getattr(grid, "nodes", None) is not None:
+        if charw:
+            raise ValueError("characteristic-wise splitting is stated for Cartesian grids only")
         geo = mapped.cached_geometry(grid)
         Vp = fluxes.pad(geo["V"], grid)
         Mp = fluxes.pad(geo["M"], grid)
@@ -124,7 +128,10 @@ def rhs(mech: MechT, grid, U: torch.Tensor, T0: torch.Tensor, t: float = 0.0, la
         return out, T
     for d in range(3):
         if _flag(flags, "inviscid"):
-            Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns, scheme)
+            if charw:
+                Fa = charwise.inviscid_flux(mech, Up, velp, pp, cp, Tp, grid, d, ns, scheme)
+            else:
+                Fa = fluxes.inviscid_flux(Up, velp, pp, cp, grid, d, ns, scheme)
             out = out - fluxes.divergence(Fa, grid, d)
             if grid.bc[d] == nscbc.BC_NSCBC:
                 out = nscbc.correct(mech, grid, st, Fa, out, d, (flags or {}).get("nscbc", {}).get(d))
