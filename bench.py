@@ -258,6 +258,9 @@ def run_ours(args):
     # --- TENO6 (the paper's sixth-order scheme) on the same workload, both precisions
     teno = run_teno_leg(args, mech, case, prim, dev) if args.teno_steps > 0 else None
 
+    # --- characteristic-wise splitting with WENO3-Z and with TENO6, same workload
+    charw = run_charwise_leg(args, mech, case, prim, dev) if args.charwise_steps > 0 else None
+
     # --- characteristic inflow / outflow boundaries: injection case, mixed
     nscbc = run_nscbc_leg(args, dev) if args.nscbc_steps > 0 else None
 
@@ -345,6 +348,7 @@ def run_ours(args):
         "kernels": kernels,
         "roofline": roofline,
         "teno6": teno,
+        "charwise": charw,
         "nscbc": nscbc,
         "mapped": mapd,
         "min_ignition_energy": mie,
@@ -370,18 +374,21 @@ def run_ours(args):
 
 # ----------------------------------------------------------------------------- TENO6 leg
 
-def run_teno_leg(args, mech, case, prim, dev):
+def run_teno_leg(args, mech, case, prim, dev, flags=None, steps_mixed=None):
     """Cell-updates/s of the same workload with the inviscid fluxes by TENO6 (six-cell
-    stencils, sweeps from global memory), mixed and FP64, CUDA events on the
-    launching stream, per-kernel times from the library's profile events."""
+    stencils, sweeps from global memory), or with the scheme `flags` selects, mixed
+    and FP64, CUDA events on the launching stream, per-kernel times from the
+    library's profile events."""
     import torch
     from paper_2202_02319_b300 import native as nv
     ns = case.mech.n_species
     ncell = case.grid.ncells
     las = case.laser.as_tuple()
+    flags = nv.RF_TENO6 if flags is None else flags
+    steps_mixed = args.teno_steps if steps_mixed is None else steps_mixed
     out = {}
-    for name, prec, steps in (("mixed", nv.RF_MIXED, args.teno_steps), ("fp64", nv.RF_FP64, max(1, args.teno_steps // 2))):
-        ctx = nv.create_ctx(mech, case.grid, prec, nv.RF_TENO6)
+    for name, prec, steps in (("mixed", nv.RF_MIXED, steps_mixed), ("fp64", nv.RF_FP64, max(1, steps_mixed // 2))):
+        ctx = nv.create_ctx(mech, case.grid, prec, flags)
         U = torch.empty((ns + 4, ncell), dtype=torch.float64, device=dev)
         T = torch.empty(ncell, dtype=torch.float64, device=dev)
         nv.init_state(ctx, prim, U, T)
@@ -408,6 +415,16 @@ def run_teno_leg(args, mech, case, prim, dev):
         del ctx, U, T
         torch.cuda.empty_cache()
     return out
+
+
+# ----------------------------------------------------------------------------- characteristic-wise leg
+
+def run_charwise_leg(args, mech, case, prim, dev):
+    """The same workload with characteristic-wise splitting (RF_CHARWISE), WENO3-Z and
+    TENO6, mixed and FP64."""
+    from paper_2202_02319_b300 import native as nv
+    return {"weno3z": run_teno_leg(args, mech, case, prim, dev, nv.RF_CHARWISE, args.charwise_steps),
+            "teno6": run_teno_leg(args, mech, case, prim, dev, nv.RF_CHARWISE | nv.RF_TENO6, args.charwise_steps)}
 
 
 # ----------------------------------------------------------------------------- NSCBC leg
@@ -749,6 +766,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--teno-steps", type=int, default=4)
+    ap.add_argument("--charwise-steps", type=int, default=2)
     ap.add_argument("--mapped-steps", type=int, default=4)
     ap.add_argument("--mapped-n", type=int, default=192)
     ap.add_argument("--nscbc-steps", type=int, default=10)
@@ -764,13 +782,19 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=20)
     ap.add_argument("--adjoint-members", type=int, default=1)
     ap.add_argument("--adjoint-ck", type=int, default=0, help="checkpoint interval (0: half the steps)")
-    ap.add_argument("--leg", default=None, choices=["mapped", "nscbc"],
+    ap.add_argument("--leg", default=None, choices=["mapped", "nscbc", "charwise"],
                     help="run only this leg and print its result (for profiling its kernels)")
     args = ap.parse_args()
     if args.leg is not None:
         import torch
         dev = torch.device("cuda")
-        leg = run_mapped_leg(args, dev) if args.leg == "mapped" else run_nscbc_leg(args, dev)
+        if args.leg == "charwise":
+            from paper_2202_02319_b300 import native as nv, synth
+            case = synth.case_jet(0, args.n, device=dev)
+            prim = case.prim.reshape(5 + case.mech.n_species, case.grid.ncells).contiguous()
+            leg = run_charwise_leg(args, nv.init_mechanism(case.mech), case, prim, dev)
+        else:
+            leg = run_mapped_leg(args, dev) if args.leg == "mapped" else run_nscbc_leg(args, dev)
         print(json.dumps({"leg": args.leg, **leg}))
     elif args.impl == "reference":
         run_reference(args)

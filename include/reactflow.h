@@ -97,7 +97,18 @@ enum rf_flags {           /* term switches for tests (0 = full method) and the s
                              scheme (global-memory sweeps), NSCBC axes included; ensembles run
                              mapped members in the member loop (mode 0) only; rejected by
                              rf_rhs_noalloc and the adjoint entry points */
-    RF_FLAGS_ALL = 63
+    RF_CHARWISE = 64,     /* characteristic-wise flux splitting (Methods, Numerical method: the
+                             optional reconstruction of characteristic instead of conserved
+                             variables) with the scheme RF_TENO6 selects: the split fluxes of
+                             each face's stencil projected on the left eigenvectors of the
+                             multicomponent Euler flux Jacobian at the face (arithmetic means of
+                             the two adjacent cells' Y_s, u, dp/d(rho_s), gamma - 1 and H),
+                             reconstructed field by field (WENO3-Z eps from the components a
+                             field is made of) and projected back.  Cartesian grids; single-grid
+                             RHS and RK steps in both precisions (global-memory sweeps);
+                             rejected with RF_MAPPED or an NSCBC axis by rf_create_ctx, and by
+                             rf_rhs_noalloc, rf_ensemble_create and the adjoint entry points */
+    RF_FLAGS_ALL = 127
 };
 
 /* Mechanism description (host arrays, copied by rf_init_mechanism).

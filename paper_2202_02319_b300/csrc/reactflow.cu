@@ -490,6 +490,12 @@ extern "C" int rf_create_ctx(const rf_mech *m, const rf_grid_desc *g, int precis
     }
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_create_ctx: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_create_ctx: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
+    if (flags & RF_CHARWISE) {
+        if (flags & RF_MAPPED) return fail(RF_EINVAL, "rf_create_ctx: RF_CHARWISE is built for Cartesian grids, not RF_MAPPED ones");
+        for (int a = 0; a < 3; ++a)
+            if (g->bc[a] == RF_BC_NSCBC)
+                return fail(RF_EINVAL, "rf_create_ctx: RF_CHARWISE with an NSCBC axis (%d) is not built", a);
+    }
     int mslot = 0;
     {
         int rc = mech_slot(m, &mslot);
@@ -727,6 +733,8 @@ struct Path {
         constexpr int NV = NS + 4;
         if (c->flags & RF_MAPPED)
             return (c->flags & RF_TENO6) ? sweep_global<MODE, 1, 1>(c, m, dir, s) : sweep_global<MODE, 0, 1>(c, m, dir, s);
+        if (c->flags & RF_CHARWISE)
+            return (c->flags & RF_TENO6) ? sweep_global<MODE, 3, 0>(c, m, dir, s) : sweep_global<MODE, 2, 0>(c, m, dir, s);
         if (c->flags & RF_TENO6) return sweep_teno<MODE>(c, m, dir, s);
         if (dir == 0 && sizeof(R) == 4) {
             // staged x sweep: a row per warp, four rows per block
@@ -1436,6 +1444,10 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
             delete e;
             return fail(RF_EINVAL, "rf_ensemble_create: member %d uses TENO6; batched ensembles run WENO3-Z", i);
         }
+        if (c->flags & RF_CHARWISE) {
+            delete e;
+            return fail(RF_EINVAL, "rf_ensemble_create: member %d uses RF_CHARWISE; batched ensembles run the component-wise splitting", i);
+        }
         if (i == 0) {
             e->mech = c->mech;
             e->mslot = c->mslot;
@@ -1682,6 +1694,7 @@ struct AdjWs {
 
 static int adj_ws(rf_ctx *c, AdjWs &w) {
     if (c->flags & RF_TENO6) return fail(RF_EINVAL, "the discrete adjoint is built for WENO3-Z, not TENO6");
+    if (c->flags & RF_CHARWISE) return fail(RF_EINVAL, "the discrete adjoint is built for the component-wise splitting, not RF_CHARWISE");
     if (c->flags & RF_MAPPED) return fail(RF_EINVAL, "the discrete adjoint is built for Cartesian grids, not RF_MAPPED ones");
     for (int a = 0; a < 3; ++a)
         if (c->g.bc[a] == RF_BC_NSCBC) return fail(RF_EINVAL, "the discrete adjoint is built for periodic and zero-gradient axes, not NSCBC (axis %d)", a);
@@ -1984,6 +1997,7 @@ extern "C" int rf_rhs_noalloc(const rf_mech *m, const rf_grid_desc *g, int preci
     if (precision != RF_FP64 && precision != RF_MIXED) return fail(RF_EINVAL, "rf_rhs_noalloc: precision %d unknown", precision);
     if (flags & ~(uint32_t)RF_FLAGS_ALL) return fail(RF_EINVAL, "rf_rhs_noalloc: unknown flag bits 0x%x", flags & ~(uint32_t)RF_FLAGS_ALL);
     if (flags & RF_MAPPED) return fail(RF_EINVAL, "rf_rhs_noalloc: RF_MAPPED needs a context (rf_set_nodes)");
+    if (flags & RF_CHARWISE) return fail(RF_EINVAL, "rf_rhs_noalloc: RF_CHARWISE runs through a context");
     const long long n = (long long)g->nx * g->ny * g->nz;
     const int ns = m->ns, nv = ns + 4, nq = Q_X0 + 3 * ns;
     const size_t rsize = precision == RF_FP64 ? sizeof(double) : sizeof(float);

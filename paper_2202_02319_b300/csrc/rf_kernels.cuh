@@ -735,13 +735,14 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 6 : 5) cell_state_kernel
 // omega_0 = d0 b1 (b0 + t) / (d0 b1 (b0 + t) + d1 b0 (b1 + t)) with b_k = (beta_k + eps) / S,
 // t = tau / S.  Every scaled quantity lies in [0, 2], so the weights cannot overflow
 // even in FP32 (values up to |f| ~ 1e19 there).
+// weno3z_eps takes eps itself (the characteristic-wise splitting forms it from the
+// components a field is made of).
 template <typename R>
-__device__ __forceinline__ R weno3z(R a, R b, R c, R e2) {
+__device__ __forceinline__ R weno3z_eps(R a, R b, R c, R eps) {
     const R q0 = fma(R(-0.5), a, R(1.5) * b);
     const R q1 = R(0.5) * b + R(0.5) * c;
     const R d0 = b - a, d1 = c - b;
     const R beta0 = d0 * d0, beta1 = d1 * d1;
-    const R eps = fma(e2, fma(a, a, fma(b, b, c * c)), R(EPS_WENO));
     const R iS = rcp(beta0 + beta1 + R(2) * eps);
     const R b0 = (beta0 + eps) * iS, b1 = (beta1 + eps) * iS;
     const R t = fabs(beta1 - beta0) * iS;
@@ -765,10 +766,9 @@ __device__ __forceinline__ double rcp_face(double x) { return rcp64(x); }
 // omega0 q0 + omega1 q1 = q1 + omega0 (d0 - d1)/2.  S >= 2 eps and a0 + a1 >= 1/12 are
 // normal, so the SFU reciprocals apply.
 template <>
-__device__ __forceinline__ float weno3z<float>(float a, float b, float c, float e2) {
+__device__ __forceinline__ float weno3z_eps<float>(float a, float b, float c, float eps) {
     const float d0 = b - a, d1 = c - b;
     const float beta0 = d0 * d0, beta1 = d1 * d1;
-    const float eps = fmaf(e2, fmaf(a, a, fmaf(b, b, c * c)), (float)EPS_WENO);
     const float iS = rcp_approx((beta0 + beta1) + 2.0f * eps);
     const float eS = eps * iS;
     const float b0 = fmaf(beta0, iS, eS), b1 = fmaf(beta1, iS, eS);
@@ -784,10 +784,9 @@ __device__ __forceinline__ float weno3z<float>(float a, float b, float c, float 
 // of S, read from its bits): no rounding, and no division.  a0 + a1 lies in [1/12, 4],
 // so the one remaining reciprocal is the Newton-Raphson rcp64.
 template <>
-__device__ __forceinline__ double weno3z<double>(double a, double b, double c, double e2) {
+__device__ __forceinline__ double weno3z_eps<double>(double a, double b, double c, double eps) {
     const double d0 = b - a, d1 = c - b;
     const double beta0 = d0 * d0, beta1 = d1 * d1;
-    const double eps = fma(e2, fma(a, a, fma(b, b, c * c)), EPS_WENO);
     const double S = (beta0 + beta1) + 2.0 * eps;
     const double iS = __hiloint2double((2046 - ((__double2hiint(S) >> 20) & 0x7ff)) << 20, 0);
     const double eS = eps * iS;
@@ -797,6 +796,18 @@ __device__ __forceinline__ double weno3z<double>(double a, double b, double c, d
     const double a1 = (2.0 / 3.0) * (b0 * (b1 + t));
     const double om0 = a0 * rcp64(a0 + a1);
     return fma(om0, 0.5 * (d0 - d1), fma(0.5, d1, b));
+}
+
+// WENO3-Z with the grid-scaled eps = e2 (a^2 + b^2 + c^2) + EPS_WENO.
+__device__ __forceinline__ float weno3z_e2(float a, float b, float c, float e2) {
+    return weno3z_eps<float>(a, b, c, fmaf(e2, fmaf(a, a, fmaf(b, b, c * c)), (float)EPS_WENO));
+}
+__device__ __forceinline__ double weno3z_e2(double a, double b, double c, double e2) {
+    return weno3z_eps<double>(a, b, c, fma(e2, fma(a, a, fma(b, b, c * c)), EPS_WENO));
+}
+template <typename R>
+__device__ __forceinline__ R weno3z(R a, R b, R c, R e2) {
+    return weno3z_e2(a, b, c, e2);
 }
 
 // ----------------------------------------------------------------------------- TENO6
@@ -1165,6 +1176,254 @@ __device__ __forceinline__ void face_flux_teno(const Member &m, const UT *__rest
     face_visc<R, NS, DIR, true>(m, in, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
 }
 
+// ----------------------------------------------------------------------------- characteristic-wise splitting
+
+// Characteristic-wise LLF splitting on Cartesian grids (Methods, Numerical method: the
+// reconstruction of characteristic instead of conserved variables, the scheme's
+// optional variant).  The eigensystem of dF_n/dU of the multicomponent Euler system is
+// taken at the face from the arithmetic means of the two adjacent cells' Y_s, u,
+// phi_s, b and H, with
+//   b = gamma - 1 = rho c^2 / p - 1,  phi_s = dp/d(rho_s) = R_s T - b (e_s - |u|^2 / 2),
+//   H = (E + p) / rho,  c^2 = sum_s Y_s phi_s + b (H - |u|^2)  (the face's closure).
+// For a vector (r_s, m, E) with r = sum_s r_s and dp = sum_s phi_s r_s - b u . m + b E
+// the left eigenvectors give
+//   u -+ c:  (dp -+ c (m_n - u_n r)) / (2 c^2),  species s:  r_s - Y_s dp / c^2,
+//   tangential axis t:  m_t - u_t r,
+// and the right eigenvectors (columns) are (Y_s, u -+ c n, H -+ u_n c) for u -+ c,
+// (e_s, u, |u|^2 - phi_s / b) for species s and (0, t, u_t) for axis t.  The split
+// fluxes f+- = ((u_n +- alpha) U + p (n + u_n e_E)) / 2 project as
+// ((u_n +- alpha) w_U + p (l_mn + u_n l_E)) / 2, w_U the projection of the conserved
+// vector, so each field's stencil values come from three per-cell scalars (r, dp of
+// U, m_n - u_n r) and one component.  WENO3-Z gives field k the eps
+// (h^2 / 3) sum_j l_kj^2 sum over its three values of f_j^2 (+ EPS_WENO): the
+// component-wise eps when l is the identity; TENO6 keeps its fixed eps.
+
+template <typename R, int NS, int DIR, int K, class S>
+__device__ __forceinline__ void face_invisc_char(const MechDev &M, const Member &m, const S &st, R (&G)[NS + 4],
+                                                 R &rhoL, R &rhoR) {
+    constexpr int NV = NS + 4;
+    constexpr int OL = K / 2 - 1, OR = K / 2;
+    constexpr int TA = DIR == 0 ? 1 : 0, TB = DIR == 2 ? 1 : 2;     // tangential axes, increasing
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = 0;
+    rhoL = 0;
+    rhoR = 0;
+    if (m.flags & F_NO_INVISCID) return;
+    R un[K], pp[K], rho[K];
+    R alpha = 0;
+#pragma unroll
+    for (int o = 0; o < K; ++o) {
+        un[o] = st.q(Q_U + DIR, o);
+        pp[o] = st.q(Q_P, o);
+        const R lam = fabs(un[o]) + st.q(Q_C, o);
+        alpha = lam > alpha ? lam : alpha;
+        R r = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) r += st.u(s, o);
+        rho[o] = r;
+    }
+    rhoL = rho[OL];
+    rhoR = rho[OR];
+    // face means of Y_s, u, phi_s, b, H over the two adjacent cells
+    R Y[NS], phi[NS], u[3], b = 0, H = 0;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) Y[s] = phi[s] = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = 0;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int o = side == 0 ? OL : OR;
+        const R ir = R(1) / rho[o];
+        const R co = st.q(Q_C, o), To = st.q(Q_T, o);
+        const R uo[3] = {st.q(Q_U, o), st.q(Q_V, o), st.q(Q_W, o)};
+        const R ke = R(0.5) * (uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2]);
+        const R bo = rho[o] * co * co / pp[o] - R(1);
+        b += R(0.5) * bo;
+        H += R(0.5) * (st.u(NS + 3, o) + pp[o]) * ir;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) u[k] += R(0.5) * uo[k];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const R RT = mech_RW<R>(M, s) * To;
+            const R es = st.q(QL<NS>::H + s, o) - RT;          // e_s = h_s - R_s T
+            Y[s] += R(0.5) * (st.u(s, o) * ir);
+            phi[s] += R(0.5) * (RT - bo * (es - ke));
+        }
+    }
+    const R u2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    R c2 = b * (H - u2);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) c2 = fma(Y[s], phi[s], c2);
+    const R c = sqrt(c2);
+    const R ic2 = R(1) / c2, h2 = R(0.5) * ic2;
+    const R unf = u[DIR];
+    // per-cell scalars of the projection: dp of U with the face's phi, b, u, and m_n - u_n r
+    R dp[K], mn[K];
+#pragma unroll
+    for (int o = 0; o < K; ++o) {
+        R d = 0;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) d = fma(phi[s], st.u(s, o), d);
+        const R um = u[0] * st.u(NS, o) + u[1] * st.u(NS + 1, o) + u[2] * st.u(NS + 2, o);
+        dp[o] = fma(b, st.u(NS + 3, o) - um, d);
+        mn[o] = fma(-unf, rho[o], st.u(NS + DIR, o));
+    }
+    // WENO3-Z: sums of the squared component split fluxes over each side's three values
+    R gp[NV], gm[NV];
+    if (K == 4) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            R sp = 0, sm = 0;
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                const R Uv = st.u(v, o);
+                R extra = 0;
+                if (v == NS + DIR) extra = R(0.5) * pp[o];
+                if (v == NS + 3) extra = R(0.5) * pp[o] * un[o];
+                const R fpv = fma(R(0.5) * (un[o] + alpha), Uv, extra);
+                const R fmv = fma(R(0.5) * (un[o] - alpha), Uv, extra);
+                if (o <= 2) sp = fma(fpv, fpv, sp);
+                if (o >= 1) sm = fma(fmv, fmv, sm);
+            }
+            gp[v] = sp;
+            gm[v] = sm;
+        }
+    }
+    const R e2 = (R)m.weps[DIR];
+    // reconstruction of one field from its projected U values wU[o] and face
+    // coefficients lmn, lE; returns the sum of the f+ and f- reconstructions
+    auto recon = [&](const R (&wU)[K], R lmn, R lE, R epsp, R epsm) -> R {
+        R wp[K], wm[K];
+#pragma unroll
+        for (int o = 0; o < K; ++o) {
+            const R extra = R(0.5) * pp[o] * fma(un[o], lE, lmn);
+            wp[o] = fma(R(0.5) * (un[o] + alpha), wU[o], extra);
+            wm[o] = fma(R(0.5) * (un[o] - alpha), wU[o], extra);
+        }
+        if (K == 6)
+            return teno6<R>(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5]) + teno6<R>(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0]);
+        return weno3z_eps<R>(wp[0], wp[1], wp[2], epsp) + weno3z_eps<R>(wm[K - 1], wm[K - 2], wm[K - 3], epsm);
+    };
+    R F[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = 0;
+    // acoustic fields u - c (sg = -1) and u + c (sg = +1)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const R sg = a == 0 ? R(-1) : R(1);
+        R wU[K];
+#pragma unroll
+        for (int o = 0; o < K; ++o) wU[o] = fma(sg * c, mn[o], dp[o]) * h2;
+        const R lmn = fma(-b, unf, sg * c) * h2, lE = b * h2;
+        R ep = 0, em = 0;
+        if (K == 4) {
+            R sp = 0, sm = 0;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                const R l = fma(-sg * c, unf, phi[s]) * h2;
+                sp = fma(l * l, gp[s], sp);
+                sm = fma(l * l, gm[s], sm);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const R l = (k == DIR ? fma(-b, u[k], sg * c) : -b * u[k]) * h2;
+                sp = fma(l * l, gp[NS + k], sp);
+                sm = fma(l * l, gm[NS + k], sm);
+            }
+            sp = fma(lE * lE, gp[NS + 3], sp);
+            sm = fma(lE * lE, gm[NS + 3], sm);
+            ep = fma(e2, sp, R(EPS_WENO));
+            em = fma(e2, sm, R(EPS_WENO));
+        }
+        const R w = recon(wU, lmn, lE, ep, em);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) F[s] = fma(Y[s], w, F[s]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) F[NS + k] = fma(k == DIR ? u[k] + sg * c : u[k], w, F[NS + k]);
+        F[NS + 3] = fma(fma(sg * unf, c, H), w, F[NS + 3]);
+    }
+    // species fields
+    const R yb = b * ic2;
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        const R yc = Y[s] * ic2;
+        R wU[K];
+#pragma unroll
+        for (int o = 0; o < K; ++o) wU[o] = fma(-yc, dp[o], st.u(s, o));
+        const R lmn = Y[s] * yb * unf, lE = -Y[s] * yb;
+        R ep = 0, em = 0;
+        if (K == 4) {
+            R sp = 0, sm = 0;
+#pragma unroll
+            for (int q = 0; q < NS; ++q) {
+                const R l = (q == s ? R(1) : R(0)) - yc * phi[q];
+                sp = fma(l * l, gp[q], sp);
+                sm = fma(l * l, gm[q], sm);
+            }
+            const R ly = Y[s] * yb;
+            R gmp = gp[NS + 3], gmm = gm[NS + 3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gmp = fma(u[k] * u[k], gp[NS + k], gmp);
+                gmm = fma(u[k] * u[k], gm[NS + k], gmm);
+            }
+            sp = fma(ly * ly, gmp, sp);
+            sm = fma(ly * ly, gmm, sm);
+            ep = fma(e2, sp, R(EPS_WENO));
+            em = fma(e2, sm, R(EPS_WENO));
+        }
+        const R w = recon(wU, lmn, lE, ep, em);
+        F[s] += w;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) F[NS + k] = fma(u[k], w, F[NS + k]);
+        F[NS + 3] = fma(u2 - phi[s] / b, w, F[NS + 3]);
+    }
+    // tangential fields
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int t = j == 0 ? TA : TB;
+        R wU[K];
+#pragma unroll
+        for (int o = 0; o < K; ++o) wU[o] = fma(-u[t], rho[o], st.u(NS + t, o));
+        R ep = 0, em = 0;
+        if (K == 4) {
+            R sp = gp[NS + t], sm = gm[NS + t], rp = 0, rm = 0;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                rp += gp[s];
+                rm += gm[s];
+            }
+            sp = fma(u[t] * u[t], rp, sp);
+            sm = fma(u[t] * u[t], rm, sm);
+            ep = fma(e2, sp, R(EPS_WENO));
+            em = fma(e2, sm, R(EPS_WENO));
+        }
+        const R w = recon(wU, R(0), R(0), ep, em);
+        F[NS + t] += w;
+        F[NS + 3] = fma(u[t], w, F[NS + 3]);
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) G[v] = -F[v];
+}
+
+// Face flux with characteristic-wise splitting from global memory (TENO: TENO6 on a
+// six-cell stencil, else WENO3-Z); the viscous part as in the component-wise scheme.
+template <typename R, typename UT, int NS, int DIR, bool TENO>
+__device__ __forceinline__ void face_flux_char(const MechDev &M, const Member &m, const UT *__restrict__ U,
+                                               const R *__restrict__ Q, const int (&cc)[3], R (&G)[NS + 4]) {
+    R rhoL, rhoR;
+    if (TENO) {
+        const GlobalStencil6<R, UT, DIR> st(m, U, Q, cc);
+        face_invisc_char<R, NS, DIR, 6>(M, m, st, G, rhoL, rhoR);
+        const InnerFour<GlobalStencil6<R, UT, DIR>> in{st};
+        face_visc<R, NS, DIR, true>(m, in, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
+    } else {
+        const GlobalStencil<R, UT, DIR> st(m, U, Q, cc);
+        face_invisc_char<R, NS, DIR, 4>(M, m, st, G, rhoL, rhoR);
+        face_visc<R, NS, DIR, true>(m, st, G, rhoL, rhoR, !(m.flags & F_NO_INVISCID));
+    }
+}
+
 template <typename R, int NS>
 __device__ __forceinline__ void face_join(const Member &m, const R (&D)[NS + 4], R (&G)[NS + 4]) {
     if (m.flags & F_NO_VISCOUS) return;
@@ -1495,6 +1754,7 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
             R G[NV];
             const int cc[3] = {f, j, k};
             if (GEOM) face_flux_mapped<R, UT, NS, 0, SCHEME>(m, U, Q, cc, G);
+            else if (SCHEME >= 2) face_flux_char<R, UT, NS, 0, SCHEME == 3>(M, m, U, Q, cc, G);
             else if (SCHEME == 1) face_flux_teno<R, UT, NS, 0>(m, U, Q, cc, G);
             else face_flux<R, UT, NS, 0>(m, U, Q, cc, G);
 #pragma unroll
@@ -1521,7 +1781,8 @@ __device__ __forceinline__ void sweep_x_block(const MechDev &M, const Member &m,
     }
 }
 
-// SCHEME 0: WENO3-Z, 1: TENO6; GEOM 1: mapped grid
+// SCHEME 0: WENO3-Z, 1: TENO6, 2 / 3: WENO3-Z / TENO6 characteristic-wise (Cartesian
+// only); GEOM 1: mapped grid
 template <typename R, typename UT, int NS, int MODE, int SCHEME = 0, int GEOM = 0>
 __global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_constant__ Member m,
                                                       int W, int rpb) {
@@ -1557,6 +1818,7 @@ __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member 
     for (int c = c0 - 1; c < c1; ++c) {
         cc[DIR] = c + 1;
         if (GEOM) face_flux_mapped<R, UT, NS, DIR, SCHEME>(m, U, Q, cc, Gn);
+        else if (SCHEME >= 2) face_flux_char<R, UT, NS, DIR, SCHEME == 3>(M, m, U, Q, cc, Gn);
         else if (SCHEME == 1) face_flux_teno<R, UT, NS, DIR>(m, U, Q, cc, Gn);
         else face_flux<R, UT, NS, DIR>(m, U, Q, cc, Gn);
         if (c >= c0) {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libr
 
 RF_OK, RF_EINVAL, RF_ENEWTON, RF_ENONFINITE, RF_ERANGE, RF_ECUDA, RF_ETIMEOUT, RF_ENOMEM = 0, -1, -2, -3, -4, -5, -6, -7
 RF_FP64, RF_MIXED = 0, 1
-RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER, RF_TENO6, RF_MAPPED = 1, 2, 4, 8, 16, 32
+RF_NO_INVISCID, RF_NO_VISCOUS, RF_NO_CHEMISTRY, RF_NO_LASER, RF_TENO6, RF_MAPPED, RF_CHARWISE = 1, 2, 4, 8, 16, 32, 64
 RF_BC_PERIODIC, RF_BC_EXTRAPOLATE, RF_BC_NSCBC = 0, 1, 2
 CODE_NAMES = {0: "RF_OK", -1: "RF_EINVAL", -2: "RF_ENEWTON", -3: "RF_ENONFINITE", -4: "RF_ERANGE",
               -5: "RF_ECUDA", -6: "RF_ETIMEOUT", -7: "RF_ENOMEM"}

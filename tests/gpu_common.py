@@ -91,13 +91,14 @@ def rel_inf(a, b):
 def rel_inf_group(a, b, ns):
     """Per-variable ||a_v - b_v||_inf over the largest |b| of the variable's group
     (species, momentum, energy), as a numpy vector: a variable whose values are all
-    tiny (a species nothing produces yet) is measured against its group's scale."""
+    tiny (a species nothing produces yet) is measured against its group's scale
+    (0/0 -> 0)."""
     a = a.reshape(a.shape[0], -1).double().cpu()
     b = b.reshape(b.shape[0], -1).double().cpu()
     num = (a - b).abs().amax(1)
     m = b.abs().amax(1)
     scale = torch.cat([m[:ns].max().repeat(ns), m[ns:ns + 3].max().repeat(3), m[ns + 3:]])
-    return (num / scale).numpy()
+    return torch.where(scale > 0, num / torch.where(scale > 0, scale, torch.ones_like(scale)), num).numpy()
 
 
 def rel_l2(a, b):

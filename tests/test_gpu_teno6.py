@@ -120,4 +120,4 @@ def test_teno6_is_rejected_where_unsupported():
     with pytest.raises(RuntimeError, match="TENO6"):
         nv.adjoint_rhs(ctx, U, T, 0.0, case.laser.as_tuple(), lam, 0.0, lam.clone(), grads)
     with pytest.raises(RuntimeError):
-        nv.create_ctx(mech, case.grid, nv.RF_FP64, 64)
+        nv.create_ctx(mech, case.grid, nv.RF_FP64, 128)          # no such flag bit

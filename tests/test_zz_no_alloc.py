@@ -70,3 +70,14 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     rc = f(mech.handle, ctypes.byref(gd), 0, 0, dummy.data_ptr(), dummy.data_ptr(), 0.0, None, dummy.data_ptr(),
            torch.cuda.current_stream().cuda_stream)
     assert rc == nv.RF_EINVAL and "maximum" in nv.last_error()
+
+
+def test_noalloc_rejects_charwise():
+    """RF_CHARWISE runs through a context only."""
+    nv, f = _lib()
+    mech = nv.init_mechanism(synth.mechanism_9sp(0))
+    gd = nv.GridDesc(8, 8, 8, 1e-4, 1e-4, 1e-4, (ctypes.c_int * 3)(0, 0, 0))
+    dummy = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rc = f(mech.handle, ctypes.byref(gd), 0, nv.RF_CHARWISE, dummy.data_ptr(), dummy.data_ptr(), 0.0, None,
+           dummy.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    assert rc == nv.RF_EINVAL and "RF_CHARWISE" in nv.last_error()
