@@ -698,14 +698,17 @@ struct Path {
     template <int MODE, int SCHEME, int GEOM>
     static int sweep_global(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
+        // the FP32 characteristic-wise sweeps run in their own register-capped kernels
+        constexpr bool charf = SCHEME >= 2 && sizeof(R) == 4 && GEOM == 0;
         if (dir == 0) {
             const int nx = c->g.nx;
+            const int xb = charf ? std::min(c->x_block, 128) : c->x_block;
             int W, rpb;
-            if (nx <= c->x_block) {
+            if (nx <= xb) {
                 W = nx;
-                rpb = std::max(1, std::min(c->x_block / nx, 320 / (nx + 2)));
+                rpb = std::max(1, std::min(xb / nx, 320 / (nx + 2)));
             } else {
-                W = c->x_block;
+                W = xb;
                 rpb = 1;
             }
             const int threads = ((W * rpb + 31) / 32) * 32;
@@ -713,13 +716,21 @@ struct Path {
             const int blocks = (nrows + rpb - 1) / rpb;
             const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
             ProfScope ps(c, PROF_SWEEP_X, s);
-            sweep_x_kernel<R, UT, NS, MODE, SCHEME, GEOM><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+            if constexpr (charf)
+                sweep_x_char_kernel<UT, NS, MODE, SCHEME><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+            else
+                sweep_x_kernel<R, UT, NS, MODE, SCHEME, GEOM><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
         } else {
             const int nd = dir == 1 ? c->g.ny : c->g.nz;
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             dim3 grid((unsigned)((lines + c->walk_block - 1) / c->walk_block), (unsigned)((nd + c->walk_seg - 1) / c->walk_seg));
             ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
-            if (dir == 1)
+            if constexpr (charf) {
+                if (dir == 1)
+                    sweep_walk_char_kernel<UT, NS, 1, MODE, SCHEME><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+                else
+                    sweep_walk_char_kernel<UT, NS, 2, MODE, SCHEME><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+            } else if (dir == 1)
                 sweep_walk_kernel<R, UT, NS, 1, MODE, SCHEME, GEOM><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
             else
                 sweep_walk_kernel<R, UT, NS, 2, MODE, SCHEME, GEOM><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);

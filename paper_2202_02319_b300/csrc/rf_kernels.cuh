@@ -1304,9 +1304,7 @@ __device__ __forceinline__ void face_invisc_char(const MechDev &M, const Member 
             return teno6<R>(wp[0], wp[1], wp[2], wp[3], wp[4], wp[5]) + teno6<R>(wm[5], wm[4], wm[3], wm[2], wm[1], wm[0]);
         return weno3z_eps<R>(wp[0], wp[1], wp[2], epsp) + weno3z_eps<R>(wm[K - 1], wm[K - 2], wm[K - 3], epsm);
     };
-    R F[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] = 0;
+    // G = -F accumulates -w times each right eigenvector
     // acoustic fields u - c (sg = -1) and u + c (sg = +1)
 #pragma unroll
     for (int a = 0; a < 2; ++a) {
@@ -1335,15 +1333,32 @@ __device__ __forceinline__ void face_invisc_char(const MechDev &M, const Member 
             ep = fma(e2, sp, R(EPS_WENO));
             em = fma(e2, sm, R(EPS_WENO));
         }
-        const R w = recon(wU, lmn, lE, ep, em);
+        const R w = -recon(wU, lmn, lE, ep, em);
 #pragma unroll
-        for (int s = 0; s < NS; ++s) F[s] = fma(Y[s], w, F[s]);
+        for (int s = 0; s < NS; ++s) G[s] = fma(Y[s], w, G[s]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) F[NS + k] = fma(k == DIR ? u[k] + sg * c : u[k], w, F[NS + k]);
-        F[NS + 3] = fma(fma(sg * unf, c, H), w, F[NS + 3]);
+        for (int k = 0; k < 3; ++k) G[NS + k] = fma(k == DIR ? u[k] + sg * c : u[k], w, G[NS + k]);
+        G[NS + 3] = fma(fma(sg * unf, c, H), w, G[NS + 3]);
     }
-    // species fields
+    // species fields; their eps sums sum_q (delta_qs - Y_s phi_q / c^2)^2 g_q as
+    // g_s (1 - Y_s phi_s / c^2)^2 + (Y_s / c^2)^2 (A - phi_s^2 g_s), A = sum_q phi_q^2 g_q
     const R yb = b * ic2;
+    R Ap = 0, Am = 0, gvp = 0, gvm = 0;
+    if (K == 4) {
+#pragma unroll
+        for (int q = 0; q < NS; ++q) {
+            const R p2 = phi[q] * phi[q];
+            Ap = fma(p2, gp[q], Ap);
+            Am = fma(p2, gm[q], Am);
+        }
+        gvp = gp[NS + 3];
+        gvm = gm[NS + 3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            gvp = fma(u[k] * u[k], gp[NS + k], gvp);
+            gvm = fma(u[k] * u[k], gm[NS + k], gvm);
+        }
+    }
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         const R yc = Y[s] * ic2;
@@ -1353,30 +1368,18 @@ __device__ __forceinline__ void face_invisc_char(const MechDev &M, const Member 
         const R lmn = Y[s] * yb * unf, lE = -Y[s] * yb;
         R ep = 0, em = 0;
         if (K == 4) {
-            R sp = 0, sm = 0;
-#pragma unroll
-            for (int q = 0; q < NS; ++q) {
-                const R l = (q == s ? R(1) : R(0)) - yc * phi[q];
-                sp = fma(l * l, gp[q], sp);
-                sm = fma(l * l, gm[q], sm);
-            }
-            const R ly = Y[s] * yb;
-            R gmp = gp[NS + 3], gmm = gm[NS + 3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                gmp = fma(u[k] * u[k], gp[NS + k], gmp);
-                gmm = fma(u[k] * u[k], gm[NS + k], gmm);
-            }
-            sp = fma(ly * ly, gmp, sp);
-            sm = fma(ly * ly, gmm, sm);
+            const R l = fma(-yc, phi[s], R(1)), ly = Y[s] * yb, p2 = phi[s] * phi[s];
+            const R rp = fmax(fma(-p2, gp[s], Ap), R(0)), rm = fmax(fma(-p2, gm[s], Am), R(0));
+            const R sp = fma(l * l, gp[s], fma(yc * yc, rp, ly * ly * gvp));
+            const R sm = fma(l * l, gm[s], fma(yc * yc, rm, ly * ly * gvm));
             ep = fma(e2, sp, R(EPS_WENO));
             em = fma(e2, sm, R(EPS_WENO));
         }
-        const R w = recon(wU, lmn, lE, ep, em);
-        F[s] += w;
+        const R w = -recon(wU, lmn, lE, ep, em);
+        G[s] += w;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) F[NS + k] = fma(u[k], w, F[NS + k]);
-        F[NS + 3] = fma(u2 - phi[s] / b, w, F[NS + 3]);
+        for (int k = 0; k < 3; ++k) G[NS + k] = fma(u[k], w, G[NS + k]);
+        G[NS + 3] = fma(u2 - phi[s] / b, w, G[NS + 3]);
     }
     // tangential fields
 #pragma unroll
@@ -1398,12 +1401,10 @@ __device__ __forceinline__ void face_invisc_char(const MechDev &M, const Member 
             ep = fma(e2, sp, R(EPS_WENO));
             em = fma(e2, sm, R(EPS_WENO));
         }
-        const R w = recon(wU, R(0), R(0), ep, em);
-        F[NS + t] += w;
-        F[NS + 3] = fma(u[t], w, F[NS + 3]);
+        const R w = -recon(wU, R(0), R(0), ep, em);
+        G[NS + t] += w;
+        G[NS + 3] = fma(u[t], w, G[NS + 3]);
     }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) G[v] = -F[v];
 }
 
 // Face flux with characteristic-wise splitting from global memory (TENO: TENO6 on a
@@ -1791,6 +1792,15 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_co
     sweep_x_block<R, UT, NS, MODE, SCHEME, GEOM>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
 
+// The FP32 characteristic-wise x sweep (SCHEME 2, 3 on a Cartesian grid) in blocks of
+// at most 128 threads, held to 168 registers for three blocks per SM.
+template <typename UT, int NS, int MODE, int SCHEME>
+__global__ void __launch_bounds__(128, 3) sweep_x_char_kernel(int mslot, const __grid_constant__ Member m, int W, int rpb) {
+    const MechDev &M = c_mech[mslot];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    sweep_x_block<float, UT, NS, MODE, SCHEME, 0>(M, m, blockIdx.x, W, rpb, smem_raw);
+}
+
 // y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
 template <typename R, typename UT, int NS, int DIR, int MODE, int SCHEME = 0, int GEOM = 0>
 __device__ __forceinline__ void sweep_walk_block(const MechDev &M, const Member &m, long long lblk, int sblk, int seg) {
@@ -1838,6 +1848,15 @@ __global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid
                                                          int seg) {
     const MechDev &M = c_mech[mslot];
     sweep_walk_block<R, UT, NS, DIR, MODE, SCHEME, GEOM>(M, m, blockIdx.x, blockIdx.y, seg);
+}
+
+// The FP32 characteristic-wise y / z sweeps (SCHEME 2, 3 on a Cartesian grid): latency-
+// bound on their global loads, so held to 168 registers for three blocks per SM (they
+// spill 80 / 112 bytes to L1).
+template <typename UT, int NS, int DIR, int MODE, int SCHEME>
+__global__ void __launch_bounds__(128, 3) sweep_walk_char_kernel(int mslot, const __grid_constant__ Member m, int seg) {
+    const MechDev &M = c_mech[mslot];
+    sweep_walk_block<float, UT, NS, DIR, MODE, SCHEME, 0>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
 // ----------------------------------------------------------------------------- staged y / z sweep (FP32 bulk)
