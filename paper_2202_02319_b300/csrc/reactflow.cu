@@ -698,11 +698,13 @@ struct Path {
     template <int MODE, int SCHEME, int GEOM>
     static int sweep_global(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
-        // the FP32 characteristic-wise sweeps run in their own register-capped kernels
-        constexpr bool charf = SCHEME >= 2 && sizeof(R) == 4 && GEOM == 0;
+        // FP32 sweeps in register-capped kernels of 128-thread blocks, CAP blocks per SM:
+        // characteristic-wise 3 (168 registers, 80 / 112 bytes of spills), mapped 3
+        // (168, up to 28 bytes), TENO6 5 (96, 52 bytes)
+        constexpr int CAP = sizeof(R) != 4 ? 0 : (SCHEME >= 2 ? 3 : (GEOM ? 3 : (SCHEME == 1 ? 5 : 0)));
         if (dir == 0) {
             const int nx = c->g.nx;
-            const int xb = charf ? std::min(c->x_block, 128) : c->x_block;
+            const int xb = CAP ? std::min(c->x_block, 128) : c->x_block;
             int W, rpb;
             if (nx <= xb) {
                 W = nx;
@@ -716,8 +718,8 @@ struct Path {
             const int blocks = (nrows + rpb - 1) / rpb;
             const size_t smem = (size_t)NV * rpb * (W + 2) * sizeof(R);
             ProfScope ps(c, PROF_SWEEP_X, s);
-            if constexpr (charf)
-                sweep_x_char_kernel<UT, NS, MODE, SCHEME><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
+            if constexpr (CAP > 0)
+                sweep_x_capped_kernel<UT, NS, MODE, SCHEME, GEOM, CAP><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
             else
                 sweep_x_kernel<R, UT, NS, MODE, SCHEME, GEOM><<<blocks, threads, smem, s>>>(c->mslot, m, W, rpb);
         } else {
@@ -725,11 +727,11 @@ struct Path {
             const long long lines = (long long)c->g.nx * (dir == 1 ? c->g.nz : c->g.ny);
             dim3 grid((unsigned)((lines + c->walk_block - 1) / c->walk_block), (unsigned)((nd + c->walk_seg - 1) / c->walk_seg));
             ProfScope ps(c, dir == 1 ? PROF_SWEEP_Y : PROF_SWEEP_Z, s);
-            if constexpr (charf) {
+            if constexpr (CAP > 0) {
                 if (dir == 1)
-                    sweep_walk_char_kernel<UT, NS, 1, MODE, SCHEME><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+                    sweep_walk_capped_kernel<UT, NS, 1, MODE, SCHEME, GEOM, CAP><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
                 else
-                    sweep_walk_char_kernel<UT, NS, 2, MODE, SCHEME><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
+                    sweep_walk_capped_kernel<UT, NS, 2, MODE, SCHEME, GEOM, CAP><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
             } else if (dir == 1)
                 sweep_walk_kernel<R, UT, NS, 1, MODE, SCHEME, GEOM><<<grid, c->walk_block, 0, s>>>(c->mslot, m, c->walk_seg);
             else

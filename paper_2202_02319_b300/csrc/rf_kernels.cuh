@@ -1792,13 +1792,15 @@ __global__ void __launch_bounds__(256) sweep_x_kernel(int mslot, const __grid_co
     sweep_x_block<R, UT, NS, MODE, SCHEME, GEOM>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
 
-// The FP32 characteristic-wise x sweep (SCHEME 2, 3 on a Cartesian grid) in blocks of
-// at most 128 threads, held to 168 registers for three blocks per SM.
-template <typename UT, int NS, int MODE, int SCHEME>
-__global__ void __launch_bounds__(128, 3) sweep_x_char_kernel(int mslot, const __grid_constant__ Member m, int W, int rpb) {
+// FP32 global-memory x sweeps with a register cap: blocks of at most 128 threads, MINB
+// of them per SM (the characteristic-wise, TENO6 and mapped sweeps, whose many live
+// values otherwise leave 8-16 warps per SM to cover their global loads).
+template <typename UT, int NS, int MODE, int SCHEME, int GEOM, int MINB>
+__global__ void __launch_bounds__(128, MINB) sweep_x_capped_kernel(int mslot, const __grid_constant__ Member m, int W,
+                                                                   int rpb) {
     const MechDev &M = c_mech[mslot];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    sweep_x_block<float, UT, NS, MODE, SCHEME, 0>(M, m, blockIdx.x, W, rpb, smem_raw);
+    sweep_x_block<float, UT, NS, MODE, SCHEME, GEOM>(M, m, blockIdx.x, W, rpb, smem_raw);
 }
 
 // y / z sweep: thread = one line (x fastest), segment of `seg` cells along DIR.
@@ -1850,13 +1852,14 @@ __global__ void __launch_bounds__(128) sweep_walk_kernel(int mslot, const __grid
     sweep_walk_block<R, UT, NS, DIR, MODE, SCHEME, GEOM>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
-// The FP32 characteristic-wise y / z sweeps (SCHEME 2, 3 on a Cartesian grid): latency-
-// bound on their global loads, so held to 168 registers for three blocks per SM (they
-// spill 80 / 112 bytes to L1).
-template <typename UT, int NS, int DIR, int MODE, int SCHEME>
-__global__ void __launch_bounds__(128, 3) sweep_walk_char_kernel(int mslot, const __grid_constant__ Member m, int seg) {
+// FP32 global-memory y / z sweeps with a register cap (MINB blocks of 128 threads per SM):
+// the characteristic-wise sweeps (latency-bound on their global loads at 221-244
+// registers) and the TENO6 and mapped ones.
+template <typename UT, int NS, int DIR, int MODE, int SCHEME, int GEOM, int MINB>
+__global__ void __launch_bounds__(128, MINB) sweep_walk_capped_kernel(int mslot, const __grid_constant__ Member m,
+                                                                      int seg) {
     const MechDev &M = c_mech[mslot];
-    sweep_walk_block<float, UT, NS, DIR, MODE, SCHEME, 0>(M, m, blockIdx.x, blockIdx.y, seg);
+    sweep_walk_block<float, UT, NS, DIR, MODE, SCHEME, GEOM>(M, m, blockIdx.x, blockIdx.y, seg);
 }
 
 // ----------------------------------------------------------------------------- staged y / z sweep (FP32 bulk)
