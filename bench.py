@@ -572,7 +572,8 @@ def run_adjoint_leg(args, dev):
     cases = synth.adjoint_members(0, nm, n, t0=0.5 * nsteps * dt)
     ck = args.adjoint_ck if args.adjoint_ck > 0 else max(1, nsteps // 2)
     probs = [adjoint.HeatReleaseProblem(c.mech, c.grid, c.prim, c.laser, nsteps=nsteps, dt=dt,
-                                        checkpoint_every=ck, device=dev) for c in cases]
+                                        checkpoint_every=ck, device=dev, store_stages=not args.adjoint_recompute)
+             for c in cases]
     p0 = [pr.default_params() for pr in probs]
     probs[0].run(p0[0], keep=False)               # warm-up (also builds the kernels' first launches)
     torch.cuda.synchronize()
@@ -591,6 +592,7 @@ def run_adjoint_leg(args, dev):
     t_grad = time.perf_counter() - t0
     cells = cases[0].grid.ncells
     return {"members": nm, "cells": cells, "steps": nsteps, "dt_s": dt, "checkpoint_every": ck,
+            "stages": "recomputed" if args.adjoint_recompute else "stored within each segment",
             "params": int(p0[0].numel()),
             "forward_ms": round(t_fwd * 1e3, 2), "forward_and_gradient_ms": round(t_grad * 1e3, 2),
             "gradient_over_forward": round(t_grad / t_fwd, 2),
@@ -782,6 +784,8 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=20)
     ap.add_argument("--adjoint-members", type=int, default=1)
     ap.add_argument("--adjoint-ck", type=int, default=0, help="checkpoint interval (0: half the steps)")
+    ap.add_argument("--adjoint-recompute", action="store_true",
+                    help="recompute every step's stages in the reverse sweep instead of keeping them")
     ap.add_argument("--leg", default=None, choices=["mapped", "nscbc", "charwise"],
                     help="run only this leg and print its result (for profiling its kernels)")
     args = ap.parse_args()

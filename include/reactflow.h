@@ -345,6 +345,27 @@ int rf_rk_step_objective(rf_ctx *c, double *U, double *T, double t, double dt, c
 int rf_adjoint_rk_step(rf_ctx *c, const double *Un, const double *Tn, double t, double dt, const rf_laser *laser,
                        double w_hrr, double *lam, double *grad_params, rf_stream s);
 
+/* rf_rk_step_objective that also keeps the step's stage inputs for the reverse pass,
+ * so that the checkpointed gradient need not recompute them (two RHS evaluations
+ * of each step it reverses).  stages (device, (2 (Ns+4) + 3) N doubles, caller-owned)
+ * receives, in order: U^(1) and U^(2) ([Ns+4][N] each), the converged temperature of
+ * U^n, that of U^(1), and the Newton warm start of U^(2) (the same as U^(1)'s) ([N]
+ * each).  U, T, J as in rf_rk_step_objective (with J NULL the stages are those of the
+ * plain step the checkpoint recomputation runs).  Errors: RF_EINVAL for a null
+ * context, state or stages pointer or dt <= 0, and the conditions of
+ * rf_rk_step_objective.  Synchronous. */
+int rf_rk_step_stages(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *laser, double *J,
+                      double *stages, rf_stream s);
+
+/* rf_adjoint_rk_step from the stage inputs rf_rk_step_stages kept for the step from
+ * U_n (device, not modified) instead of recomputing them; same lam, grad_params and
+ * w_hrr.  The temperatures in stages serve as Newton warm starts and are overwritten
+ * (use each stages buffer once).  The result equals rf_adjoint_rk_step's to the order
+ * of the FP64 atomic sums.  Errors: RF_EINVAL for a null pointer or dt <= 0, and the
+ * conditions of rf_adjoint_rk_step.  Asynchronous. */
+int rf_adjoint_rk_step_stored(rf_ctx *c, const double *Un, double *stages, double t, double dt, const rf_laser *laser,
+                              double w_hrr, double *lam, double *grad_params, rf_stream s);
+
 /* Batched ensembles (workload shape of the paper's ensemble studies, Results,
  * Ensemble simulation; Methods, Diffusion flame): members are contexts of one
  * mechanism and precision with their own grid sizes, states and lasers.

@@ -9,8 +9,12 @@ Parameters p = (E, x0, y0, z0, sigma_r, ln A_0 .. ln A_{Nr-1}).
 
 The forward run keeps the state every `checkpoint_every` steps; the reverse run
 restores each checkpoint, recomputes the states of its segment and walks back
-through them with rf_adjoint_rk_step.  All arithmetic is in the CUDA library;
-this module only schedules calls and stores states.
+through them with rf_adjoint_rk_step.  With store_stages (the default) the
+recomputation also keeps each step's stage inputs (rf_rk_step_stages, (2 (Ns + 4)
++ 3) N doubles per step of a segment), so that the reverse of every step but the
+segment's last skips the two RHS evaluations that recompute them
+(rf_adjoint_rk_step_stored).  All arithmetic is in the CUDA library; this module
+only schedules calls and stores states.
 """
 from __future__ import annotations
 
@@ -24,7 +28,7 @@ from . import native as nv
 
 class HeatReleaseProblem:
     def __init__(self, mech, grid, prim, laser, nsteps: int, dt: float, t0: float = 0.0,
-                 checkpoint_every: int = 20, device="cuda"):
+                 checkpoint_every: int = 20, device="cuda", store_stages: bool = True):
         self.mech0 = mech
         self.grid = grid
         self.prim = torch.as_tensor(prim, dtype=torch.float64).reshape(5 + mech.n_species, -1)
@@ -33,6 +37,7 @@ class HeatReleaseProblem:
         self.dt = float(dt)
         self.t0 = float(t0)
         self.ck = max(1, int(checkpoint_every))
+        self.store_stages = bool(store_stages)
         self.device = torch.device(device)
         self.np = 5 + mech.n_reactions
         self._state = None
@@ -91,12 +96,22 @@ class HeatReleaseProblem:
             U, T = cks[k0][0].clone(), cks[k0][1].clone()
             seg = []
             for k in range(k0, k1):                # recompute the segment's step inputs
-                seg.append((U.clone(), T.clone()))
-                if k + 1 < k1:
-                    nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las, want_J=False)
+                if k + 1 < k1 and self.store_stages:
+                    # keep the step's stage inputs: its reverse then skips two RHS
+                    st = torch.empty(nv.stages_size(ctx), dtype=torch.float64, device=self.device)
+                    seg.append((U.clone(), None, st))
+                    nv.rk_step_stages(ctx, U, T, self.t0 + k * self.dt, self.dt, las, st)
+                else:
+                    seg.append((U.clone(), T.clone(), None))
+                    if k + 1 < k1:
+                        nv.rk_step_objective(ctx, U, T, self.t0 + k * self.dt, self.dt, las, want_J=False)
             for k in range(k1 - 1, k0 - 1, -1):
-                Un, Tn = seg[k - k0]
-                nv.adjoint_rk_step(ctx, Un, Tn, self.t0 + k * self.dt, self.dt, las, 1.0, lam, grads)
+                Un, Tn, st = seg[k - k0]
+                if st is not None:
+                    nv.adjoint_rk_step_stored(ctx, Un, st, self.t0 + k * self.dt, self.dt, las, 1.0, lam, grads)
+                else:
+                    nv.adjoint_rk_step(ctx, Un, Tn, self.t0 + k * self.dt, self.dt, las, 1.0, lam, grads)
+                seg[k - k0] = None
         nv.check(ctx)
         return grads.cpu()
 

@@ -1785,12 +1785,16 @@ struct AdjPath {
 
     // U_{n+1} from U_n through rhs evaluations and stage combinations (the same
     // arithmetic the adjoint step differentiates); *J += dt sum_k b_k H(U^(k)).
+    // With `stages` (device, (2 nv + 3) n doubles) the step also keeps U^(1), U^(2), the
+    // converged temperatures of U^n and U^(1) and the Newton warm start of U^(2) for
+    // adjoint_step_stored.
     static int step_objective(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *L, double *J,
-                              cudaStream_t s) {
+                              cudaStream_t s, double *stages = nullptr) {
         AdjWs w;
         int rc = adj_ws(c, w);
         if (rc) return rc;
         const long long N = c->n * c->nv;
+        const size_t tb = (size_t)c->n * 8;
         const double b[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
         const double *in[3] = {U, c->U1, c->U2};
         const double ts[3] = {t, t + dt, t + 0.5 * dt};
@@ -1808,10 +1812,19 @@ struct AdjPath {
             if (k == 0) {   // U1 = Un + dt R
                 CUDA_TRY(cudaMemcpyAsync(c->U1, U, N * 8, cudaMemcpyDeviceToDevice, s));
                 if ((rc = axpby(c->U1, w.R, dt, 1.0, N, s))) return rc;
+                if (stages) {
+                    CUDA_TRY(cudaMemcpyAsync(stages, c->U1, N * 8, cudaMemcpyDeviceToDevice, s));
+                    CUDA_TRY(cudaMemcpyAsync(stages + 2 * N, T, tb, cudaMemcpyDeviceToDevice, s));
+                }
             } else if (k == 1) {   // U2 = 3/4 Un + 1/4 (U1 + dt R)
                 CUDA_TRY(cudaMemcpyAsync(c->U2, c->U1, N * 8, cudaMemcpyDeviceToDevice, s));
                 if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
                 if ((rc = axpby(c->U2, U, 0.75, 0.25, N, s))) return rc;
+                if (stages) {
+                    CUDA_TRY(cudaMemcpyAsync(stages + N, c->U2, N * 8, cudaMemcpyDeviceToDevice, s));
+                    CUDA_TRY(cudaMemcpyAsync(stages + 2 * N + c->n, T, tb, cudaMemcpyDeviceToDevice, s));
+                    CUDA_TRY(cudaMemcpyAsync(stages + 2 * N + 2 * c->n, T, tb, cudaMemcpyDeviceToDevice, s));
+                }
             } else {   // Un+1 = 1/3 Un + 2/3 (U2 + dt R)
                 if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
                 if ((rc = axpby(U, c->U2, 2.0 / 3.0, 1.0 / 3.0, N, s))) return rc;
@@ -1839,23 +1852,44 @@ struct AdjPath {
         if ((rc = axpby(c->U2, w.R, dt, 1.0, N, s))) return rc;
         if ((rc = axpby(c->U2, Un, 0.75, 0.25, N, s))) return rc;
         CUDA_TRY(cudaMemcpyAsync(w.T2, w.T1, c->n * 8, cudaMemcpyDeviceToDevice, s));
+        return adjoint_reverse(c, Un, c->U1, c->U2, w.T0, w.T1, w.T2, t, dt, L, wH, lam, grads, s);
+    }
+
+    // adjoint_step from the stage inputs step_objective kept in `stages` (their
+    // temperatures serve as Newton warm starts and are overwritten).
+    static int adjoint_step_stored(rf_ctx *c, const double *Un, double *stages, double t, double dt, const rf_laser *L,
+                                   double wH, double *lam, double *grads, cudaStream_t s) {
+        const long long N = c->n * c->nv;
+        double *T0 = stages + 2 * N;
+        return adjoint_reverse(c, Un, stages, stages + N, T0, T0 + c->n, T0 + 2 * c->n, t, dt, L, wH, lam, grads, s);
+    }
+
+    // The reverse of one step given its stage inputs U1, U2 and temperatures T0 (of Un),
+    // T1 (of U1) and T2 (warm start of U2), each overwritten by the converged one.
+    static int adjoint_reverse(rf_ctx *c, const double *Un, const double *U1, const double *U2, double *T0, double *T1,
+                               double *T2, double t, double dt, const rf_laser *L, double wH, double *lam, double *grads,
+                               cudaStream_t s) {
+        AdjWs w;
+        int rc = adj_ws(c, w);
+        if (rc) return rc;
+        const long long N = c->n * c->nv;
         // reverse: stage 3 (U2, t + dt/2)
         CUDA_TRY(cudaMemsetAsync(w.Ub2, 0, N * 8, s));
         CUDA_TRY(cudaMemsetAsync(w.lamS, 0, N * 8, s));
         if ((rc = axpby(w.lamS, lam, 2.0 / 3.0 * dt, 0.0, N, s))) return rc;
-        if ((rc = adjoint_rhs(c, c->U2, w.T2, t + 0.5 * dt, L, w.lamS, wH * dt * (2.0 / 3.0), w.Ub2, grads, s))) return rc;
+        if ((rc = adjoint_rhs(c, U2, T2, t + 0.5 * dt, L, w.lamS, wH * dt * (2.0 / 3.0), w.Ub2, grads, s))) return rc;
         if ((rc = axpby(w.Ub2, lam, 2.0 / 3.0, 1.0, N, s))) return rc;
         // stage 2 (U1, t + dt)
         CUDA_TRY(cudaMemsetAsync(w.Ub1, 0, N * 8, s));
         if ((rc = axpby(w.lamS, w.Ub2, 0.25 * dt, 0.0, N, s))) return rc;
-        if ((rc = adjoint_rhs(c, c->U1, w.T1, t + dt, L, w.lamS, wH * dt / 6.0, w.Ub1, grads, s))) return rc;
+        if ((rc = adjoint_rhs(c, U1, T1, t + dt, L, w.lamS, wH * dt / 6.0, w.Ub1, grads, s))) return rc;
         if ((rc = axpby(w.Ub1, w.Ub2, 0.25, 1.0, N, s))) return rc;
         // stage 1 (Un, t): lam_n = 1/3 lam + 3/4 Ub2 + Ub1 + VJP(Un, dt Ub1)
         CUDA_TRY(cudaMemcpyAsync(w.Ln, w.Ub1, N * 8, cudaMemcpyDeviceToDevice, s));
         if ((rc = axpby(w.Ln, w.Ub2, 0.75, 1.0, N, s))) return rc;
         if ((rc = axpby(w.Ln, lam, 1.0 / 3.0, 1.0, N, s))) return rc;
         if ((rc = axpby(w.lamS, w.Ub1, dt, 0.0, N, s))) return rc;
-        if ((rc = adjoint_rhs(c, Un, w.T0, t, L, w.lamS, wH * dt / 6.0, w.Ln, grads, s))) return rc;
+        if ((rc = adjoint_rhs(c, Un, T0, t, L, w.lamS, wH * dt / 6.0, w.Ln, grads, s))) return rc;
         CUDA_TRY(cudaMemcpyAsync(lam, w.Ln, N * 8, cudaMemcpyDeviceToDevice, s));
         return RF_OK;
     }
@@ -1889,6 +1923,19 @@ extern "C" int rf_adjoint_rk_step(rf_ctx *c, const double *Un, const double *Tn,
                                   double w_hrr, double *lam, double *grad_params, rf_stream s) {
     if (!c || !Un || !Tn || !lam || !grad_params || !(dt > 0.0)) return fail(RF_EINVAL, "rf_adjoint_rk_step: bad argument");
     ADJ_DISPATCH(c, adjoint_step(c, Un, Tn, t, dt, L, w_hrr, lam, grad_params, (cudaStream_t)s));
+}
+
+extern "C" int rf_rk_step_stages(rf_ctx *c, double *U, double *T, double t, double dt, const rf_laser *L, double *J,
+                                 double *stages, rf_stream s) {
+    if (!c || !U || !T || !stages || !(dt > 0.0)) return fail(RF_EINVAL, "rf_rk_step_stages: bad argument");
+    ADJ_DISPATCH(c, step_objective(c, U, T, t, dt, L, J, (cudaStream_t)s, stages));
+}
+
+extern "C" int rf_adjoint_rk_step_stored(rf_ctx *c, const double *Un, double *stages, double t, double dt,
+                                         const rf_laser *L, double w_hrr, double *lam, double *grad_params, rf_stream s) {
+    if (!c || !Un || !stages || !lam || !grad_params || !(dt > 0.0))
+        return fail(RF_EINVAL, "rf_adjoint_rk_step_stored: bad argument");
+    ADJ_DISPATCH(c, adjoint_step_stored(c, Un, stages, t, dt, L, w_hrr, lam, grad_params, (cudaStream_t)s));
 }
 
 // ----------------------------------------------------------------------------- peak probe

@@ -81,6 +81,10 @@ _sigs = {
                                             _vp]),
     "rf_adjoint_rk_step": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser),
                                           ctypes.c_double, _vp, _vp, _vp]),
+    "rf_rk_step_stages": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(Laser), _dp,
+                                         _vp, _vp]),
+    "rf_adjoint_rk_step_stored": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.POINTER(Laser), ctypes.c_double, _vp, _vp, _vp]),
     "rf_ensemble_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                           ctypes.POINTER(Laser), _vp, ctypes.POINTER(_vp)]),
     "rf_ensemble_free": (None, [_vp]),
@@ -418,3 +422,32 @@ def adjoint_rk_step(ctx: Context, Un, Tn, t: float, dt: float, laser, w_hrr: flo
     L = _laser(laser)
     _check(_lib.rf_adjoint_rk_step(ctx.handle, _ptr(Un), _ptr(Tn), float(t), float(dt), ctypes.byref(L) if L else None,
                                    float(w_hrr), _ptr(lam), _ptr(grad_params), _stream(stream)), "rf_adjoint_rk_step")
+
+
+def stages_size(ctx: Context) -> int:
+    """Doubles of the stages buffer rk_step_stages fills: (2 (Ns + 4) + 3) N."""
+    return (2 * ctx.nv + 3) * ctx.n
+
+
+def rk_step_stages(ctx: Context, U, T, t: float, dt: float, laser, stages, stream=None, want_J: bool = False) -> float:
+    """rk_step_objective that also keeps the step's stage inputs in `stages` (a CUDA
+    float64 tensor of stages_size(ctx) values) for adjoint_rk_step_stored."""
+    if stages.numel() < stages_size(ctx) or stages.element_size() != 8 or not stages.is_cuda:
+        raise ValueError("stages: a CUDA float64 tensor of stages_size(ctx) values")
+    L = _laser(laser)
+    J = ctypes.c_double(0.0)
+    _check(_lib.rf_rk_step_stages(ctx.handle, _ptr(U), _ptr(T), float(t), float(dt), ctypes.byref(L) if L else None,
+                                  ctypes.byref(J) if want_J else None, _ptr(stages), _stream(stream)), "rf_rk_step_stages")
+    return J.value
+
+
+def adjoint_rk_step_stored(ctx: Context, Un, stages, t: float, dt: float, laser, w_hrr: float, lam, grad_params,
+                           stream=None):
+    """adjoint_rk_step from the stage inputs rk_step_stages kept (their temperatures are
+    overwritten)."""
+    if stages.numel() < stages_size(ctx):
+        raise ValueError("stages: fewer than stages_size(ctx) values")
+    L = _laser(laser)
+    _check(_lib.rf_adjoint_rk_step_stored(ctx.handle, _ptr(Un), _ptr(stages), float(t), float(dt),
+                                          ctypes.byref(L) if L else None, float(w_hrr), _ptr(lam), _ptr(grad_params),
+                                          _stream(stream)), "rf_adjoint_rk_step_stored")

@@ -68,6 +68,11 @@ def test_host_argument_checks():
     assert "NSCBC" in nv.last_error()
     d = nv.NscbcDesc(101325.0, 0.25, 1.0, 1.0, 1.0, 1.0, 0.0, None)
     assert nv._lib.rf_set_nscbc(None, 0, 0, ctypes.byref(d)) == nv.RF_EINVAL
+    # the stored-stage adjoint entry points refuse null pointers before any device call
+    assert nv._lib.rf_rk_step_stages(None, None, None, 0.0, 1e-9, None, None, None, None) == nv.RF_EINVAL
+    assert "rf_rk_step_stages" in nv.last_error()
+    assert nv._lib.rf_adjoint_rk_step_stored(None, None, None, 0.0, 1e-9, None, 1.0, None, None, None) == nv.RF_EINVAL
+    assert "rf_adjoint_rk_step_stored" in nv.last_error()
     # more than three molecules on one side of a reaction
     m2 = synth.mechanism_4sp(0)
     m2.nu_f = m2.nu_f.copy()

@@ -185,3 +185,46 @@ def test_objective_nodes_keep_their_own_checkpoints():
     J1.backward()
     assert torch.allclose(b0.grad, a.grad, rtol=1e-9, atol=1e-12 * float(a.grad.abs().max()))
     assert not torch.allclose(b1.grad, a.grad, rtol=1e-6, atol=0.0)
+
+
+def test_stored_stages_match_recomputation():
+    """rf_rk_step_stages advances the state bit for bit as rf_rk_step_objective does,
+    and the reverse step from its kept stage inputs (rf_adjoint_rk_step_stored) equals
+    the recomputing one (rf_adjoint_rk_step) to the order of the FP64 atomic sums; the
+    checkpointed gradient with and without stored stages likewise."""
+    from paper_2202_02319_b300 import adjoint, native as nv
+    case = _case()
+    mech, ctx, U, T = gpu_setup(case)
+    las = case.laser.as_tuple()
+    dt, t = 4e-9, case.laser.t0 - 8e-9
+    U0, T0 = U.clone(), T.clone()
+    st = torch.empty(nv.stages_size(ctx), dtype=torch.float64, device="cuda")
+    Ua, Ta = U.clone(), T.clone()
+    Ja = nv.rk_step_stages(ctx, Ua, Ta, t, dt, las, st, want_J=True)
+    Ub, Tb = U.clone(), T.clone()
+    Jb = nv.rk_step_objective(ctx, Ub, Tb, t, dt, las)
+    nv.check(ctx)
+    assert torch.equal(Ua, Ub) and torch.equal(Ta, Tb) and Ja == Jb
+    g = torch.Generator().manual_seed(11)
+    lam0 = torch.randn(U.shape, generator=g, dtype=torch.float64).cuda()
+    la, lb = lam0.clone(), lam0.clone()
+    ga = torch.zeros(5 + case.mech.n_reactions, dtype=torch.float64, device="cuda")
+    gb = torch.zeros_like(ga)
+    nv.adjoint_rk_step(ctx, U0, T0, t, dt, las, 1.0, la, ga)
+    # stages of the plain step (no heat-release evaluation), as the gradient keeps them
+    st2 = torch.empty_like(st)
+    nv.rk_step_stages(ctx, U0.clone(), T0.clone(), t, dt, las, st2)
+    nv.adjoint_rk_step_stored(ctx, U0, st2, t, dt, las, 1.0, lb, gb)
+    nv.check(ctx)
+    assert _rel(lb, la) < 1e-13
+    assert float(((gb - ga).abs() / ga.abs().clamp_min(ga.abs().max() * 1e-12)).max()) < 1e-12
+    with pytest.raises(ValueError):
+        nv.rk_step_stages(ctx, U0.clone(), T0.clone(), t, dt, las, st[:10])
+    grads = []
+    for store in (True, False):
+        prob = adjoint.HeatReleaseProblem(case.mech, case.grid, case.prim, case.laser, nsteps=7, dt=4e-9,
+                                          checkpoint_every=4, store_stages=store)
+        p = prob.default_params()
+        J, state = prob.run_with_state(p)
+        grads.append(prob.gradient(state))
+    assert float(((grads[0] - grads[1]).abs() / grads[1].abs().clamp_min(grads[1].abs().max() * 1e-12)).max()) < 1e-11
