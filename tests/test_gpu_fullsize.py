@@ -104,19 +104,21 @@ SCHEMES = [("teno6", 16, {"scheme": "teno6"}, 3), ("charwise_weno3z", 64, {"spli
            ("charwise_teno6", 80, {"scheme": "teno6", "splitting": "characteristic"}, 3)]
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 @pytest.mark.parametrize("name,flags,ofl,r", SCHEMES, ids=[x[0] for x in SCHEMES])
-def test_fullsize_rhs_sampled_other_schemes(jet, name, flags, ofl, r):
+def test_fullsize_rhs_sampled_other_schemes(jet, name, flags, ofl, r, precision):
     """TENO6 and characteristic-wise splitting (WENO3-Z, TENO6) at 256^3 in FP64, in the
     configuration the bench's legs time, on sampled cells (patch radius r: the scheme's
     halo).  TENO6: 1e-12 per variable.  Characteristic-wise: 1e-12 of the group's
     largest sampled value, or twice the oracle's own movement at the sample under a
     one-ulp perturbation of the patch state where that is larger (the projection
     cancels terms of the size of the species energies, so its rounding does not scale
-    with the RHS)."""
+    with the RHS).  Mixed precision: 1e-4 of the group's largest sampled value, the
+    mixed RHS bar of the WENO3-Z test above."""
     from paper_2202_02319_b300 import native as nv
     case = jet
     ns = case.mech.n_species
-    mech, ctx, U, T = _gpu_state(case, 0, flags)
+    mech, ctx, U, T = _gpu_state(case, precision, flags)
     out = torch.empty_like(U)
     t = case.laser.t0
     nv.rhs(ctx, U, T, t, case.laser.as_tuple(), out)
@@ -133,21 +135,24 @@ def test_fullsize_rhs_sampled_other_schemes(jet, name, flags, ofl, r):
         ro, _ = oracle.rhs.rhs(mt, g, Up, Tp, t, las, ofl)
         orc.append(ro[:, r, r, r])
         gpu.append(out[:, (c[2] * N + c[1]) * N + c[0]].cpu())
-        if "splitting" in ofl:
+        if "splitting" in ofl and precision == 0:
             xi = torch.randint(0, 2, Up.shape, generator=gen, dtype=torch.float64) * 2.0 - 1.0
             r1, _ = oracle.rhs.rhs(mt, g, Up * (1.0 + xi * 2.0 ** -52), Tp, t, las, ofl)
             noise.append((r1[:, r, r, r] - ro[:, r, r, r]).abs())
     del out, U, T, ctx
     gpu, orc = torch.stack(gpu, 1), torch.stack(orc, 1)
     diff = (gpu - orc).abs().amax(1)
-    if noise:
+    tol = 1e-12 if precision == 0 else 1e-4
+    if precision:
+        scale = _group_scale(orc.abs().amax(1), ns)
+    elif noise:
         nz = torch.stack(noise, 1).amax(1)
         scale = torch.maximum(_group_scale(orc.abs().amax(1), ns), 2.0e12 * _group_scale(nz, ns))
     else:
         scale = orc.abs().amax(1)
     err = torch.where(scale > 0, diff / torch.where(scale > 0, scale, torch.ones_like(scale)), diff).numpy()
-    print(name, "err", err.max())
-    assert err.max() < 1e-12, err
+    print(name, precision, "err", err.max())
+    assert err.max() < tol, err
 
 
 @pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-6)], ids=["fp64", "mixed"])
