@@ -120,15 +120,15 @@ def sweep_bytes_method(ns: int) -> int:
 
 # Counts of the mixed-precision cell-state kernel (9 species, 19 reactions) from one
 # ncu capture of the 96^3 jet case, per cell and averaged over the three launches of an
-# RK step (the first also forms the chemical time-step rates: 155.0 DFMA, 69.0 DMUL,
-# 32.0 DADD and 328.3 DRAM bytes; the other two 155.4, 69.1, 32.2 and 331.0): FP64
+# RK step (the first also forms the chemical time-step rates: 209.0 DFMA, 69.0 DMUL,
+# 15.0 DADD and 322.1 DRAM bytes; the other two 209.4, 69.1, 15.2 and 326.6): FP64
 # thread instructions (DFMA, DMUL, DADD; FLOP = 2 DFMA + DMUL + DADD) and DRAM =
 # dram__bytes_read.sum + dram__bytes_write.sum (traffic grows with the cell count, so a
 # full 256^3 launch is the per-cell figure times 256^3).  Retaken with every change of
-# the kernel (this capture: the Newton mixture polynomial formed as FP32 pairs).
-CELL_STATE_MIXED_FP64_INST = (155.27, 69.07, 32.13)      # DFMA, DMUL, DADD per cell
+# the kernel.
+CELL_STATE_MIXED_FP64_INST = (209.27, 69.08, 15.11)      # DFMA, DMUL, DADD per cell
 CELL_STATE_MIXED_FP64_FLOP_PER_CELL = 2 * CELL_STATE_MIXED_FP64_INST[0] + sum(CELL_STATE_MIXED_FP64_INST[1:])
-CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 330.1              # (328.3 + 2 x 331.0) / 3
+CELL_STATE_MIXED_DRAM_BYTES_PER_CELL = 325.1              # (322.1 + 2 x 326.6) / 3
 
 
 def cell_state_bytes(ns: int, rsize: int) -> int:

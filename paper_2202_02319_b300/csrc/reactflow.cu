@@ -109,17 +109,7 @@ static int mech_slot(const rf_mech *mc, int *out) {
     }
     for (int k = 0; k < MECH_SLOTS; ++k) {
         if (g_slot_owner[dev][k]) continue;
-        m->d.slot = k;
         CUDA_TRY(cudaMemcpyToSymbol(c_mech, &m->d, sizeof(MechDev), k * sizeof(MechDev)));
-        float2 split[2][NSMAX][6];
-        for (int r = 0; r < 2; ++r)
-            for (int s = 0; s < NSMAX; ++s)
-                for (int q = 0; q < 6; ++q) {
-                    const double v = m->d.ecR[r][s][q];
-                    const float h = (float)v;
-                    split[r][s][q] = make_float2(h, (float)(v - (double)h));
-                }
-        CUDA_TRY(cudaMemcpyToSymbol(g_ecRs, split, sizeof(split), k * sizeof(split)));
         g_slot_owner[dev][k] = m;
         m->slot[dev] = k;
         *out = k;

@@ -26,7 +26,6 @@ enum StatusBits : int { ST_NEWTON = 1, ST_NONFINITE = 2, ST_RANGE = 4, ST_TIMEOU
 // Mechanism constants (species, NASA-7 sets, transport, compact reactions).
 struct MechDev {
     int ns, nr, two_ranges, npress;            // npress: pressure-dependent reactions
-    int slot;                                  // this copy's constant-memory slot
     double Tmid;
     double W[NSMAX], invW[NSMAX], RW[NSMAX];   // R/W_s
     double cpc[2][NSMAX][5];                   // cp/R = c0 + c1 T + ... + c4 T^4, per range
@@ -409,57 +408,10 @@ struct MixPoly {
     float cvf[5];
 };
 
-// FP32 (high, low) split of the energy coefficients ecR of every mechanism slot
-// (high = ecR rounded to FP32, low = the rest rounded to FP32), for the mixed path's
-// mixture polynomial.
-__device__ float2 g_ecRs[MECH_SLOTS][2][NSMAX][6];
-
 // The species coefficients hold e_s = h_s - (R/W_s) T (the -R/W_s in the linear
 // term); the constant term's sum starts from e5 (the Newton solve's -e_target).
-// Without CV64 (the mixed path) each coefficient sum_s w_s ecR_s,k (+ e5) is formed
-// as an unevaluated FP32 pair on the FP32 pipe (the weights and the coefficients
-// split into two FP32 parts, exact products by FMA, Knuth's two-sum for the
-// accumulation, the low parts summed) and widened once: relative error about 2^-46
-// of the largest term, against 54 FP64 FMAs at 9 species.  The FP32 operations are
-// the rounding intrinsics, which the compiler does not contract.
 template <int NS, bool CV64>
 __device__ __forceinline__ void mix_poly(const MechDev &M, int r, const double (&Y)[NS], double e5, MixPoly &P) {
-    if constexpr (!CV64) {
-        const float2 *__restrict__ tab = &g_ecRs[M.slot][r][0][0];
-        float sh[6], sl[6];
-#pragma unroll
-        for (int k = 0; k < 5; ++k) sh[k] = sl[k] = 0.f;
-        sh[5] = d2f(e5);
-        sl[5] = d2f(e5 - f2d(sh[5]));
-#pragma unroll
-        for (int s = 0; s < NS; ++s) {
-            const float wh = d2f(Y[s]), wl = d2f(Y[s] - f2d(wh));
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const float2 a = tab[s * 6 + k];
-                const float ph = __fmul_rn(wh, a.x);
-                float pl = fmaf(wh, a.x, -ph);                    // exact: wh a.x = ph + pl
-                pl = fmaf(wh, a.y, fmaf(wl, a.x, pl));            // the cross terms
-                const float t = __fadd_rn(sh[k], ph);
-                const float bb = __fsub_rn(t, sh[k]);
-                const float err = __fadd_rn(__fsub_rn(sh[k], __fsub_rn(t, bb)), __fsub_rn(ph, bb));
-                sl[k] = __fadd_rn(sl[k], __fadd_rn(err, pl));
-                sh[k] = t;
-            }
-        }
-        float hi[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            P.e[k] = f2d(sh[k]) + f2d(sl[k]);
-            hi[k] = sh[k];
-        }
-        P.cvf[0] = hi[0];
-        P.cvf[1] = 2.0f * hi[1];
-        P.cvf[2] = 3.0f * hi[2];
-        P.cvf[3] = 4.0f * hi[3];
-        P.cvf[4] = 5.0f * hi[4];
-        return;
-    }
     double c[6] = {0, 0, 0, 0, 0, e5};
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
