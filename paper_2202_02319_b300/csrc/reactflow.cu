@@ -1480,9 +1480,9 @@ extern "C" int rf_ensemble_create(rf_ctx *const *members, int n, double *const *
         if (lasers) L = lasers[i];
         e->las.push_back(L);
     }
-    cudaError_t er = cudaMalloc((void **)&e->d_bar, 2 * sizeof(unsigned int));
+    cudaError_t er = cudaMalloc((void **)&e->d_bar, 4 * sizeof(unsigned int));
     if (er == cudaSuccess) er = cudaMalloc((void **)&e->d_timeout, sizeof(int));
-    if (er == cudaSuccess) er = cudaMemset(e->d_bar, 0, 2 * sizeof(unsigned int));
+    if (er == cudaSuccess) er = cudaMemset(e->d_bar, 0, 4 * sizeof(unsigned int));
     if (er == cudaSuccess) er = cudaMemset(e->d_timeout, 0, sizeof(int));
     if (er == cudaSuccess) er = cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking);
     if (er == cudaSuccess) er = cudaEventCreateWithFlags(&e->ev_in, cudaEventDisableTiming);
@@ -1563,7 +1563,7 @@ extern "C" int rf_run_ensemble(rf_ensemble *e, int nsteps, int mode, double cfl,
         }
     } else {
         CUDA_TRY(cudaMemsetAsync(e->d_timeout, 0, sizeof(int), s));
-        CUDA_TRY(cudaMemsetAsync(e->d_bar, 0, 2 * sizeof(unsigned int), s));
+        CUDA_TRY(cudaMemsetAsync(e->d_bar, 0, 4 * sizeof(unsigned int), s));
         EnsDev E = ens_dev(e, 1);
         ens_begin_kernel<<<(e->n + 127) / 128, 128, 0, s>>>(E, e->t_dev, cfl, dt_fixed);
         LAUNCH_CHECK();

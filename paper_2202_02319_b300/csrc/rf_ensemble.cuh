@@ -26,7 +26,8 @@ struct EnsDev {
     int nmembers;
     int seg;                     // cells walked per thread in the y / z sweeps
     int newton_maxit;
-    unsigned int *bar;           // [0] arrivals, [1] generation
+    unsigned int *bar;           // [0] arrivals, [1] generation, [2] / [3] next y / z item of the
+                                 // persistent sweep launch
     int *timeout;                // set when a grid barrier gives up
     long long max_spins;         // bound on a barrier wait (iterations of ~100 ns)
     unsigned int bar_expect;     // blocks a barrier waits for (gridDim.x; larger only in tests)
@@ -115,6 +116,29 @@ __device__ __forceinline__ void ens_walk_phase(const MechDev &M, const EnsDev &E
                                                Member &sm, int &s_ok) {
     const int k = DIR == 1 ? 2 : 3;
     for (int w = blockIdx.x; w < E.nitems[k]; w += gridDim.x) {
+        const EnsItem it = E.items[k][w];
+        if (!load_member(E.tab[stage], it.m, sm, s_ok)) continue;
+        if constexpr (sizeof(R) == 4)
+            sweep_walk_staged_block<NS, DIR, MODE>(M, sm, it.a, it.b, E.seg, (float *)smem);
+        else
+            sweep_walk_block<R, UT, NS, DIR, MODE>(M, sm, it.a, it.b, E.seg);
+    }
+}
+
+// The same phase with dynamic work assignment: each block takes the next item from the
+// counter E.bar[k] (k = 2 for y, 3 for z) until the list is exhausted, so that blocks
+// that drew short items (members' ragged edges) take more; the items and their
+// arithmetic are those of ens_walk_phase.
+template <typename R, typename UT, int NS, int DIR, int MODE>
+__device__ __forceinline__ void ens_walk_phase_dynamic(const MechDev &M, const EnsDev &E, int stage, unsigned char *smem,
+                                                       Member &sm, int &s_ok, int &s_w) {
+    const int k = DIR == 1 ? 2 : 3;
+    for (;;) {
+        if (threadIdx.x == 0) s_w = (int)atomicAdd(E.bar + k, 1u);
+        __syncthreads();
+        const int w = s_w;
+        __syncthreads();
+        if (w >= E.nitems[k]) break;
         const EnsItem it = E.items[k][w];
         if (!load_member(E.tab[stage], it.m, sm, s_ok)) continue;
         if constexpr (sizeof(R) == 4)
@@ -216,6 +240,10 @@ __device__ __forceinline__ bool grid_barrier(const EnsDev &E, int &s_flag) {
         int ok = 1;
         if (atomicAdd(E.bar, 1u) == E.bar_expect - 1) {
             atomicExch(E.bar, 0u);
+            // every block is past its y items and none has taken a z item: restart both
+            // work counters (the y one for the next launch)
+            atomicExch(E.bar + 2, 0u);
+            atomicExch(E.bar + 3, 0u);
             __threadfence();
             atomicAdd(E.bar + 1, 1u);
         } else {
@@ -254,13 +282,13 @@ __global__ void __launch_bounds__(128) ens_sweep_stage_kernel(int mslot, const _
     using UT = typename std::conditional<sizeof(R) == 4, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Member sm;
-    __shared__ int s_ok, s_flag;
+    __shared__ int s_ok, s_flag, s_w;
     if (*(volatile int *)E.timeout) return;     // an earlier stage of this step gave up: run nothing
-    ens_walk_phase<R, UT, NS, 1, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok);
+    ens_walk_phase_dynamic<R, UT, NS, 1, MODE_ACCUM>(M, E, stage, smem_raw, sm, s_ok, s_w);
     if (!grid_barrier(E, s_flag)) return;
     // FP32 bulk: the z sweep accumulates and an elementwise launch applies the stage (the
     // stage's FP64 operations would hold this launch's few warps); FP64: fused
-    ens_walk_phase<R, UT, NS, 2, sizeof(R) == 4 ? MODE_ACCUM : MODE_STAGE>(M, E, stage, smem_raw, sm, s_ok);
+    ens_walk_phase_dynamic<R, UT, NS, 2, sizeof(R) == 4 ? MODE_ACCUM : MODE_STAGE>(M, E, stage, smem_raw, sm, s_ok, s_w);
 }
 
 }  // namespace rf
