@@ -699,9 +699,9 @@ struct Path {
     static int sweep_global(rf_ctx *c, const Member &m, int dir, cudaStream_t s) {
         constexpr int NV = NS + 4;
         // FP32 sweeps in register-capped kernels of 128-thread blocks, CAP blocks per SM:
-        // characteristic-wise 3 (168 registers, 80 / 112 bytes of spills), mapped 3
-        // (168, up to 28 bytes), TENO6 5 (96, 52 bytes)
-        constexpr int CAP = sizeof(R) != 4 ? 0 : (SCHEME >= 2 ? 3 : (GEOM ? 3 : (SCHEME == 1 ? 5 : 0)));
+        // characteristic-wise 3 (168 registers, 80 / 112 bytes of spills), mapped 4
+        // (128, up to 44 bytes), TENO6 5 (96, 52 bytes)
+        constexpr int CAP = sizeof(R) != 4 ? 0 : (SCHEME >= 2 ? 3 : (GEOM ? 4 : (SCHEME == 1 ? 5 : 0)));
         if (dir == 0) {
             const int nx = c->g.nx;
             const int xb = CAP ? std::min(c->x_block, 128) : c->x_block;
